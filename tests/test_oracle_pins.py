@@ -1,0 +1,378 @@
+"""Pins for the FP64 oracle against what the mathematics fixes (no GPU).
+
+The paper prints no worked example for its SPME pipeline (it validates against OpenMM, Sec. I), so each
+oracle function is pinned to closed forms, textbook special cases, invariants, brute force on tiny
+inputs and the NaCl Madelung constant. Each pin is chosen so a plausible mistake fails it: a dropped
+1/(pi V) or B-spline modulus (Ewald convergence, Madelung), a sign or index error in the forces or virial
+(finite differences), a transposed reciprocal matrix (triclinic Ewald comparison), a wrong frequency
+aliasing (Ewald convergence).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2009_12617_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------------------------
+# B-splines
+
+
+def _m4_closed(x):
+    """Textbook piecewise cubic B-spline on [0, 4]."""
+    if x <= 0 or x >= 4:
+        return 0.0
+    if x < 1:
+        return x ** 3 / 6
+    if x < 2:
+        return (-3 * x ** 3 + 12 * x ** 2 - 12 * x + 4) / 6
+    if x < 3:
+        return (3 * x ** 3 - 24 * x ** 2 + 60 * x - 44) / 6
+    return (4 - x) ** 3 / 6
+
+
+def _mp_truncated_power(p, x):
+    """Cardinal B-spline by the truncated-power formula (1/(p-1)!) sum_k (-1)^k C(p,k) (x-k)_+^(p-1)."""
+    return sum((-1) ** k * math.comb(p, k) * max(x - k, 0.0) ** (p - 1) for k in range(p + 1)) / math.factorial(
+        p - 1)
+
+
+def test_bspline_cubic_closed_form(oracle_mod):
+    for x in np.linspace(-0.5, 4.5, 401):
+        assert oracle_mod.bspline(4, x) == pytest.approx(_m4_closed(x), abs=1e-13)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
+def test_bspline_truncated_power(oracle_mod, p):
+    for x in np.linspace(0.013, p - 0.013, 97):
+        assert oracle_mod.bspline(p, x) == pytest.approx(_mp_truncated_power(p, x), abs=1e-12)
+
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6, 8])
+def test_bspline_partition_of_unity_and_symmetry(oracle_mod, p):
+    for w in np.linspace(0.0, 0.999, 37):
+        s = sum(oracle_mod.bspline(p, w + j) for j in range(p))
+        ds = sum(oracle_mod.bspline_deriv(p, w + j) for j in range(p))
+        assert s == pytest.approx(1.0, abs=1e-14)
+        assert ds == pytest.approx(0.0, abs=1e-14)
+        assert oracle_mod.bspline(p, w + 0.5) == pytest.approx(oracle_mod.bspline(p, p - w - 0.5), abs=1e-15)
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_bspline_derivative_matches_finite_difference(oracle_mod, p):
+    h = 1e-6
+    for x in np.linspace(0.1, p - 0.1, 53):
+        fd = (oracle_mod.bspline(p, x + h) - oracle_mod.bspline(p, x - h)) / (2 * h)
+        assert oracle_mod.bspline_deriv(p, x) == pytest.approx(fd, abs=1e-8)
+
+
+def test_bspline_node_values_golden(oracle_mod):
+    with open(os.path.join(GOLDEN, "bspline_nodes.txt")) as f:
+        rows = [list(map(int, ln.split())) for ln in f if ln.strip() and not ln.startswith("#")]
+    for row in rows:
+        p, num, den = row[0], row[1:-1], row[-1]
+        assert len(num) == p - 1
+        for k, nk in enumerate(num, start=1):
+            assert oracle_mod.bspline(p, k) == pytest.approx(nk / den, abs=1e-15)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Charge spreading
+
+
+def test_spread_node_atom_exact_weights(oracle_mod):
+    """An atom on a mesh node (w = 0) has weights M_4(j) = 0, 1/6, 2/3, 1/6 on nodes base - j."""
+    L, K = 10.0, (10, 12, 14)
+    box = np.diag([L, L, L])
+    node = np.array([3, 5, 7])
+    pos = (node / np.array(K) * L)[None, :]
+    Q = oracle_mod.spread(pos, [2.0], K, 4, box)
+    w = np.array([0.0, 1 / 6, 2 / 3, 1 / 6])
+    expect = np.zeros(K)
+    for a in range(4):
+        for b in range(4):
+            for c in range(4):
+                expect[(node[0] - a) % K[0], (node[1] - b) % K[1], (node[2] - c) % K[2]] += 2.0 * w[a] * w[b] * w[c]
+    np.testing.assert_allclose(Q, expect, atol=1e-15)
+
+
+def test_spread_charge_sum_and_periodic_images(oracle_mod):
+    """Sum of Q equals the total charge; on a mesh smaller than p the image sum wraps onto itself."""
+    rng = np.random.default_rng(0)
+    L = 7.0
+    box = np.diag([L, L, L])
+    pos = rng.random((5, 3)) * L
+    q = rng.normal(size=5)
+    for K in [(3, 3, 3), (5, 4, 6), (8, 8, 8)]:
+        Q = oracle_mod.spread(pos, q, K, 4, box)
+        assert Q.sum() == pytest.approx(q.sum(), abs=1e-13)
+        # brute-force image sum of eq. (3) for this tiny mesh
+        u = oracle_mod.scaled_coords(pos, K, box)
+        Qb = np.zeros(K)
+        for i in range(5):
+            wts = []
+            for al in range(3):
+                wa = np.zeros(K[al])
+                for k in range(K[al]):
+                    for nimg in range(-6, 7):
+                        wa[k] += oracle_mod.bspline(4, u[i, al] - k - nimg * K[al])
+                wts.append(wa)
+            Qb += q[i] * np.einsum("a,b,c->abc", *wts)
+        np.testing.assert_allclose(Q, Qb, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# DFT
+
+
+def test_dft_separable_equals_full_and_numpy(oracle_mod):
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(4, 6, 5)) + 1j * rng.normal(size=(4, 6, 5))
+    for sign in (+1, -1):
+        a = oracle_mod.dft3(x, sign)
+        b = oracle_mod.dft3(x, sign, full=True)
+        np.testing.assert_allclose(a, b, atol=1e-11)
+    # numpy's fftn uses exp(-2 pi i ...): sign -1
+    np.testing.assert_allclose(oracle_mod.dft3(x, -1), np.fft.fftn(x), atol=1e-11)
+    np.testing.assert_allclose(oracle_mod.dft3(x, +1), np.fft.ifftn(x) * x.size, atol=1e-11)
+
+
+def test_dft_parseval(oracle_mod):
+    rng = np.random.default_rng(2)
+    Q = rng.normal(size=(8, 10, 12))
+    F = oracle_mod.dft3(Q, +1)
+    assert np.sum(np.abs(F) ** 2) == pytest.approx(Q.size * np.sum(Q ** 2), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Moduli
+
+
+@pytest.mark.parametrize("K", [8, 10, 32, 40, 64])
+def test_bmod_closed_forms(oracle_mod, K):
+    """p = 4: |sum M4(k+1) e^{i k t}|^2 = ((2 + cos t)/3)^2; p = 6: ((66 + 52 cos t + 2 cos 2t)/120)^2."""
+    for m in range(K):
+        t = 2 * math.pi * m / K
+        assert oracle_mod.bmod2(K, 4, m) == pytest.approx(1.0 / ((2 + math.cos(t)) / 3) ** 2, rel=1e-13)
+        d6 = (66 + 52 * math.cos(t) + 2 * math.cos(2 * t)) / 120
+        assert oracle_mod.bmod2(K, 6, m) == pytest.approx(1.0 / d6 ** 2, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Ewald comparison terms: an independent numpy implementation
+
+
+def _np_ewald_recip(pos, q, beta, box, mcut):
+    recip = np.linalg.inv(box)  # columns are a*_alpha
+    V = abs(np.linalg.det(box))
+    nmax = [int(math.ceil(mcut * np.linalg.norm(box[a]))) for a in range(3)]
+    ms = np.array([(a, b, c) for a in range(-nmax[0], nmax[0] + 1) for b in range(-nmax[1], nmax[1] + 1)
+                   for c in range(-nmax[2], nmax[2] + 1) if (a, b, c) != (0, 0, 0)], dtype=float)
+    mv = ms @ recip.T
+    m2 = np.sum(mv ** 2, axis=1)
+    keep = m2 <= mcut ** 2
+    mv, m2 = mv[keep], m2[keep]
+    f = np.exp(-math.pi ** 2 * m2 / beta ** 2) / m2
+    S = np.exp(2j * math.pi * pos @ mv.T).T @ q  # (nm,)
+    E = np.sum(f * np.abs(S) ** 2) / (2 * math.pi * V)
+    ph = np.exp(2j * math.pi * pos @ mv.T)  # (n, nm)
+    # F_j = -dE/dr_j ;  dE/dr_j = (1/(2 pi V)) sum f 2 Re(conj(S) q_j 2 pi i m' e^{i th_j})
+    dS = (np.conj(S)[None, :] * 1j * ph).real  # (n, nm)
+    F = -(q[:, None] * (2.0 / V)) * ((dS * f[None, :]) @ mv)
+    e_m = f * np.abs(S) ** 2 / (2 * math.pi * V)
+    fac = 2 * (1 + math.pi ** 2 * m2 / beta ** 2) / m2
+    vir = np.zeros(6)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for k, (a, b) in enumerate(pairs):
+        vir[k] = np.sum(e_m * ((1.0 if a == b else 0.0) - fac * mv[:, a] * mv[:, b]))
+    return E, F, vir
+
+
+def _np_ewald_real(pos, q, beta, box, rcut):
+    from scipy.special import erfc
+
+    E = 0.0
+    F = np.zeros_like(pos)
+    rinv = np.linalg.inv(box)
+    nmax = [int(math.ceil(rcut * np.linalg.norm(rinv[:, a]))) + 1 for a in range(3)]
+    shifts = np.array([(a, b, c) for a in range(-nmax[0], nmax[0] + 1) for b in range(-nmax[1], nmax[1] + 1)
+                       for c in range(-nmax[2], nmax[2] + 1)], dtype=float) @ box
+    for i in range(len(q)):
+        d = pos[i][None, None, :] - pos[None, :, :] + shifts[:, None, :]  # (ns, n, 3)
+        r = np.linalg.norm(d, axis=2)
+        mask = (r <= rcut) & (r > 0)
+        rr = np.where(mask, r, 1.0)
+        e = np.where(mask, q[i] * q[None, :] * erfc(beta * rr) / rr, 0.0)
+        E += 0.5 * e.sum()
+        s = np.where(mask, q[i] * q[None, :] * (erfc(beta * rr) / rr + 2 * beta / math.sqrt(math.pi)
+                                                 * np.exp(-beta ** 2 * rr ** 2)) / rr ** 2, 0.0)
+        F[i] = np.sum(s[:, :, None] * d, axis=(0, 1))
+    return E, F
+
+
+def _tri_box():
+    return np.array([[9.0, 0.0, 0.0], [2.1, 8.5, 0.0], [-1.3, 1.7, 10.2]])
+
+
+@pytest.mark.parametrize("tri", [False, True])
+def test_ewald_terms_match_independent_numpy(oracle_mod, tri):
+    rng = np.random.default_rng(3)
+    box = _tri_box() if tri else np.diag([9.0, 10.0, 11.0])
+    n = 24
+    pos = rng.random((n, 3)) @ box
+    q = rng.normal(size=n)
+    q -= q.mean()
+    beta = 0.45
+    mcut = oracle_mod.ewald_mcut(beta)
+    E, F, V = _np_ewald_recip(pos, q, beta, box, mcut)
+    r = oracle_mod.ewald_recip(pos, q, beta, box)
+    assert r["energy"] == pytest.approx(E, rel=1e-12)
+    np.testing.assert_allclose(r["forces"], F, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(r["virial"], V, rtol=1e-10, atol=1e-12)
+    Er, Fr = _np_ewald_real(pos, q, beta, box, 6.0 / beta)
+    rr = oracle_mod.ewald_real(pos, q, beta, box)
+    assert rr["energy"] == pytest.approx(Er, rel=1e-12)
+    np.testing.assert_allclose(rr["forces"], Fr, rtol=1e-10, atol=1e-12)
+    assert oracle_mod.ewald_self(q, beta) == pytest.approx(-beta / math.sqrt(math.pi) * np.sum(q ** 2), rel=1e-14)
+
+
+def _madelung():
+    with open(os.path.join(GOLDEN, "madelung_nacl.txt")) as f:
+        vals = dict(ln.split() for ln in f if ln.strip() and not ln.startswith("#"))
+    return float(vals["M"]), float(vals["a_angstrom"]), int(vals["cells"])
+
+
+@pytest.mark.parametrize("beta", [0.7, 1.1])
+def test_ewald_madelung(oracle_mod, beta):
+    M, a, cells = _madelung()
+    pos, q, box = wl.rocksalt(a, cells)
+    tot = (oracle_mod.ewald_recip(pos, q, beta, box)["energy"] + oracle_mod.ewald_real(pos, q, beta, box)["energy"]
+           + oracle_mod.ewald_self(q, beta))
+    assert -tot * (a / 2) / (len(q) / 2) == pytest.approx(M, abs=1e-6)
+
+
+def test_spme_madelung(oracle_mod):
+    """E_rec(SPME) + E_dir + E_self reproduces the NaCl Madelung constant to 6 digits."""
+    M, a, cells = _madelung()
+    pos, q, box = wl.rocksalt(a, cells)
+    beta = 0.9
+    r = oracle_mod.spme(pos, q, (32, 32, 32), 6, beta, box)
+    tot = r["energy"] + oracle_mod.ewald_real(pos, q, beta, box)["energy"] + oracle_mod.ewald_self(q, beta)
+    assert -tot * (a / 2) / (len(q) / 2) == pytest.approx(M, abs=1e-6)
+    # the NaCl lattice is a force-free equilibrium: every reciprocal force is set by symmetry to ~0
+    assert np.abs(r["forces"]).max() < 1e-9
+
+
+def _small_water(n=150, L=18.0, seed=5):
+    pos, q = wl.water_box(n, L, seed)
+    return pos.astype(np.float64), q.astype(np.float64), np.diag([L, L, L])
+
+
+@pytest.mark.parametrize("p", [4, 6])
+def test_spme_converges_to_ewald(oracle_mod, p):
+    """SPME -> Ewald as the mesh is refined, with error falling at least like h^(p-1)."""
+    pos, q, box = _small_water()
+    beta = 0.34
+    ref = oracle_mod.ewald_recip(pos, q, beta, box)
+    Ks = (12, 24, 48) if p == 4 else (12, 24)
+    errE, errF, errV = [], [], []
+    for K in Ks:
+        r = oracle_mod.spme(pos, q, (K, K, K), p, beta, box)
+        errE.append(abs(r["energy"] - ref["energy"]) / abs(ref["energy"]))
+        errF.append(np.sqrt(np.mean((r["forces"] - ref["forces"]) ** 2) / np.mean(ref["forces"] ** 2)))
+        errV.append(np.max(np.abs(r["virial"] - ref["virial"])) / np.max(np.abs(ref["virial"])))
+    for err in (errE, errF, errV):
+        slopes = [math.log2(err[i] / err[i + 1]) for i in range(len(err) - 1)]
+        assert min(slopes) >= p - 1, (err, slopes)
+    assert errE[-1] < 1e-3 and errF[-1] < 1e-3
+
+
+def test_spme_triclinic_converges_to_ewald(oracle_mod):
+    """A triclinic cell: a transposed reciprocal matrix or wrong m' would not converge."""
+    rng = np.random.default_rng(7)
+    box = _tri_box()
+    pos = rng.random((40, 3)) @ box
+    q = rng.normal(size=40)
+    q -= q.mean()
+    beta = 0.4
+    ref = oracle_mod.ewald_recip(pos, q, beta, box)
+    r = oracle_mod.spme(pos, q, (36, 36, 40), 6, beta, box)
+    assert r["energy"] == pytest.approx(ref["energy"], rel=1e-5)
+    np.testing.assert_allclose(r["forces"], ref["forces"], atol=1e-4 * np.abs(ref["forces"]).max())
+    np.testing.assert_allclose(r["virial"], ref["virial"], atol=1e-5 * np.abs(ref["virial"]).max())
+
+
+@pytest.mark.parametrize("tri", [False, True])
+def test_spme_forces_are_gradient(oracle_mod, tri):
+    """F = -dE/dr by central differences (SPME forces are the exact gradient of SPME energy for p >= 3)."""
+    rng = np.random.default_rng(11)
+    box = _tri_box() if tri else np.diag([11.0, 12.0, 13.0])
+    n = 12
+    pos = rng.random((n, 3)) @ box
+    q = rng.normal(size=n)
+    q -= q.mean()
+    K, p, beta = (16, 18, 20), 4, 0.4
+    F = oracle_mod.spme(pos, q, K, p, beta, box)["forces"]
+    h = 1e-5
+    for i in range(0, n, 3):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = -(oracle_mod.spme(pp, q, K, p, beta, box)["energy"] - oracle_mod.spme(pm, q, K, p, beta, box)["energy"]) / (2 * h)
+            assert F[i, d] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("tri", [False, True])
+def test_spme_virial_is_strain_derivative(oracle_mod, tri):
+    """Pi_ab = -dE/d eps_ab under r -> (I+eps) r, a -> (I+eps) a at fixed fractional coordinates."""
+    rng = np.random.default_rng(13)
+    box = _tri_box() if tri else np.diag([11.0, 12.0, 13.0])
+    n = 16
+    frac = rng.random((n, 3))
+    q = rng.normal(size=n)
+    q -= q.mean()
+    K, p, beta = (16, 16, 20), 4, 0.4
+    vir = oracle_mod.spme(frac @ box, q, K, p, beta, box)["virial"]
+    h = 1e-6
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for k, (a, b) in enumerate(pairs):
+        es = []
+        for sgn in (+1, -1):
+            eps = np.zeros((3, 3))
+            eps[a, b] = sgn * h
+            T = np.eye(3) + eps
+            bx = box @ T.T  # rows a_alpha -> (I + eps) a_alpha
+            es.append(oracle_mod.spme(frac @ bx, q, K, p, beta, bx)["energy"])
+        fd = -(es[0] - es[1]) / (2 * h)
+        assert vir[k] == pytest.approx(fd, rel=1e-6, abs=1e-9), (k, vir[k], fd)
+
+
+def test_spme_phi_identity_and_translation(oracle_mod):
+    """E = 1/2 sum Q phi; shifting every atom by one mesh cell leaves E and F unchanged."""
+    pos, q, box = _small_water(90, 15.0, 17)
+    K, p, beta = (20, 24, 30), 4, 0.34
+    r = oracle_mod.spme(pos, q, K, p, beta, box, want_mesh=True)
+    assert r["e_phi"] == pytest.approx(r["energy"], rel=1e-12)
+    for al in range(3):
+        shift = box[al] / K[al]
+        s = oracle_mod.spme(pos + shift, q, K, p, beta, box)
+        assert s["energy"] == pytest.approx(r["energy"], rel=1e-11)
+        np.testing.assert_allclose(s["forces"], r["forces"], atol=1e-11 * np.abs(r["forces"]).max())
+    # a whole-cell shift (a periodic image) changes nothing either
+    s = oracle_mod.spme(pos + box[0] - 2 * box[2], q, K, p, beta, box)
+    assert s["energy"] == pytest.approx(r["energy"], rel=1e-11)
+
+
+def test_spme_empty_and_single_charge(oracle_mod):
+    box = np.diag([10.0, 10.0, 10.0])
+    r = oracle_mod.spme(np.zeros((0, 3)), np.zeros(0), (8, 8, 8), 4, 0.3, box)
+    assert r["energy"] == 0.0 and np.all(r["virial"] == 0.0)
+    # a lone charge: E_rec is a positive self-interaction that does not depend on where it sits
+    e0 = oracle_mod.spme([[1.0, 2.0, 3.0]], [1.0], (16, 16, 16), 6, 0.3, box)["energy"]
+    e1 = oracle_mod.spme([[4.2, 7.1, 0.3]], [1.0], (16, 16, 16), 6, 0.3, box)["energy"]
+    assert e0 > 0 and e1 == pytest.approx(e0, rel=1e-4)
