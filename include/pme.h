@@ -1,0 +1,185 @@
+/*
+ * pme.h — C ABI of the GB300 reciprocal-space Smooth Particle Mesh Ewald (SPME) library.
+ *
+ * The library evaluates the long-range (reciprocal-space) part of Ewald electrostatics by SPME, the
+ * pipeline the paper runs on its FPGA cluster (Sec. III-A, "Long-Range Pipeline"): B-spline charge
+ * spreading onto a K1 x K2 x K3 mesh (Sec. III-A "Charge Spreading"), a forward 3D FFT, a multiply by the
+ * influence ("Green's") function, an inverse 3D FFT (Sec. III-A "FFT"), and force interpolation with the
+ * B-spline derivatives (Sec. III-A "Force Interpolation"). Energy and virial are reduced on the fly in
+ * the influence-function step. The equations are the standard SPME ones [Essmann et al. 1995], which
+ * the paper cites for the method (Sec. II) without writing them out:
+ *   E = 1/2 sum_{m != 0} B(m) C(m) |FFT(Q)(m)|^2,
+ *   C(m) = exp(-pi^2 |m'|^2 / beta^2) / (pi V |m'|^2),  B(m) = prod_alpha |b_alpha(m_alpha)|^2,
+ *   Pi_ab = 1/2 sum B C |FFT(Q)|^2 (delta_ab - 2 (1 + pi^2 |m'|^2 / beta^2) m'_a m'_b / |m'|^2),
+ *   F_i = -q_i sum_k grad_i[theta_1 theta_2 theta_3](k) phi(k),  phi = IFFT(B C FFT(Q)).
+ *
+ * Only the reciprocal-space term is computed: the caller adds the real-space and self terms.
+ *
+ * Units: lengths in Angstrom, charges in e, Coulomb constant 1: energy and virial in e^2/A, forces in
+ * e^2/A^2. Multiply by 332.0637 for kcal/mol.
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers on the plan's device (for example a torch CUDA tensor's
+ *     data_ptr()), unless the function name ends in _host. Scalars returned through pointers
+ *     (energy, virial) are host pointers unless stated otherwise.
+ *   - pos is n x 3 float32, row-major (x, y, z per atom); any position is accepted and wrapped into
+ *     the periodic cell. q is n float32. forces is n x 3 float32, overwritten.
+ *   - virial[6] = (xx, yy, zz, xy, xz, yz).
+ *   - The caller owns all input/output arrays; the library owns plans, meshes, tables and scratch.
+ *   - No call aborts, throws across the ABI or traps on the device. Errors come back as pme_status;
+ *     pme_last_error_detail() gives a message for the last error on the calling thread.
+ *   - A plan is not thread-safe: one host thread (or external locking) per plan.
+ */
+#ifndef PME_GB300_H
+#define PME_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pme_plan pme_plan;      /* opaque: one periodic system geometry + its resident device state */
+typedef struct pme_batch pme_batch;    /* opaque: a fixed set of systems evaluated in one persistent launch */
+typedef struct pme_server pme_server;  /* opaque: continuous-batching request loop */
+typedef int64_t pme_ticket;
+
+typedef enum {
+    PME_OK = 0,
+    PME_EINVAL = 1,        /* invalid argument, or a non-finite / absurdly far position or charge */
+    PME_EUNSUPPORTED = 2,  /* valid SPME parameters this build does not implement (e.g. odd p) */
+    PME_ENOMEM = 3,        /* device or host allocation failed, or over the server memory budget */
+    PME_ECUDA = 4,         /* a CUDA runtime call failed (detail has the CUDA error string) */
+    PME_EOVERFLOW = 5,     /* sum |q| too large for the 64-bit fixed-point charge mesh */
+    PME_EAGAIN = 6,        /* server: no slot or memory free right now; retry later */
+    PME_ETIMEOUT = 7,      /* a bounded device-side wait gave up (persistent kernel dependency) */
+    PME_PENDING = 8        /* pme_poll: request still in flight */
+} pme_status;
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* Single system                                                                                           */
+
+/* Create a plan for mesh K[3] (K1, K2, K3), B-spline order p, Ewald splitting parameter beta (1/A) and
+ * periodic cell box[9] (rows are the cell vectors a, b, c in A; any non-singular, right- or left-handed
+ * cell). cuda_stream is a cudaStream_t (NULL = the legacy default stream) on the current device; every
+ * launch of the plan goes to it.
+ * Requirements: each K_alpha even, 8 <= K_alpha <= 128 and with no prime factor other than 2, 3, 5;
+ * p in {4, 6, 8} and p <= min(K); beta > 0 and finite. Invalid values return PME_EINVAL; odd p returns
+ * PME_EUNSUPPORTED. The plan precomputes the influence-function table B(m)C(m) in FP64 (stored as an
+ * unevaluated sum of two floats) and the FFT twiddles, and allocates the mesh (about 30 bytes per mesh
+ * point). On success *out receives the plan; on failure *out is NULL. */
+pme_status pme_create(const int K[3], int p, double beta, const double box[9], void *cuda_stream, pme_plan **out);
+
+/* Replace the periodic cell (e.g. after a barostat step); recomputes the influence table. Same box
+ * rules as pme_create. Synchronous with respect to the plan stream. */
+pme_status pme_set_box(pme_plan *plan, const double box[9]);
+
+/* One SPME evaluation, synchronous: enqueues the pipeline on the plan stream, waits for it, and returns
+ * energy (host double*) and virial (host double[6]); either may be NULL. n = 0 gives energy 0, virial 0.
+ * pos, q, forces are device pointers (see conventions). The first call with a given n (or a larger n
+ * than before) may allocate per-atom scratch; later calls allocate nothing. Returns PME_EINVAL for a
+ * non-finite position or charge, PME_EOVERFLOW when sum |q| >= 2^22 e (the fixed-point mesh headroom);
+ * in both cases the outputs are unspecified. */
+pme_status pme_compute(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, double *energy,
+                       double *virial);
+
+/* pme_compute with diagnostic taps: when non-NULL, mesh_dev (DEVICE, K1*K2*K3 int64, [k1][k2][k3] with k3
+ * fastest) receives the charge mesh after spreading as fixed-point integers round(Q * 2^40) summed
+ * exactly, and phi_dev (DEVICE, K1*K2*K3 float) the potential mesh phi after the inverse FFT. Meant for
+ * verification (stage-by-stage comparison, bit-exactness of the mesh); costs two extra copies. */
+pme_status pme_compute_debug(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
+                             double *energy, double *virial, int64_t *mesh_dev, float *phi_dev);
+
+/* Asynchronous form of pme_compute: enqueues the pipeline and returns without waiting. ev_dev is a
+ * DEVICE pointer to 7 doubles that receives (energy, virial[6]) when the stream reaches that point.
+ * Allocates nothing once pme_reserve(plan, n) (or an earlier call with at least n atoms) has run, so it
+ * may be captured in a CUDA graph. Device-side errors are latched in the plan and returned by the next
+ * pme_sync(). */
+pme_status pme_enqueue(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, double *ev_dev);
+
+/* Pre-allocate per-atom scratch for up to n atoms (so later pme_enqueue calls allocate nothing). */
+pme_status pme_reserve(pme_plan *plan, int64_t n);
+
+/* Wait for the plan stream and return (and clear) any device-side error latched by enqueued work. */
+pme_status pme_sync(pme_plan *plan);
+
+/* pme_compute with HOST arrays (pos, q, forces in pageable or pinned host memory): the library copies
+ * inputs to its own device staging, evaluates, and copies forces back, all on the plan stream, and
+ * returns when forces, energy and virial are in host memory. */
+pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
+                            double *energy, double *virial);
+
+/* Per-stage device time: runs reps evaluations, each stage kernel bracketed by CUDA events on the plan
+ * stream, and returns the mean microseconds per stage in stage_us[6] = (bin, spread, forward FFT,
+ * influence multiply + energy/virial, inverse FFT, force interpolation). Arrays as in pme_compute;
+ * forces receive the last evaluation's result. Synchronous. */
+pme_status pme_profile_stages(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, int reps,
+                              double stage_us[6]);
+
+/* Device bytes the plan holds right now (mesh, tables, per-atom scratch). */
+size_t pme_plan_device_bytes(const pme_plan *plan);
+
+void pme_destroy(pme_plan *plan);
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* Batched evaluation: many independent systems in ONE persistent kernel launch                            */
+
+/* Build a batch over nsys existing plans (not owned by the batch; each must outlive it and must not be
+ * used elsewhere while the batch runs). Atom counts n[s] are fixed for the batch. Atom arrays of all
+ * systems are packed back to back in the order given: system s owns atoms [off_s, off_s + n[s]) with
+ * off_s = n[0] + ... + n[s-1]. The batch runs on cuda_stream and captures its launch in a CUDA graph on
+ * first use. */
+pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, void *cuda_stream, pme_batch **out);
+
+/* Evaluate every system of the batch: pos (Ntot x 3), q (Ntot), forces (Ntot x 3) are packed device
+ * arrays; ev_dev is a DEVICE array of nsys x 7 doubles (energy, virial[6] per system). Asynchronous:
+ * call pme_batch_sync() to wait and collect device-side errors. */
+pme_status pme_batch_enqueue(pme_batch *batch, const float *pos, const float *q, float *forces, double *ev_dev);
+pme_status pme_batch_sync(pme_batch *batch);
+void pme_batch_destroy(pme_batch *batch);
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent requests                                                   */
+
+/* A server owns a worker thread that admits submitted requests into "waves" (one persistent launch
+ * each) while earlier waves are still running, bounded by max_slots requests in flight and by
+ * mem_budget_bytes of device memory held by the plans of in-flight requests. */
+pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server **out);
+
+/* Submit one evaluation on a resident plan. pos, q, forces are device arrays that must stay valid until
+ * pme_poll returns PME_OK or an error; energy (double*) and virial (double[6]) are host pointers written
+ * before completion is reported (either may be NULL). Requests on the same plan run one at a time, in
+ * submission order. Returns PME_EAGAIN when max_slots requests are already queued or in flight, or the
+ * plan alone exceeds the memory budget (PME_ENOMEM). */
+pme_status pme_submit(pme_server *srv, pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
+                      double *energy, double *virial, pme_ticket *out);
+
+/* Query a ticket: PME_OK when done (results written; the ticket is then retired), PME_PENDING while in
+ * flight, or the request's error. block != 0 waits until it is done. */
+pme_status pme_poll(pme_server *srv, pme_ticket ticket, int block);
+
+/* Device-side latency statistics of completed requests (microseconds from submit to completion). */
+pme_status pme_server_stats(pme_server *srv, int64_t *completed, double *p50_us, double *p99_us, int64_t *waves);
+
+void pme_server_destroy(pme_server *srv);
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* Errors and test hooks                                                                                   */
+
+const char *pme_strerror(pme_status s);
+
+/* Copy the calling thread's last error message (NUL-terminated, truncated to len) into buf. Returns the
+ * status that produced it (PME_OK if none). */
+pme_status pme_last_error_detail(char *buf, size_t len);
+
+/* Test hook: when set (nonzero) on a batch, its next launch makes one dependency wait on a counter that
+ * nothing advances. The bounded wait gives up after wait_limit_ns (<= 2 s) and the launch reports
+ * PME_ETIMEOUT from pme_batch_sync(), leaving the device usable. 0 restores normal operation. */
+pme_status pme_batch_debug_stall(pme_batch *batch, int enable, int64_t wait_limit_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PME_GB300_H */

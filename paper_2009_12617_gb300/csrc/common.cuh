@@ -1,0 +1,258 @@
+// Shared definitions for the SPME stage bodies.
+//
+// Every stage body is written as a sequence of data-parallel phases ("for idx = tid; idx < total;
+// idx += nthreads") separated by CTA barriers. Built by nvcc they are the CUDA kernels' bodies; built by
+// a host C++ compiler with PME_HOST_EMULATION they run with one thread per CTA (tid = 0, nthreads = 1,
+// barriers vanish), which the CPU tests use to check the index arithmetic against the FP64 oracle. The
+// library itself only contains the CUDA build.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#if defined(PME_HOST_EMULATION)
+#include <cuda_runtime.h>  // host-side vector types only (float2, float4, int2, ulonglong2)
+#include <string.h>
+#define PME_DEV inline
+#define PME_TID 0
+#define PME_NTH 1
+#define PME_SYNC() ((void)0)
+#define PME_FENCE() ((void)0)
+#define PME_SHARED static
+#else
+#include <cuda_runtime.h>
+#define PME_DEV __device__ __forceinline__
+#define PME_TID ((int)threadIdx.x)
+#define PME_NTH ((int)blockDim.x)
+#define PME_SYNC() __syncthreads()
+#define PME_FENCE() __threadfence()
+#define PME_SHARED __shared__
+#endif
+
+namespace pme {
+
+// Mesh edge of one spread / gather tile. Atoms are binned by the tile that holds their highest support
+// point; the tile's shared-memory region is (TILE + p - 1)^3 mesh points.
+constexpr int TILE = 8;
+// Fixed-point scale of the charge mesh: Q is accumulated as round(q theta1 theta2 theta3 * 2^40) in int64,
+// so the mesh is bit-identical whatever order the atoms are added in.
+constexpr float FIX_SCALE = 1099511627776.0f;            // 2^40
+constexpr float FIX_INV = 9.094947017729282379150390625e-13f;  // 2^-40
+// Sum |q| is accumulated in fixed point 2^24 per e. The mesh headroom is |Q| < 2^23 e; sum |q| < 2^22 e
+// bounds every mesh value and every partial sum, so larger totals are refused.
+constexpr float QABS_SCALE = 16777216.0f;                // 2^24
+constexpr unsigned long long QABS_LIMIT = 1ull << 46;    // 2^22 e in 2^24 units
+constexpr int BIN_CHUNK = 256;   // atoms per binning work item
+constexpr int OVF_ITEMS = 8;     // extra spread / gather work items that handle bucket-overflow atoms
+constexpr int MAX_K = 128;
+
+enum StatusBits : unsigned {
+    ST_NONFINITE = 1u,   // a position or charge is NaN / Inf, or absurdly far outside the cell
+    ST_OVERFLOW = 2u,    // sum |q| beyond the fixed-point headroom
+    ST_TIMEOUT = 4u,     // a bounded dependency wait gave up
+    ST_INTERNAL = 8u     // an internal consistency check failed
+};
+
+// Per-system control block in device memory. Zeroed at creation; every counter is reset by the stage
+// that consumes it last, so no memset is needed between evaluations.
+struct Ctl {
+    unsigned status;            // StatusBits, latched until the host reads and clears it
+    unsigned novf;              // atoms that did not fit in their tile's bucket
+    unsigned long long qabs;    // sum |q| in 2^-24 e units
+    unsigned conv_done;         // finished k1-pencil items (the last one reduces energy / virial)
+    unsigned gather_done;       // finished gather items (the last one resets novf)
+    unsigned pad[2];
+    double ev[8];               // energy, virial xx yy zz xy xz yz (internal copy for synchronous calls)
+};
+
+// Everything a stage needs to know about one system, passed by value to kernels.
+struct SysDev {
+    int K1, K2, K3, H3;          // mesh; H3 = K3/2 + 1 (half spectrum along k3)
+    int p;                       // B-spline order
+    int nt1, nt2, nt3, ntiles;   // spread / gather tiles per dimension
+    int cap;                     // bucket capacity (atoms per tile)
+    int n;                       // atoms
+    int nbin;                    // binning work items = ceil(n / BIN_CHUNK)
+    // u_alpha = sum_j r_j C[j][alpha], C[j][alpha] = K_alpha a*_alpha[j], as an unevaluated float sum
+    // chi + clo (about 48 significant bits), index 3*j + alpha.
+    float chi[9], clo[9];
+    // a*_alpha[j] (index 3*j + alpha) for m' = sum_alpha mt_alpha a*_alpha, and pi^2 / beta^2.
+    float rec[9];
+    float pi2b2;
+    // inputs / outputs (caller-owned)
+    const float *pos;
+    const float *q;
+    float *forces;
+    double *ev;
+    // resident state (library-owned)
+    unsigned long long *grid;    // K1*K2*K3 int64 fixed-point charge mesh, [k1][k2][k3]
+    float2 *spec;                // K1*K2*H3 complex half spectrum, [k1][m2][m3]
+    float *phi;                  // K1*K2*K3 potential mesh, [k1][k2][k3]
+    const float2 *bc;            // influence table B*C as (hi, lo) floats, [m2][m1][m3]
+    const float2 *tw1, *tw2;     // exp(-2 pi i k / K1), exp(-2 pi i k / K2)
+    const float2 *tw3h, *tw3;    // exp(-2 pi i k / (K3/2)), exp(-2 pi i k / K3) for k <= K3/2
+    float4 *bka;                 // bucket records (w1, w2, w3, q), [tile][cap]
+    int2 *bkb;                   // bucket records (packed base, atom index)
+    unsigned *bcount;            // atoms binned per tile
+    float4 *ova;                 // overflow records, capacity n
+    int2 *ovb;
+    double *partials;            // 8 doubles per k1-pencil item
+    Ctl *ctl;
+};
+
+// ---------------------------------------------------------------------------------------------------------
+// small helpers that differ between the CUDA build and the host emulation
+
+#if defined(PME_HOST_EMULATION)
+template <class T> inline T ldcg(const T *p) { return *p; }
+inline unsigned atomic_add_u32(unsigned *p, unsigned v) { unsigned o = *p; *p = o + v; return o; }
+inline void atomic_or_u32(unsigned *p, unsigned v) { *p |= v; }
+inline void atomic_add_u64(unsigned long long *p, unsigned long long v) { *p += v; }
+inline void red_add_u64(unsigned long long *p, unsigned long long v) { *p += v; }
+inline float fmul_rn(float a, float b) { return a * b; }
+inline float fadd_rn(float a, float b) { return a + b; }
+inline float fsub_rn(float a, float b) { return a - b; }
+inline long long f2ll_rn(float x) { return llrintf(x); }
+#else
+template <class T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned atomic_add_u32(unsigned *p, unsigned v) { return atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_or_u32(unsigned *p, unsigned v) { atomicOr(p, v); }
+__device__ __forceinline__ void atomic_add_u64(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
+__device__ __forceinline__ float fmul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ long long f2ll_rn(float x) { return __float2ll_rn(x); }
+#endif
+
+PME_DEV int imin(int a, int b) { return a < b ? a : b; }
+
+PME_DEV float qnan_f() {
+    union {
+        unsigned u;
+        float f;
+    } v;
+    v.u = 0x7fc00000u;
+    return v.f;
+}
+
+// int64 fixed point (scale 2^40) -> float. Split into a signed high word and an unsigned low word so
+// only 32-bit conversions are used; the result is within one rounding of v * 2^-40.
+PME_DEV float fix_to_float(long long v) {
+    float hi = (float)(int)(v >> 32);
+    float lo = (float)(unsigned)(v & 0xffffffffll);
+    return (hi * 4294967296.0f + lo) * FIX_INV;
+}
+
+// Double-float accumulator: value = hi + lo with |lo| <= ulp(hi)/2 (Knuth's TwoSum).
+struct DF {
+    float hi, lo;
+};
+PME_DEV DF df_add(DF a, float b) {
+    float s = fadd_rn(a.hi, b);
+    float bb = fsub_rn(s, a.hi);
+    float err = fadd_rn(fsub_rn(a.hi, fsub_rn(s, bb)), fsub_rn(b, bb));
+    DF r;
+    r.hi = s;
+    r.lo = a.lo + err;
+    return r;
+}
+PME_DEV DF df_add(DF a, DF b) {
+    DF r = df_add(a, b.hi);
+    r.lo += b.lo;
+    float s = fadd_rn(r.hi, r.lo);
+    r.lo = fsub_rn(r.lo, fsub_rn(s, r.hi));
+    r.hi = s;
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Scaled fractional coordinate of one position along dimension al (paper Sec. III-A "Charge Spreading":
+// an atom sits at a fractional position between mesh points). u = sum_j r_j C[j][al] is formed from exact
+// FP32 products (TwoProd via fma) and TwoSum, so w = u - floor(u) carries no FP32 rounding of u itself
+// (|u| up to ~2^23): GB300's FP64 pipe is too slow to spend on every atom. Returns false for a non-finite
+// or absurdly distant position. b = floor(u) mod K, w in [0, 1].
+PME_DEV bool scaled_coord(const SysDev &d, const float r[3], int al, int K, int &b, float &w) {
+    float uh = 0.f, ul = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float ch = d.chi[3 * j + al], cl = d.clo[3 * j + al];
+        const float p = fmul_rn(r[j], ch);
+        float e = fmaf(r[j], ch, -p);  // exact error of the product
+        e = fmaf(r[j], cl, e);
+        const float s = fadd_rn(uh, p);
+        const float bb = fsub_rn(s, uh);
+        const float err = fadd_rn(fsub_rn(uh, fsub_rn(s, bb)), fsub_rn(p, bb));
+        uh = s;
+        ul = ul + (err + e);
+    }
+    const float s = fadd_rn(uh, ul);
+    ul = fsub_rn(ul, fsub_rn(s, uh));
+    uh = s;
+    if (!(fabsf(uh) < 1.0e9f)) return false;  // also rejects NaN
+    const float fl = floorf(uh);
+    float ww = fadd_rn(fsub_rn(uh, fl), ul);
+    long long bi = (long long)fl;
+    if (ww >= 1.f) {
+        ww -= 1.f;
+        bi += 1;
+    } else if (ww < 0.f) {
+        ww += 1.f;
+        bi -= 1;
+    }
+    long long m = bi % K;
+    if (m < 0) m += K;
+    b = (int)m;
+    w = ww;
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Cardinal B-spline weights th[j] = M_P(w + j), j = 0..P-1, by the two-term recursion from the hat
+// function M_2 (the "b-spline calculation" of the paper's Sec. V-C pipeline); with dth[j] = M_P'(w + j) =
+// M_{P-1}(w + j) - M_{P-1}(w + j - 1) when requested. The mesh point of weight j is base - j.
+//
+// The recursion runs on N_n = (n-1)! M_n, whose coefficients are exact small integers, and divides once
+// by (P-1)! with a correctly rounded division at the end. Multiplying by a rounded 1/(n-1) at every order
+// instead would scale every atom's weights by the same relative error, a bias the energy (sixth power of
+// the weights) amplifies; the remaining rounding errors here differ from atom to atom.
+
+template <int P>
+PME_DEV void bspline_order_up(float w, float *th, int n) {
+    th[n - 1] = (1.0f - w) * th[n - 2];
+#pragma unroll
+    for (int j = n - 2; j >= 1; --j) th[j] = (w + (float)j) * th[j] + ((float)(n - j) - w) * th[j - 1];
+    th[0] = w * th[0];
+}
+
+PME_DEV constexpr float factorial_f(int k) { return k <= 1 ? 1.0f : (float)k * factorial_f(k - 1); }
+
+template <int P>
+PME_DEV void bspline_w(float w, float *th) {
+    th[0] = w;
+    th[1] = 1.0f - w;
+#pragma unroll
+    for (int n = 3; n <= P; ++n) bspline_order_up<P>(w, th, n);
+    const float f = factorial_f(P - 1);
+#pragma unroll
+    for (int j = 0; j < P; ++j) th[j] = th[j] / f;
+}
+
+template <int P>
+PME_DEV void bspline_wd(float w, float *th, float *dth) {
+    th[0] = w;
+    th[1] = 1.0f - w;
+#pragma unroll
+    for (int n = 3; n <= P - 1; ++n) bspline_order_up<P>(w, th, n);
+    const float fd = factorial_f(P - 2);
+    dth[0] = th[0] / fd;
+#pragma unroll
+    for (int j = 1; j <= P - 2; ++j) dth[j] = (th[j] - th[j - 1]) / fd;
+    dth[P - 1] = -th[P - 2] / fd;
+    bspline_order_up<P>(w, th, P);
+    const float f = factorial_f(P - 1);
+#pragma unroll
+    for (int j = 0; j < P; ++j) th[j] = th[j] / f;
+}
+
+}  // namespace pme

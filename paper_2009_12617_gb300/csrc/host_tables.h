@@ -1,0 +1,170 @@
+// Host-side set-up of a system: argument validation, cell geometry, FFT twiddles and the influence table.
+// Plain C++ (no CUDA calls), shared by the library's plan code and the CPU emulation build.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace pme {
+
+constexpr double PI_D = 3.14159265358979323846;
+
+// 2, 3, 5-smooth
+inline bool smooth235(int k) {
+    if (k <= 0) return false;
+    for (int f : {2, 3, 5})
+        while (k % f == 0) k /= f;
+    return k == 1;
+}
+
+// Returns 0 (ok), 1 (invalid) or 2 (valid SPME input this build does not implement); msg gets a reason.
+inline int validate_params(const int K[3], int p, double beta, const double box[9], char *msg, size_t len) {
+    for (int a = 0; a < 3; ++a) {
+        if (K[a] < 8 || K[a] > MAX_K || (K[a] & 1) || !smooth235(K[a])) {
+            snprintf(msg, len, "K[%d] = %d: each mesh edge must be even, in [8, %d] and 2,3,5-smooth", a, K[a], MAX_K);
+            return 1;
+        }
+    }
+    if (p < 2 || p > K[0] || p > K[1] || p > K[2]) {
+        snprintf(msg, len, "p = %d must be in [2, min(K)]", p);
+        return 1;
+    }
+    if (p != 4 && p != 6 && p != 8) {
+        snprintf(msg, len, "p = %d: only B-spline orders 4, 6, 8 are implemented", p);
+        return 2;
+    }
+    if (!(beta > 0.0) || !isfinite(beta)) {
+        snprintf(msg, len, "beta must be positive and finite");
+        return 1;
+    }
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(box[i])) {
+            snprintf(msg, len, "box has a non-finite entry");
+            return 1;
+        }
+    return 0;
+}
+
+// recip[3*alpha + j] = component j of a*_alpha (a*_alpha . a_beta = delta), vol = |det|. false if singular.
+inline bool cell_reciprocal(const double box[9], double recip[9], double *vol) {
+    const double *a = box, *b = box + 3, *c = box + 6;
+    const double bxc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+    const double cxa[3] = {c[1] * a[2] - c[2] * a[1], c[2] * a[0] - c[0] * a[2], c[0] * a[1] - c[1] * a[0]};
+    const double axb[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    const double det = a[0] * bxc[0] + a[1] * bxc[1] + a[2] * bxc[2];
+    double scale = 0.0;
+    for (int i = 0; i < 9; ++i) scale = fmax(scale, fabs(box[i]));
+    if (!(fabs(det) > 1e-12 * scale * scale * scale)) return false;
+    for (int j = 0; j < 3; ++j) {
+        recip[j] = bxc[j] / det;
+        recip[3 + j] = cxa[j] / det;
+        recip[6 + j] = axb[j] / det;
+    }
+    *vol = fabs(det);
+    return true;
+}
+
+// Mesh geometry, coordinate transform and tiling of a system.
+inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const double recip[9]) {
+    d.K1 = K[0];
+    d.K2 = K[1];
+    d.K3 = K[2];
+    d.H3 = K[2] / 2 + 1;
+    d.p = p;
+    d.nt1 = (K[0] + TILE - 1) / TILE;
+    d.nt2 = (K[1] + TILE - 1) / TILE;
+    d.nt3 = (K[2] + TILE - 1) / TILE;
+    d.ntiles = d.nt1 * d.nt2 * d.nt3;
+    for (int j = 0; j < 3; ++j)
+        for (int al = 0; al < 3; ++al) {
+            const double c = (double)K[al] * recip[3 * al + j];  // K_alpha a*_alpha[j]
+            const float hi = (float)c;
+            d.chi[3 * j + al] = hi;
+            d.clo[3 * j + al] = (float)(c - (double)hi);
+            d.rec[3 * j + al] = (float)recip[3 * al + j];
+        }
+    d.pi2b2 = (float)(PI_D * PI_D / (beta * beta));
+}
+
+// out[k] = exp(-2 pi i k / L), k < count
+inline void make_twiddles(int L, int count, float2 *out) {
+    for (int k = 0; k < count; ++k) {
+        const double a = -2.0 * PI_D * (double)k / (double)L;
+        out[k].x = (float)cos(a);
+        out[k].y = (float)sin(a);
+    }
+}
+
+// M_p at the integer knots 0..p by the recursion M_n(x) = [x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)] / (n - 1).
+inline std::vector<double> bspline_knots(int p) {
+    std::vector<double> M(p + 1, 0.0), prev(p + 1, 0.0);
+    prev[1] = 1.0;  // M_2(1) = 1
+    for (int n = 3; n <= p; ++n) {
+        for (int x = 0; x <= p; ++x) M[x] = ((double)x * prev[x] + (double)(n - x) * (x >= 1 ? prev[x - 1] : 0.0)) / (n - 1);
+        prev = M;
+    }
+    return prev;
+}
+
+// |b(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K)|^2 (the Euler exponential-spline factor).
+inline std::vector<double> bspline_moduli(int K, int p) {
+    const std::vector<double> M = bspline_knots(p);
+    std::vector<double> b(K);
+    for (int m = 0; m < K; ++m) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k <= p - 2; ++k) {
+            const double a = 2.0 * PI_D * (double)((int64_t)m * k % K) / (double)K;
+            sr += M[k + 1] * cos(a);
+            si += M[k + 1] * sin(a);
+        }
+        b[m] = 1.0 / (sr * sr + si * si);
+    }
+    return b;
+}
+
+inline int signed_freq_h(int m, int K) { return 2 * m <= K ? m : m - K; }
+
+// Influence table on the half spectrum, [m2][m1][m3] with m3 <= K3/2, as (hi, lo) floats of the FP64
+// value B(m) (C(m) + C(-m)) / 2 (the even part of B*C; the two halves differ only on Nyquist axes of
+// non-orthogonal cells, because index K/2 always means frequency +K/2). C(0) = 0.
+inline void make_influence(const int K[3], int p, double beta, const double recip[9], double vol, float2 *out) {
+    const std::vector<double> b1 = bspline_moduli(K[0], p), b2 = bspline_moduli(K[1], p), b3 = bspline_moduli(K[2], p);
+    const int H3 = K[2] / 2 + 1;
+    const double fac = PI_D * PI_D / (beta * beta);
+    auto C = [&](int mt1, int mt2, int mt3) {
+        double mv[3];
+        for (int j = 0; j < 3; ++j) mv[j] = mt1 * recip[j] + mt2 * recip[3 + j] + mt3 * recip[6 + j];
+        const double m2n = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+        return exp(-fac * m2n) / (PI_D * vol * m2n);
+    };
+    for (int m2 = 0; m2 < K[1]; ++m2)
+        for (int m1 = 0; m1 < K[0]; ++m1)
+            for (int m3 = 0; m3 < H3; ++m3) {
+                double v = 0.0;
+                if (m1 | m2 | m3) {
+                    const double cm = C(signed_freq_h(m1, K[0]), signed_freq_h(m2, K[1]), signed_freq_h(m3, K[2]));
+                    const double cp = C(signed_freq_h((K[0] - m1) % K[0], K[0]), signed_freq_h((K[1] - m2) % K[1], K[1]),
+                                        signed_freq_h((K[2] - m3) % K[2], K[2]));
+                    v = b1[m1] * b2[m2] * b3[m3] * 0.5 * (cm + cp);
+                }
+                float2 &o = out[((size_t)m2 * K[0] + m1) * H3 + m3];
+                o.x = (float)v;
+                o.y = (float)(v - (double)o.x);
+            }
+}
+
+// Bucket capacity per tile for n atoms: twice the mean occupancy plus a margin, a multiple of 32.
+// Atoms beyond it go to the overflow list (handled by global-memory paths), so this only tunes speed.
+inline int bucket_capacity(int64_t n, int ntiles) {
+    const double mean = (double)n / (double)ntiles;
+    int cap = (int)(2.0 * mean + 32.0);
+    cap = (cap + 31) / 32 * 32;
+    return cap < 32 ? 32 : cap;
+}
+
+}  // namespace pme

@@ -1,0 +1,422 @@
+// Single-system plans: the C ABI of pme.h for pme_create / pme_compute / pme_enqueue and friends.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/pme.h"
+#include "host_tables.h"
+#include "kernels.h"
+#include "plan_internal.h"
+
+namespace pme {
+
+// ---------------------------------------------------------------------------------------------------------
+// error reporting
+
+static thread_local char g_msg[512] = "";
+static thread_local pme_status g_status = PME_OK;
+
+pme_status fail(pme_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    g_status = s;
+    return s;
+}
+
+pme_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(PME_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+pme_status status_from_bits(unsigned bits) {
+    if (bits & ST_TIMEOUT) return fail(PME_ETIMEOUT, "a bounded device-side dependency wait gave up");
+    if (bits & ST_NONFINITE)
+        return fail(PME_EINVAL, "a position or charge is non-finite, |q| >= 2^22 e, or a position is absurdly far out");
+    if (bits & ST_OVERFLOW) return fail(PME_EOVERFLOW, "sum |q| >= 2^22 e exceeds the fixed-point charge mesh headroom");
+    if (bits & ST_INTERNAL) return fail(PME_ECUDA, "internal consistency check failed on the device");
+    return PME_OK;
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+}
+DeviceGuard::~DeviceGuard() {
+    if (prev_ != dev_) cudaSetDevice(prev_);
+}
+
+cudaError_t ensure_configured(int dev) {
+    static std::mutex mu;
+    static std::vector<char> done(256, 0);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    cudaError_t e = configure_kernels();
+    if (e == cudaSuccess) done[dev] = 1;
+    return e;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------------------------------------
+// plan construction
+
+static pme_status upload_tables(pme_plan *pl) {
+    const int *K = pl->K;
+    const int H3 = K[2] / 2 + 1, Nh = K[2] / 2;
+    std::vector<float2> bc((size_t)K[0] * K[1] * H3);
+    make_influence(K, pl->p, pl->beta, pl->recip, pl->vol, bc.data());
+    std::vector<float2> tw((size_t)K[0] + K[1] + Nh + Nh + 1);
+    make_twiddles(K[0], K[0], tw.data());
+    make_twiddles(K[1], K[1], tw.data() + K[0]);
+    make_twiddles(Nh, Nh, tw.data() + K[0] + K[1]);
+    make_twiddles(K[2], Nh + 1, tw.data() + K[0] + K[1] + Nh);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaMemcpy((void *)pl->d.bc, bc.data(), bc.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(influence table)");
+    if ((e = cudaMemcpy((void *)pl->d.tw1, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(twiddles)");
+    return PME_OK;
+}
+
+static pme_status alloc_mesh(pme_plan *pl) {
+    SysDev &d = pl->d;
+    const size_t K1 = d.K1, K2 = d.K2, K3 = d.K3, H3 = d.H3, Nh = K3 / 2;
+    size_t off = 0;
+    const size_t o_grid = off; off = align256(off + K1 * K2 * K3 * 8);
+    const size_t o_spec = off; off = align256(off + K1 * K2 * H3 * 8);
+    const size_t o_phi = off;  off = align256(off + K1 * K2 * K3 * 4);
+    const size_t o_bc = off;   off = align256(off + K1 * K2 * H3 * 8);
+    const size_t o_tw = off;   off = align256(off + (K1 + K2 + Nh + Nh + 1) * 8);
+    const size_t o_cnt = off;  off = align256(off + (size_t)d.ntiles * 4);
+    const size_t o_par = off;  off = align256(off + K2 * 8 * 8);
+    const size_t o_ctl = off;  off = align256(off + sizeof(Ctl));
+    cudaError_t e = cudaMalloc(&pl->mesh_mem, off);
+    if (e != cudaSuccess) {
+        pl->mesh_mem = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? PME_ENOMEM : PME_ECUDA, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
+    }
+    pl->mesh_bytes = off;
+    char *b = (char *)pl->mesh_mem;
+    d.grid = (unsigned long long *)(b + o_grid);
+    d.spec = (float2 *)(b + o_spec);
+    d.phi = (float *)(b + o_phi);
+    d.bc = (const float2 *)(b + o_bc);
+    float2 *tw = (float2 *)(b + o_tw);
+    d.tw1 = tw;
+    d.tw2 = tw + K1;
+    d.tw3h = tw + K1 + K2;
+    d.tw3 = tw + K1 + K2 + Nh;
+    d.bcount = (unsigned *)(b + o_cnt);
+    d.partials = (double *)(b + o_par);
+    d.ctl = (Ctl *)(b + o_ctl);
+    // The int64 mesh, bucket counts and control block start at zero; afterwards the consuming stages
+    // reset them, so evaluations need no memset.
+    if ((e = cudaMemset(pl->mesh_mem, 0, off)) != cudaSuccess) return cuda_fail(e, "cudaMemset(mesh)");
+    return PME_OK;
+}
+
+pme_status plan_reserve(pme_plan *pl, int64_t n) {
+    if (n <= pl->n_cap && pl->atom_mem) return PME_OK;
+    SysDev &d = pl->d;
+    const int64_t ncap = n > 0 ? n : 1;
+    const int cap = bucket_capacity(ncap, d.ntiles);
+    const size_t nb = (size_t)d.ntiles * cap;
+    size_t off = 0;
+    const size_t o_bka = off; off = align256(off + nb * 16);
+    const size_t o_bkb = off; off = align256(off + nb * 8);
+    const size_t o_ova = off; off = align256(off + (size_t)ncap * 16);
+    const size_t o_ovb = off; off = align256(off + (size_t)ncap * 8);
+    cudaError_t e = cudaStreamSynchronize(pl->stream);  // nothing in flight may still use the old buffers
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (pl->atom_mem) cudaFree(pl->atom_mem);
+    pl->atom_mem = nullptr;
+    pl->atom_bytes = 0;
+    pl->n_cap = 0;
+    e = cudaMalloc(&pl->atom_mem, off);
+    if (e != cudaSuccess) {
+        pl->atom_mem = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? PME_ENOMEM : PME_ECUDA, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
+    }
+    char *b = (char *)pl->atom_mem;
+    d.bka = (float4 *)(b + o_bka);
+    d.bkb = (int2 *)(b + o_bkb);
+    d.ova = (float4 *)(b + o_ova);
+    d.ovb = (int2 *)(b + o_ovb);
+    d.cap = cap;
+    pl->atom_bytes = off;
+    pl->n_cap = ncap;
+    return PME_OK;
+}
+
+SysDev plan_descriptor(const pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *ev_dev) {
+    SysDev d = pl->d;
+    d.n = (int)n;
+    d.nbin = (int)((n + BIN_CHUNK - 1) / BIN_CHUNK);
+    d.pos = pos;
+    d.q = q;
+    d.forces = forces;
+    d.ev = ev_dev ? ev_dev : pl->d.ctl->ev;
+    return d;
+}
+
+pme_status check_atoms(const pme_plan *pl, const float *pos, const float *q, int64_t n, const float *forces) {
+    if (!pl) return fail(PME_EINVAL, "plan is NULL");
+    if (n < 0 || n > (int64_t)0x3fffffff) return fail(PME_EINVAL, "n = %lld out of range [0, 2^30)", (long long)n);
+    if (n > 0 && (!pos || !q || !forces)) return fail(PME_EINVAL, "pos, q and forces must be non-NULL when n > 0");
+    return PME_OK;
+}
+
+// Read (and clear) the device status word after the stream has drained.
+pme_status collect_status(pme_plan *pl, bool copy_ctl) {
+    cudaError_t e;
+    if (!copy_ctl) {
+        if ((e = cudaMemcpyAsync(&pl->h_ctl->status, &pl->d.ctl->status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 pl->stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(status)");
+    }
+    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const unsigned bits = pl->h_ctl->status;
+    if (bits) {
+        if ((e = cudaMemsetAsync(&pl->d.ctl->status, 0, sizeof(unsigned), pl->stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync(status)");
+        if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        pl->h_ctl->status = 0;
+    }
+    return status_from_bits(bits);
+}
+
+}  // namespace pme
+
+using namespace pme;
+
+extern "C" {
+
+const char *pme_strerror(pme_status s) {
+    switch (s) {
+        case PME_OK: return "ok";
+        case PME_EINVAL: return "invalid argument";
+        case PME_EUNSUPPORTED: return "unsupported parameters";
+        case PME_ENOMEM: return "out of memory";
+        case PME_ECUDA: return "CUDA error";
+        case PME_EOVERFLOW: return "fixed-point charge mesh overflow";
+        case PME_EAGAIN: return "no capacity right now; retry";
+        case PME_ETIMEOUT: return "device-side wait timed out";
+        case PME_PENDING: return "pending";
+    }
+    return "unknown status";
+}
+
+pme_status pme_last_error_detail(char *buf, size_t len) {
+    if (buf && len) {
+        strncpy(buf, g_msg, len - 1);
+        buf[len - 1] = 0;
+    }
+    return g_status;
+}
+
+pme_status pme_create(const int K[3], int p, double beta, const double box[9], void *cuda_stream, pme_plan **out) {
+    if (!out) return fail(PME_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!K || !box) return fail(PME_EINVAL, "K and box must be non-NULL");
+    char msg[256];
+    const int v = validate_params(K, p, beta, box, msg, sizeof(msg));
+    if (v == 1) return fail(PME_EINVAL, "%s", msg);
+    if (v == 2) return fail(PME_EUNSUPPORTED, "%s", msg);
+    double recip[9], vol;
+    if (!cell_reciprocal(box, recip, &vol)) return fail(PME_EINVAL, "box is singular");
+    pme_plan *pl = new (std::nothrow) pme_plan();
+    if (!pl) return fail(PME_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&pl->dev);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    if ((e = ensure_configured(pl->dev)) != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "configure kernels");
+    }
+    pl->stream = (cudaStream_t)cuda_stream;
+    memcpy(pl->K, K, sizeof(pl->K));
+    pl->p = p;
+    pl->beta = beta;
+    memcpy(pl->box, box, sizeof(pl->box));
+    memcpy(pl->recip, recip, sizeof(recip));
+    pl->vol = vol;
+    memset(&pl->d, 0, sizeof(pl->d));
+    fill_geometry(pl->d, K, p, beta, recip);
+    pme_status st;
+    if ((st = alloc_mesh(pl)) != PME_OK || (st = upload_tables(pl)) != PME_OK || (st = plan_reserve(pl, 1)) != PME_OK) {
+        pme_destroy(pl);
+        return st;
+    }
+    if ((e = cudaMallocHost((void **)&pl->h_ctl, sizeof(Ctl))) != cudaSuccess) {
+        pl->h_ctl = nullptr;
+        pme_destroy(pl);
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    memset(pl->h_ctl, 0, sizeof(Ctl));
+    *out = pl;
+    return PME_OK;
+}
+
+pme_status pme_set_box(pme_plan *pl, const double box[9]) {
+    if (!pl || !box) return fail(PME_EINVAL, "plan and box must be non-NULL");
+    char msg[256];
+    const int v = validate_params(pl->K, pl->p, pl->beta, box, msg, sizeof(msg));
+    if (v) return fail(PME_EINVAL, "%s", msg);
+    double recip[9], vol;
+    if (!cell_reciprocal(box, recip, &vol)) return fail(PME_EINVAL, "box is singular");
+    DeviceGuard g(pl->dev);
+    memcpy(pl->box, box, sizeof(pl->box));
+    memcpy(pl->recip, recip, sizeof(recip));
+    pl->vol = vol;
+    fill_geometry(pl->d, pl->K, pl->p, pl->beta, recip);
+    return upload_tables(pl);
+}
+
+pme_status pme_reserve(pme_plan *pl, int64_t n) {
+    if (!pl) return fail(PME_EINVAL, "plan is NULL");
+    if (n < 0 || n > (int64_t)0x3fffffff) return fail(PME_EINVAL, "n out of range");
+    DeviceGuard g(pl->dev);
+    return plan_reserve(pl, n);
+}
+
+pme_status pme_enqueue(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *ev_dev) {
+    pme_status st = check_atoms(pl, pos, q, n, forces);
+    if (st) return st;
+    DeviceGuard g(pl->dev);
+    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
+    const SysDev d = plan_descriptor(pl, pos, q, n, forces, ev_dev);
+    cudaError_t e = launch_pipeline(d, pl->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return PME_OK;
+}
+
+pme_status pme_sync(pme_plan *pl) {
+    if (!pl) return fail(PME_EINVAL, "plan is NULL");
+    DeviceGuard g(pl->dev);
+    return collect_status(pl, false);
+}
+
+pme_status pme_compute(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *energy,
+                       double *virial) {
+    return pme_compute_debug(pl, pos, q, n, forces, energy, virial, nullptr, nullptr);
+}
+
+pme_status pme_compute_debug(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *energy,
+                             double *virial, int64_t *mesh_dev, float *phi_dev) {
+    pme_status st = check_atoms(pl, pos, q, n, forces);
+    if (st) return st;
+    DeviceGuard g(pl->dev);
+    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
+    const SysDev d = plan_descriptor(pl, pos, q, n, forces, nullptr);
+    DebugTaps taps = {(unsigned long long *)mesh_dev, phi_dev};
+    cudaError_t e = launch_pipeline(d, pl->stream, (mesh_dev || phi_dev) ? &taps : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if ((e = cudaMemcpyAsync(pl->h_ctl, pl->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(result)");
+    if ((st = collect_status(pl, true)) != PME_OK) return st;
+    if (energy) *energy = pl->h_ctl->ev[0];
+    if (virial)
+        for (int c = 0; c < 6; ++c) virial[c] = pl->h_ctl->ev[1 + c];
+    return PME_OK;
+}
+
+pme_status pme_compute_host(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *energy,
+                            double *virial) {
+    pme_status st = check_atoms(pl, pos, q, n, forces);
+    if (st) return st;
+    DeviceGuard g(pl->dev);
+    cudaError_t e;
+    if (n > pl->host_cap) {
+        if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        if (pl->host_mem) cudaFree(pl->host_mem);
+        pl->host_mem = nullptr;
+        pl->host_cap = 0;
+        const size_t bytes = align256((size_t)n * 12) * 2 + align256((size_t)n * 4);
+        if ((e = cudaMalloc(&pl->host_mem, bytes)) != cudaSuccess) {
+            pl->host_mem = nullptr;
+            return fail(PME_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        }
+        pl->host_cap = n;
+    }
+    char *b = (char *)pl->host_mem;
+    float *dpos = (float *)b, *dfor = (float *)(b + align256((size_t)pl->host_cap * 12));
+    float *dq = (float *)(b + 2 * align256((size_t)pl->host_cap * 12));
+    if (n > 0) {
+        if ((e = cudaMemcpyAsync(dpos, pos, (size_t)n * 12, cudaMemcpyHostToDevice, pl->stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(pos)");
+        if ((e = cudaMemcpyAsync(dq, q, (size_t)n * 4, cudaMemcpyHostToDevice, pl->stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(q)");
+    }
+    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
+    const SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, nullptr);
+    if ((e = launch_pipeline(d, pl->stream)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (n > 0 && (e = cudaMemcpyAsync(forces, dfor, (size_t)n * 12, cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(forces)");
+    if ((e = cudaMemcpyAsync(pl->h_ctl, pl->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(result)");
+    if ((st = collect_status(pl, true)) != PME_OK) return st;
+    if (energy) *energy = pl->h_ctl->ev[0];
+    if (virial)
+        for (int c = 0; c < 6; ++c) virial[c] = pl->h_ctl->ev[1 + c];
+    return PME_OK;
+}
+
+pme_status pme_profile_stages(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, int reps,
+                              double stage_us[6]) {
+    pme_status st = check_atoms(pl, pos, q, n, forces);
+    if (st) return st;
+    if (reps < 1 || !stage_us) return fail(PME_EINVAL, "reps must be >= 1 and stage_us non-NULL");
+    DeviceGuard g(pl->dev);
+    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
+    const SysDev d = plan_descriptor(pl, pos, q, n, forces, nullptr);
+    cudaEvent_t ev[NUM_STAGES + 1];
+    for (int i = 0; i <= NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
+    double acc[NUM_STAGES] = {0};
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        for (int s = 0; s < NUM_STAGES; ++s) {
+            cudaEventRecord(ev[s], pl->stream);
+            launch_stage(d, s, pl->stream);
+        }
+        cudaEventRecord(ev[NUM_STAGES], pl->stream);
+        if ((e = cudaEventSynchronize(ev[NUM_STAGES])) != cudaSuccess) break;
+        for (int s = 0; s < NUM_STAGES; ++s) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+            acc[s] += ms;
+        }
+    }
+    for (int i = 0; i <= NUM_STAGES; ++i) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "profiled launch");
+    for (int s = 0; s < NUM_STAGES; ++s) stage_us[s] = 1000.0 * acc[s] / reps;
+    return collect_status(pl, false);
+}
+
+size_t pme_plan_device_bytes(const pme_plan *pl) {
+    return pl ? pl->mesh_bytes + pl->atom_bytes + (pl->host_mem ? align256((size_t)pl->host_cap * 12) * 2 +
+                                                                          align256((size_t)pl->host_cap * 4)
+                                                                    : 0)
+              : 0;
+}
+
+void pme_destroy(pme_plan *pl) {
+    if (!pl) return;
+    DeviceGuard g(pl->dev);
+    cudaStreamSynchronize(pl->stream);
+    if (pl->mesh_mem) cudaFree(pl->mesh_mem);
+    if (pl->atom_mem) cudaFree(pl->atom_mem);
+    if (pl->host_mem) cudaFree(pl->host_mem);
+    if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
+    delete pl;
+}
+
+}  // extern "C"

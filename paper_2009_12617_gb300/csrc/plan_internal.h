@@ -1,0 +1,48 @@
+// Internal definition of pme_plan and helpers shared by the plan, batch and server code.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/pme.h"
+#include "common.cuh"
+
+struct pme_plan {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int K[3] = {0, 0, 0};
+    int p = 0;
+    double beta = 0.0;
+    double box[9] = {0};
+    double recip[9] = {0};
+    double vol = 0.0;
+    pme::SysDev d;                  // descriptor of the resident device state (atom fields unset)
+    void *mesh_mem = nullptr;       // mesh, spectrum, potential, tables, counters (fixed per plan)
+    size_t mesh_bytes = 0;
+    void *atom_mem = nullptr;       // tile buckets and overflow list (grows with n)
+    size_t atom_bytes = 0;
+    int64_t n_cap = 0;
+    void *host_mem = nullptr;       // device staging for pme_compute_host
+    int64_t host_cap = 0;
+    pme::Ctl *h_ctl = nullptr;      // pinned host copy of the control block
+};
+
+namespace pme {
+
+pme_status fail(pme_status s, const char *fmt, ...);
+pme_status cuda_fail(cudaError_t e, const char *what);
+pme_status status_from_bits(unsigned bits);
+pme_status plan_reserve(pme_plan *pl, int64_t n);
+pme_status check_atoms(const pme_plan *pl, const float *pos, const float *q, int64_t n, const float *forces);
+SysDev plan_descriptor(const pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *ev_dev);
+cudaError_t ensure_configured(int dev);
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+
+   private:
+    int prev_ = 0, dev_ = 0;
+};
+
+}  // namespace pme

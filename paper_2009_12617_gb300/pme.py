@@ -1,0 +1,328 @@
+"""Thin Python binding of the C ABI in include/pme.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls, and every step of the SPME evaluation runs
+in the CUDA library ``libpme_gb300.so``. Array arguments are torch CUDA tensors (float32, contiguous; the
+library reads their device pointers) except in ``pme_compute_host``, which takes host numpy arrays.
+There is no CPU fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PME_OK = 0
+PME_EINVAL = 1
+PME_EUNSUPPORTED = 2
+PME_ENOMEM = 3
+PME_ECUDA = 4
+PME_EOVERFLOW = 5
+PME_EAGAIN = 6
+PME_ETIMEOUT = 7
+PME_PENDING = 8
+
+STATUS_NAMES = {0: "PME_OK", 1: "PME_EINVAL", 2: "PME_EUNSUPPORTED", 3: "PME_ENOMEM", 4: "PME_ECUDA",
+                5: "PME_EOVERFLOW", 6: "PME_EAGAIN", 7: "PME_ETIMEOUT", 8: "PME_PENDING"}
+
+# every symbol include/pme.h declares
+EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme_enqueue", "pme_reserve", "pme_sync", "pme_compute_host",
+           "pme_profile_stages", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
+           "pme_batch_destroy", "pme_server_create", "pme_submit", "pme_poll", "pme_server_stats",
+           "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall")
+
+
+class PMEError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {detail}")
+        self.status = status
+        self.detail = detail
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_st = ctypes.c_int
+
+
+def load_library(path: str | None = None):
+    """Load libpme_gb300.so (built by __graft_entry__.build() / paper_2009_12617_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "pme_create": (_st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp, ctypes.POINTER(_vp)]),
+        "pme_set_box": (_st, [_vp, ctypes.POINTER(ctypes.c_double)]),
+        "pme_compute": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "pme_compute_debug": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+        "pme_enqueue": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
+        "pme_reserve": (_st, [_vp, _i64]),
+        "pme_sync": (_st, [_vp]),
+        "pme_compute_host": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "pme_profile_stages": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "pme_plan_device_bytes": (ctypes.c_size_t, [_vp]),
+        "pme_destroy": (None, [_vp]),
+        "pme_batch_create": (_st, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp, ctypes.POINTER(_vp)]),
+        "pme_batch_enqueue": (_st, [_vp, _vp, _vp, _vp, _vp]),
+        "pme_batch_sync": (_st, [_vp]),
+        "pme_batch_destroy": (None, [_vp]),
+        "pme_batch_debug_stall": (_st, [_vp, ctypes.c_int, _i64]),
+        "pme_server_create": (_st, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
+        "pme_submit": (_st, [_vp, _vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
+        "pme_poll": (_st, [_vp, _i64, ctypes.c_int]),
+        "pme_server_stats": (_st, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
+        "pme_server_destroy": (None, [_vp]),
+        "pme_strerror": (ctypes.c_char_p, [_st]),
+        "pme_last_error_detail": (_st, [ctypes.c_char_p, ctypes.c_size_t]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error_detail() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load_library().pme_last_error_detail(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int) -> int:
+    if status != PME_OK and status != PME_PENDING:
+        raise PMEError(status, last_error_detail())
+    return status
+
+
+def _ptr(t) -> int:
+    """Device pointer of a CUDA tensor (float32, contiguous), or 0 for None."""
+    if t is None:
+        return 0
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _f32(t, shape_tail, name):
+    import torch
+
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if tuple(t.shape[1:]) != shape_tail:
+        raise ValueError(f"{name} has shape {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+# ---------------------------------------------------------------------------------------------------------
+# C entry points (same names as include/pme.h)
+
+
+def pme_create(K, p: int, beta: float, box, stream=None) -> int:
+    K = (ctypes.c_int * 3)(*[int(k) for k in K])
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    out = _vp()
+    check(load_library().pme_create(K, int(p), float(beta), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    _vp(_stream_handle(stream)), ctypes.byref(out)))
+    return out.value
+
+
+def pme_set_box(plan: int, box) -> None:
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    check(load_library().pme_set_box(_vp(plan), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def pme_compute(plan: int, pos, q, forces) -> tuple[float, np.ndarray]:
+    """Synchronous evaluation on torch CUDA tensors pos (n,3), q (n,), forces (n,3); returns (E, virial[6])."""
+    n = int(q.shape[0])
+    e = ctypes.c_double()
+    vir = (ctypes.c_double * 6)()
+    check(load_library().pme_compute(_vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), n,
+                                     _vp(_f32(forces, (3,), "forces")), ctypes.byref(e), vir))
+    return e.value, np.array(vir[:])
+
+
+def pme_compute_debug(plan: int, pos, q, forces, mesh=None, phi=None) -> tuple[float, np.ndarray]:
+    """pme_compute that also copies the fixed-point charge mesh (int64 CUDA tensor of shape K) and the
+    potential mesh (float32 CUDA tensor of shape K) into mesh / phi when given."""
+    n = int(q.shape[0])
+    e = ctypes.c_double()
+    vir = (ctypes.c_double * 6)()
+    check(load_library().pme_compute_debug(_vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), n,
+                                           _vp(_f32(forces, (3,), "forces")), ctypes.byref(e), vir,
+                                           _vp(_ptr(mesh)), _vp(_ptr(phi))))
+    return e.value, np.array(vir[:])
+
+
+def pme_enqueue(plan: int, pos, q, forces, ev_dev=None) -> None:
+    """Asynchronous evaluation; ev_dev is a float64 CUDA tensor of 7 (or None for the plan's own slot)."""
+    n = int(q.shape[0])
+    check(load_library().pme_enqueue(_vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), n,
+                                     _vp(_f32(forces, (3,), "forces")), _vp(_ptr(ev_dev))))
+
+
+def pme_reserve(plan: int, n: int) -> None:
+    check(load_library().pme_reserve(_vp(plan), int(n)))
+
+
+def pme_sync(plan: int) -> None:
+    check(load_library().pme_sync(_vp(plan)))
+
+
+def pme_compute_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray | None = None):
+    """Evaluation on HOST numpy arrays (float32); returns (forces, E, virial[6])."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    n = int(q.shape[0])
+    if pos.shape != (n, 3):
+        raise ValueError("pos must be (n, 3)")
+    if forces is None:
+        forces = np.empty((n, 3), dtype=np.float32)
+    if forces.dtype != np.float32 or forces.shape != (n, 3) or not forces.flags.c_contiguous:
+        raise ValueError("forces must be a contiguous float32 (n, 3) array")
+    e = ctypes.c_double()
+    vir = (ctypes.c_double * 6)()
+    check(load_library().pme_compute_host(_vp(plan), _vp(pos.ctypes.data), _vp(q.ctypes.data), n,
+                                          _vp(forces.ctypes.data), ctypes.byref(e), vir))
+    return forces, e.value, np.array(vir[:])
+
+
+STAGE_NAMES = ("bin", "spread", "fft_fwd", "influence", "fft_inv", "gather")
+
+
+def pme_profile_stages(plan: int, pos, q, forces, reps: int = 10) -> dict:
+    """Mean microseconds per stage kernel (CUDA events on the plan stream) over reps evaluations."""
+    out = (ctypes.c_double * 6)()
+    check(load_library().pme_profile_stages(_vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")),
+                                            int(q.shape[0]), _vp(_f32(forces, (3,), "forces")), int(reps), out))
+    return dict(zip(STAGE_NAMES, out[:]))
+
+
+def pme_plan_device_bytes(plan: int) -> int:
+    return int(load_library().pme_plan_device_bytes(_vp(plan)))
+
+
+def pme_destroy(plan: int) -> None:
+    if plan:
+        load_library().pme_destroy(_vp(plan))
+
+
+def pme_batch_create(plans, n, stream=None) -> int:
+    arr = (_vp * len(plans))(*[_vp(p) for p in plans])
+    ns = (_i64 * len(n))(*[int(x) for x in n])
+    out = _vp()
+    check(load_library().pme_batch_create(len(plans), arr, ns, _vp(_stream_handle(stream)), ctypes.byref(out)))
+    return out.value
+
+
+def pme_batch_enqueue(batch: int, pos, q, forces, ev_dev) -> None:
+    check(load_library().pme_batch_enqueue(_vp(batch), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")),
+                                           _vp(_f32(forces, (3,), "forces")), _vp(_ptr(ev_dev))))
+
+
+def pme_batch_sync(batch: int) -> int:
+    return check(load_library().pme_batch_sync(_vp(batch)))
+
+
+def pme_batch_destroy(batch: int) -> None:
+    if batch:
+        load_library().pme_batch_destroy(_vp(batch))
+
+
+def pme_batch_debug_stall(batch: int, enable: bool, wait_limit_ns: int = 200_000_000) -> None:
+    check(load_library().pme_batch_debug_stall(_vp(batch), int(bool(enable)), int(wait_limit_ns)))
+
+
+def pme_server_create(mem_budget_bytes: int, max_slots: int) -> int:
+    out = _vp()
+    check(load_library().pme_server_create(int(mem_budget_bytes), int(max_slots), ctypes.byref(out)))
+    return out.value
+
+
+class Ticket:
+    """A submitted request: keeps the host result slots alive until the request completes."""
+
+    def __init__(self):
+        self.id = _i64()
+        self.energy = ctypes.c_double()
+        self.virial = (ctypes.c_double * 6)()
+
+
+def pme_submit(srv: int, plan: int, pos, q, forces) -> Ticket:
+    t = Ticket()
+    st = load_library().pme_submit(_vp(srv), _vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")),
+                                   int(q.shape[0]), _vp(_f32(forces, (3,), "forces")), ctypes.byref(t.energy),
+                                   t.virial, ctypes.byref(t.id))
+    if st == PME_EAGAIN:
+        return None
+    check(st)
+    return t
+
+
+def pme_poll(srv: int, ticket: Ticket, block: bool = False) -> int:
+    return check(load_library().pme_poll(_vp(srv), ticket.id.value, int(bool(block))))
+
+
+def pme_server_stats(srv: int) -> dict:
+    c, w = _i64(), _i64()
+    p50, p99 = ctypes.c_double(), ctypes.c_double()
+    check(load_library().pme_server_stats(_vp(srv), ctypes.byref(c), ctypes.byref(p50), ctypes.byref(p99),
+                                          ctypes.byref(w)))
+    return {"completed": c.value, "p50_us": p50.value, "p99_us": p99.value, "waves": w.value}
+
+
+def pme_server_destroy(srv: int) -> None:
+    if srv:
+        load_library().pme_server_destroy(_vp(srv))
+
+
+def pme_strerror(status: int) -> str:
+    return load_library().pme_strerror(int(status)).decode()
+
+
+# ---------------------------------------------------------------------------------------------------------
+# convenience wrapper
+
+
+class Plan:
+    """Owns a pme_plan: Plan(K, p, beta, box, stream=None)."""
+
+    def __init__(self, K, p: int, beta: float, box, stream=None):
+        self.K = tuple(int(k) for k in K)
+        self.p = int(p)
+        self.beta = float(beta)
+        self.handle = pme_create(self.K, self.p, self.beta, box, stream)
+
+    def compute(self, pos, q, forces=None):
+        import torch
+
+        if forces is None:
+            forces = torch.empty_like(pos)
+        e, vir = pme_compute(self.handle, pos, q, forces)
+        return forces, e, vir
+
+    def enqueue(self, pos, q, forces, ev_dev=None):
+        pme_enqueue(self.handle, pos, q, forces, ev_dev)
+
+    def close(self):
+        if self.handle:
+            pme_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every symbol include/pme.h declares; argument validation
+that needs no GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2009_12617_gb300 import build, pme
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return pme.load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pme.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pme_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declarations_match_binding():
+    assert sorted(pme.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {build.library_path()}").read()
+    for name in _declared():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def test_strerror(lib):
+    for s in range(9):
+        assert pme.pme_strerror(s)
+    assert pme.pme_strerror(0) == "ok"
+
+
+@pytest.mark.parametrize("K,p,beta,expect", [
+    ((14, 16, 16), 4, 0.3, pme.PME_EINVAL),    # 7 is not an allowed prime factor
+    ((15, 16, 16), 4, 0.3, pme.PME_EINVAL),    # odd edge
+    ((6, 16, 16), 4, 0.3, pme.PME_EINVAL),     # below 8
+    ((256, 16, 16), 4, 0.3, pme.PME_EINVAL),   # above 128
+    ((16, 16, 16), 5, 0.3, pme.PME_EUNSUPPORTED),  # odd order
+    ((16, 16, 16), 2, 0.3, pme.PME_EUNSUPPORTED),
+    ((16, 16, 16), 10, 0.3, pme.PME_EUNSUPPORTED),
+    ((16, 16, 16), 4, 0.0, pme.PME_EINVAL),
+    ((16, 16, 16), 4, float("nan"), pme.PME_EINVAL),
+])
+def test_create_validation(lib, K, p, beta, expect):
+    with pytest.raises(pme.PMEError) as ei:
+        pme.pme_create(K, p, beta, np.eye(3) * 20.0)
+    assert ei.value.status == expect
+    assert ei.value.detail
+
+
+def test_create_singular_box(lib):
+    box = np.array([[10.0, 0, 0], [20.0, 0, 0], [0, 0, 10.0]])
+    with pytest.raises(pme.PMEError) as ei:
+        pme.pme_create((16, 16, 16), 4, 0.3, box)
+    assert ei.value.status == pme.PME_EINVAL
+
+
+def test_null_arguments(lib):
+    out = ctypes.c_void_p()
+    assert lib.pme_create(None, 4, 0.3, None, None, ctypes.byref(out)) == pme.PME_EINVAL
+    assert lib.pme_compute(None, None, None, 0, None, None, None) == pme.PME_EINVAL
+    assert lib.pme_sync(None) == pme.PME_EINVAL
+    lib.pme_destroy(None)

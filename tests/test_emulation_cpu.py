@@ -1,0 +1,90 @@
+"""The library's stage bodies, compiled for the CPU with one thread per CTA (tests/emu), against the FP64
+oracle: checks the index arithmetic, FFT plumbing, influence table and reductions without a GPU. The
+tolerances are the ones the GPU parity tests use."""
+import numpy as np
+import pytest
+
+from paper_2009_12617_gb300 import workloads as wl
+
+from helpers import (E_REL_TOL, F_RMS_TOL, PHI_TOL, V_TOL, build_emu, emu_spme, mesh_error_ok, rel_energy,
+                     rel_virial, rms_force)
+
+
+@pytest.fixture(scope="module")
+def emu():
+    return build_emu()
+
+
+CASES = [
+    ((32, 32, 32), 4),   # the 2048-atom parity workload
+    ((20, 24, 30), 6),   # radix 5 / 3 / mixed, ragged tiles
+    ((32, 40, 48), 8),
+    ((10, 12, 18), 4),   # small ragged meshes (tiles of 8 with tails of 2, 4, 2)
+    ((8, 8, 8), 8),      # the p - 1 halo wraps onto the same tile
+]
+
+
+@pytest.mark.parametrize("K,p", CASES)
+def test_emulated_pipeline_matches_oracle(oracle_mod, emu, K, p):
+    s = wl.parity_system()
+    n = 2048 if min(K) >= 20 else 300
+    pos, q = s.pos[:n], s.q[:n].copy()
+    q[-1] -= q.sum()  # keep the subset neutral
+    st, F, ev, mesh, phi = emu_spme(emu, pos, q, K, p, 0.34, s.box)
+    assert st == 0
+    r = oracle_mod.spme(pos.astype(float), q.astype(float), K, p, 0.34, s.box, want_mesh=True)
+    assert rel_energy(ev[0], r["energy"]) < E_REL_TOL
+    assert rms_force(F, r["forces"]) < F_RMS_TOL
+    assert rel_virial(ev[1:], r["virial"]) < V_TOL
+    ok, worst = mesh_error_ok(mesh, r["Q"], oracle_mod.spread(pos.astype(float), np.abs(q.astype(float)), K, p, s.box))
+    assert ok, worst
+    assert np.abs(phi - r["phi"]).max() < PHI_TOL * np.abs(r["phi"]).max()
+
+
+def test_emulated_triclinic(oracle_mod, emu):
+    s = wl.parity_system()
+    box = np.array([[27.4, 0, 0], [3.1, 26.0, 0], [-2.0, 4.0, 28.0]])
+    st, F, ev, _, _ = emu_spme(emu, s.pos, s.q, (30, 32, 36), 6, 0.34, box)
+    r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), (30, 32, 36), 6, 0.34, box)
+    assert st == 0
+    assert rel_energy(ev[0], r["energy"]) < E_REL_TOL
+    assert rms_force(F, r["forces"]) < F_RMS_TOL
+    assert rel_virial(ev[1:], r["virial"]) < V_TOL
+
+
+def test_emulated_overflow_path_and_repeat(oracle_mod, emu):
+    """Tiny bucket capacity sends most atoms down the overflow path; two evaluations in a row must agree
+    bit for bit (every counter and the int64 mesh are reset by their consumers; status 0x100 flags a
+    leftover)."""
+    s = wl.parity_system()
+    st1, F1, ev1, m1, _ = emu_spme(emu, s.pos, s.q, (32, 32, 32), 4, 0.34, s.box, cap=32, repeat=1)
+    st2, F2, ev2, m2, _ = emu_spme(emu, s.pos, s.q, (32, 32, 32), 4, 0.34, s.box, cap=0, repeat=3)
+    assert st1 == 0 and st2 == 0
+    assert np.array_equal(m1, m2)
+    r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), (32, 32, 32), 4, 0.34, s.box)
+    for F, ev in ((F1, ev1), (F2, ev2)):
+        assert rel_energy(ev[0], r["energy"]) < E_REL_TOL
+        assert rms_force(F, r["forces"]) < F_RMS_TOL
+
+
+def test_emulated_mesh_permutation_invariant(emu):
+    """The fixed-point mesh does not depend on the order the atoms are given in."""
+    s = wl.parity_system()
+    perm = np.random.default_rng(3).permutation(s.n)
+    _, F1, ev1, m1, _ = emu_spme(emu, s.pos, s.q, (32, 32, 32), 4, 0.34, s.box)
+    _, F2, ev2, m2, _ = emu_spme(emu, s.pos[perm], s.q[perm], (32, 32, 32), 4, 0.34, s.box)
+    assert np.array_equal(m1, m2)
+    assert ev1[0] == ev2[0]
+    assert np.array_equal(F1[perm], F2)
+
+
+def test_emulated_invalid_inputs(emu):
+    s = wl.parity_system()
+    pos = s.pos.copy()
+    pos[5, 1] = np.nan
+    st, F, _, _, _ = emu_spme(emu, pos, s.q, (32, 32, 32), 4, 0.34, s.box)
+    assert st & 1 and np.isnan(F[5]).all()
+    q = s.q.copy()
+    q[:] = 3000.0  # sum |q| = 6.1e6 e > 2^22
+    st, _, _, _, _ = emu_spme(emu, s.pos, q, (32, 32, 32), 4, 0.34, s.box)
+    assert st & 2

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA pipeline, called through the C ABI, against the FP64 oracle on the same seeded inputs.
+
+Tolerances (tests/helpers.py): relative energy 1e-6, RMS force 1e-5 of RMS force, virial 1e-5 of max |Pi|,
+charge mesh pointwise within 1e-6 of the |q| mesh plus the 2^-40 quantum, phi 1e-5 of max |phi|; the
+fixed-point mesh bit-exact run to run and under any permutation of the atoms.
+"""
+import numpy as np
+import pytest
+
+from paper_2009_12617_gb300 import workloads as wl
+
+from helpers import (E_REL_TOL, F_RMS_TOL, PHI_TOL, V_TOL, mesh_error_ok, rel_energy, rel_virial, rms_force)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pmelib():
+    from paper_2009_12617_gb300 import build, pme
+
+    build.build_library()
+    pme.load_library()
+    assert torch.cuda.is_available()
+    return pme
+
+
+def gpu_eval(pme, plan, pos, q, K=None, taps=False):
+    dev = torch.device("cuda:0")
+    pos_d = torch.from_numpy(np.ascontiguousarray(pos, np.float32)).to(dev)
+    q_d = torch.from_numpy(np.ascontiguousarray(q, np.float32)).to(dev)
+    F = torch.full_like(pos_d, float("nan"))
+    mesh = torch.zeros(tuple(K), dtype=torch.int64, device=dev) if taps else None
+    phi = torch.zeros(tuple(K), dtype=torch.float32, device=dev) if taps else None
+    E, vir = pme.pme_compute_debug(plan, pos_d, q_d, F, mesh, phi)
+    out = {"energy": E, "virial": vir, "forces": F.cpu().numpy()}
+    if taps:
+        out["mesh"] = mesh.cpu().numpy()
+        out["phi"] = phi.cpu().numpy()
+    return out
+
+
+def check_against_oracle(oracle_mod, g, pos, q, K, p, beta, box, taps=True):
+    r = oracle_mod.spme(np.asarray(pos, np.float64), np.asarray(q, np.float64), K, p, beta, box, want_mesh=taps)
+    assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL, (g["energy"], r["energy"])
+    assert rms_force(g["forces"], r["forces"]) < F_RMS_TOL
+    assert rel_virial(g["virial"], r["virial"]) < V_TOL
+    if taps:
+        Qabs = oracle_mod.spread(np.asarray(pos, np.float64), np.abs(np.asarray(q, np.float64)), K, p, box)
+        ok, worst = mesh_error_ok(g["mesh"], r["Q"], Qabs)
+        assert ok, worst
+        assert np.abs(g["phi"] - r["phi"]).max() < PHI_TOL * np.abs(r["phi"]).max()
+    return r
+
+
+def test_parity_config1(pmelib, oracle_mod):
+    """2048 atoms (682 water-like triplets + one ion pair), 27.4 A cubic box, 32^3, p = 4, beta = 0.34."""
+    s = wl.parity_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        g = gpu_eval(pmelib, plan, s.pos, s.q, s.K, taps=True)
+        check_against_oracle(oracle_mod, g, s.pos, s.q, s.K, s.p, s.beta, s.box)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+SHAPES = [((8, 10, 12), 4), ((16, 18, 20), 6), ((24, 30, 32), 8), ((36, 40, 48), 4), ((50, 54, 60), 6),
+          ((64, 72, 80), 4), ((90, 96, 100), 4), ((108, 120, 128), 6), ((40, 40, 40), 8), ((8, 8, 8), 8)]
+
+
+@pytest.mark.parametrize("K,p", SHAPES, ids=[f"{K[0]}x{K[1]}x{K[2]}_p{p}" for K, p in SHAPES])
+def test_parity_mesh_shapes(pmelib, oracle_mod, K, p):
+    """Every radix-2/3/5 length from 8 to 128 in some dimension, ragged tiles, orders 4, 6 and 8."""
+    L = np.array(K, dtype=float) * 1.1
+    box = np.diag(L)
+    n = 3000
+    rng = np.random.default_rng(sum(K) + p)
+    pos = (rng.random((n, 3)) * L).astype(np.float32)
+    q = rng.normal(size=n)
+    q -= q.mean()
+    q = q.astype(np.float32)
+    plan = pmelib.pme_create(K, p, 0.34, box)
+    try:
+        g = gpu_eval(pmelib, plan, pos, q, K, taps=True)
+        check_against_oracle(oracle_mod, g, pos, q, K, p, 0.34, box)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_parity_triclinic(pmelib, oracle_mod):
+    s = wl.parity_system()
+    box = np.array([[27.4, 0, 0], [3.1, 26.0, 0], [-2.0, 4.0, 28.0]])
+    plan = pmelib.pme_create((30, 32, 36), 6, 0.34, box)
+    try:
+        g = gpu_eval(pmelib, plan, s.pos, s.q, (30, 32, 36), taps=True)
+        check_against_oracle(oracle_mod, g, s.pos, s.q, (30, 32, 36), 6, 0.34, box)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_parity_full_size_headline(pmelib, oracle_mod):
+    """65536 atoms, 86.9 A, 64^3, p = 4 (the paper-sized system), every output against the oracle."""
+    s = wl.headline_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        g = gpu_eval(pmelib, plan, s.pos, s.q, s.K, taps=True)
+        check_against_oracle(oracle_mod, g, s.pos, s.q, s.K, s.p, s.beta, s.box)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_parity_full_size_large(pmelib, oracle_mod):
+    """262144 atoms, 137.9 A, 128^3, p = 6: energy, virial, all forces and both meshes."""
+    s = wl.large_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        g = gpu_eval(pmelib, plan, s.pos, s.q, s.K, taps=True)
+        check_against_oracle(oracle_mod, g, s.pos, s.q, s.K, s.p, s.beta, s.box)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_mesh_bit_exact_repeat_and_permutation(pmelib):
+    """The int64 charge mesh is bit-identical over repeated runs and any input order; so is everything
+    downstream (no floating-point atomics anywhere)."""
+    s = wl.headline_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        g0 = gpu_eval(pmelib, plan, s.pos, s.q, s.K, taps=True)
+        for _ in range(3):
+            g = gpu_eval(pmelib, plan, s.pos, s.q, s.K, taps=True)
+            assert np.array_equal(g["mesh"], g0["mesh"])
+            assert g["energy"] == g0["energy"] and np.array_equal(g["virial"], g0["virial"])
+            assert np.array_equal(g["forces"], g0["forces"])
+        perm = np.random.default_rng(9).permutation(s.n)
+        gp = gpu_eval(pmelib, plan, s.pos[perm], s.q[perm], s.K, taps=True)
+        assert np.array_equal(gp["mesh"], g0["mesh"])
+        assert gp["energy"] == g0["energy"]
+        assert np.array_equal(gp["forces"], g0["forces"][perm])
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_empty_single_and_wrapped(pmelib, oracle_mod):
+    box = np.diag([20.0, 21.0, 22.0])
+    plan = pmelib.pme_create((20, 24, 24), 4, 0.34, box)
+    try:
+        g = gpu_eval(pmelib, plan, np.zeros((0, 3), np.float32), np.zeros(0, np.float32))
+        assert g["energy"] == 0.0 and np.all(g["virial"] == 0.0)
+        one = np.array([[3.3, 4.4, 5.5]], np.float32)
+        g = gpu_eval(pmelib, plan, one, np.array([1.0], np.float32))
+        r = oracle_mod.spme(one.astype(float), [1.0], (20, 24, 24), 4, 0.34, box)
+        assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL
+        # positions far outside the cell are wrapped (images of the parity system)
+        s = wl.parity_system()
+        shift = np.array([3 * 20.0, -5 * 21.0, 40 * 22.0], np.float32)
+        g = gpu_eval(pmelib, plan, s.pos[:500] + shift, s.q[:500])
+        r = oracle_mod.spme(s.pos[:500].astype(float) + shift.astype(float), s.q[:500].astype(float), (20, 24, 24), 4,
+                            0.34, box)
+        assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL
+        assert rms_force(g["forces"], r["forces"]) < F_RMS_TOL
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_clustered_atoms_use_overflow_path(pmelib, oracle_mod):
+    """Every atom inside one spread tile: the tile's bucket overflows and the global-memory paths run."""
+    rng = np.random.default_rng(21)
+    box = np.diag([30.0, 30.0, 30.0])
+    pos = (10.0 + rng.random((4000, 3)) * 1.5).astype(np.float32)
+    q = rng.normal(size=4000)
+    q -= q.mean()
+    q = q.astype(np.float32)
+    plan = pmelib.pme_create((32, 32, 32), 4, 0.34, box)
+    try:
+        g = gpu_eval(pmelib, plan, pos, q, (32, 32, 32), taps=True)
+        check_against_oracle(oracle_mod, g, pos, q, (32, 32, 32), 4, 0.34, box)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_host_pointer_path(pmelib, oracle_mod):
+    s = wl.parity_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        F, E, vir = pmelib.pme_compute_host(plan, s.pos, s.q)
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
+        assert rel_energy(E, r["energy"]) < E_REL_TOL
+        assert rms_force(F, r["forces"]) < F_RMS_TOL
+        assert rel_virial(vir, r["virial"]) < V_TOL
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_enqueue_in_cuda_graph(pmelib):
+    """pme_enqueue allocates nothing after pme_reserve, so a torch CUDA graph can capture it; replays give
+    the synchronous result bit for bit."""
+    s = wl.parity_system()
+    stream = torch.cuda.Stream()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
+    try:
+        pos = torch.from_numpy(s.pos).cuda()
+        q = torch.from_numpy(s.q).cuda()
+        F_ref = torch.empty_like(pos)
+        with torch.cuda.stream(stream):
+            E_ref, vir_ref = pmelib.pme_compute(plan, pos, q, F_ref)
+            pmelib.pme_reserve(plan, s.n)
+            F = torch.empty_like(pos)
+            ev = torch.zeros(7, dtype=torch.float64, device="cuda")
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                pmelib.pme_enqueue(plan, pos, q, F, ev)
+            for _ in range(3):
+                graph.replay()
+            pmelib.pme_sync(plan)
+        assert torch.equal(F, F_ref)
+        assert ev[0].item() == E_ref and np.array_equal(ev[1:].cpu().numpy(), vir_ref)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_set_box(pmelib, oracle_mod):
+    s = wl.parity_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        box2 = s.box * 1.03
+        pmelib.pme_set_box(plan, box2)
+        g = gpu_eval(pmelib, plan, s.pos, s.q)
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, box2)
+        assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL
+        assert rms_force(g["forces"], r["forces"]) < F_RMS_TOL
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_invalid_inputs_report_and_recover(pmelib, oracle_mod):
+    s = wl.parity_system()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        pos = s.pos.copy()
+        pos[7, 2] = np.inf
+        with pytest.raises(pmelib.PMEError) as ei:
+            gpu_eval(pmelib, plan, pos, s.q)
+        assert ei.value.status == pmelib.PME_EINVAL
+        q = np.full(s.n, 3000.0, np.float32)  # sum |q| = 6.1e6 e >= 2^22
+        with pytest.raises(pmelib.PMEError) as ei:
+            gpu_eval(pmelib, plan, s.pos, q)
+        assert ei.value.status == pmelib.PME_EOVERFLOW
+        # the plan is still usable and exact afterwards
+        g = gpu_eval(pmelib, plan, s.pos, s.q)
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
+        assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL
+    finally:
+        pmelib.pme_destroy(plan)
