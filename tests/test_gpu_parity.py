@@ -154,9 +154,9 @@ def test_empty_single_and_wrapped(pmelib, oracle_mod):
         # positions far outside the cell are wrapped (images of the parity system)
         s = wl.parity_system()
         shift = np.array([3 * 20.0, -5 * 21.0, 40 * 22.0], np.float32)
-        g = gpu_eval(pmelib, plan, s.pos[:500] + shift, s.q[:500])
-        r = oracle_mod.spme(s.pos[:500].astype(float) + shift.astype(float), s.q[:500].astype(float), (20, 24, 24), 4,
-                            0.34, box)
+        far = (s.pos[:500] + shift).astype(np.float32)  # the same FP32 inputs go to both sides
+        g = gpu_eval(pmelib, plan, far, s.q[:500])
+        r = oracle_mod.spme(far.astype(float), s.q[:500].astype(float), (20, 24, 24), 4, 0.34, box)
         assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL
         assert rms_force(g["forces"], r["forces"]) < F_RMS_TOL
     finally:
