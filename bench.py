@@ -154,12 +154,19 @@ def measured_peaks():
 
 
 def traffic_record(stage: str):
-    """ncu DRAM bytes per launch for the stage's kernel, from the committed profile summary (or None)."""
+    """ncu DRAM bytes per launch of the stage's kernel from the committed capture summary, or None when the
+    kernel sources changed since the counters were taken (or no capture exists)."""
+    import hashlib
+
     path = os.path.join(ROOT, "profiles", "dram_bytes.json")
     try:
         with open(path) as f:
-            return json.load(f).get(stage)
-    except (OSError, ValueError):
+            rec = json.load(f)
+        sha = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["source_files"])).hexdigest()
+        if sha != rec["source_sha256"]:
+            return None
+        return rec["bytes_per_launch"].get(stage)
+    except (OSError, ValueError, KeyError):
         return None
 
 
