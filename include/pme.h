@@ -122,6 +122,24 @@ size_t pme_plan_device_bytes(const pme_plan *plan);
 
 void pme_destroy(pme_plan *plan);
 
+/* Allocation-free evaluation of one small system, for callers that must not allocate device memory:
+ * applications that gave all device memory to their own pool at start-up (nothing may be left for
+ * cudaMalloc), and latency-bound callers that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree imply. The paper has no counterpart; it is an interface for such callers.
+ * The caller passes only inputs and outputs, as in pme_compute (device pos, q, forces; host energy and
+ * virial, either may be NULL); K, p, beta and box follow the pme_create rules. Everything else (meshes,
+ * spectrum, influence table, recomputed on the device every call, bucket lists, counters) lives in one
+ * static device array of 4 MiB that every GPU loading the library holds until the process exits.
+ * Limits: K1*K2*K3 <= 32768 with each K_alpha <= 64, n <= 16384, and the carved scratch must fit in 4 MiB;
+ * anything larger returns PME_EINVAL with the reason. One cooperative kernel launch on cuda_stream, then the
+ * call waits for it. The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and the cooperative grid size, so make that first call before any stream capture. Every call starts by
+ * clearing the parts of the array that must be zero, but all calls share the one array: calls that overlap
+ * on the GPU (from different streams or threads) race and give wrong results. */
+pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double box[9], const float *pos,
+                               const float *q, int64_t n, float *forces, double *energy, double *virial,
+                               void *cuda_stream);
+
 /* ------------------------------------------------------------------------------------------------------ */
 /* Batched evaluation: many independent systems in ONE persistent kernel launch                            */
 

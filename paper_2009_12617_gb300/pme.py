@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "PME_OK", 1: "PME_EINVAL", 2: "PME_EUNSUPPORTED", 3: "PME_ENO
 EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme_enqueue", "pme_reserve", "pme_sync", "pme_compute_host",
            "pme_profile_stages", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
            "pme_batch_destroy", "pme_server_create", "pme_submit", "pme_poll", "pme_server_stats",
-           "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall")
+           "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall",
+           "pme_compute_noalloc")
 
 
 class PMEError(RuntimeError):
@@ -80,6 +81,7 @@ def load_library(path: str | None = None):
         "pme_server_destroy": (None, [_vp]),
         "pme_strerror": (ctypes.c_char_p, [_st]),
         "pme_last_error_detail": (_st, [ctypes.c_char_p, ctypes.c_size_t]),
+        "pme_compute_noalloc": (_st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -286,6 +288,20 @@ def pme_server_stats(srv: int) -> dict:
 def pme_server_destroy(srv: int) -> None:
     if srv:
         load_library().pme_server_destroy(_vp(srv))
+
+
+def pme_compute_noalloc(K, p: int, beta: float, box, pos, q, forces, stream=None) -> tuple[float, np.ndarray]:
+    """Allocation-free evaluation of one small system (see include/pme.h): the library allocates no device
+    memory for it, using a fixed static device array instead. Returns (E, virial[6]); forces filled."""
+    Kc = (ctypes.c_int * 3)(*[int(k) for k in K])
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    e = ctypes.c_double()
+    vir = (ctypes.c_double * 6)()
+    check(load_library().pme_compute_noalloc(Kc, int(p), float(beta), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), int(q.shape[0]),
+                                             _vp(_f32(forces, (3,), "forces")), ctypes.byref(e), vir,
+                                             _vp(_stream_handle(stream))))
+    return e.value, np.array(vir[:])
 
 
 def pme_strerror(status: int) -> str:
