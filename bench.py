@@ -394,9 +394,196 @@ def main():
         dist.close()
 
 
+def leg_batched(args, sampler):
+    """64 uneven water-like systems (atom counts log-uniform 1024..32768, meshes 32..48) evaluated in one
+    persistent launch per step, against one launch sequence per system (eager, and replayed from a graph)."""
+    import torch
+
+    from paper_2009_12617_gb300 import pme
+    from paper_2009_12617_gb300 import workloads as wl
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    systems = wl.batch_systems(64, seed=4)
+    stream = torch.cuda.Stream(dev)
+    plans = [pme.pme_create(s.K, s.p, s.beta, s.box, stream=stream) for s in systems]
+    ns = [s.n for s in systems]
+    pos = torch.from_numpy(np.concatenate([s.pos for s in systems])).to(dev)
+    q = torch.from_numpy(np.concatenate([s.q for s in systems])).to(dev)
+    F = torch.empty_like(pos)
+    ev = torch.zeros((len(systems), 7), dtype=torch.float64, device=dev)
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    b = pme.pme_batch_create(plans, ns, stream=stream)
+    st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    out = {}
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                pme.pme_batch_enqueue(b, pos, q, F, ev)
+            pme.pme_batch_sync(b)
+            t0 = time.time()
+            st.record(stream)
+            for _ in range(reps):
+                pme.pme_batch_enqueue(b, pos, q, F, ev)
+            en.record(stream)
+            torch.cuda.synchronize(dev)
+            sampler.window(t0, time.time())
+            pme.pme_batch_sync(b)
+            t_batch = st.elapsed_time(en) / reps  # ms per batch of 64
+            Fb, evb = F.clone(), ev.clone()
+            # one launch sequence per system, same stream
+            for i, pl in enumerate(plans):
+                pme.pme_reserve(pl, ns[i])
+            views = [(pos[offs[i]:offs[i + 1]], q[offs[i]:offs[i + 1]], F[offs[i]:offs[i + 1]], ev[i]) for i in range(len(plans))]
+            for i, pl in enumerate(plans):
+                pme.pme_enqueue(pl, *views[i])
+            torch.cuda.synchronize(dev)
+            st.record(stream)
+            for _ in range(reps):
+                for i, pl in enumerate(plans):
+                    pme.pme_enqueue(pl, *views[i])
+            en.record(stream)
+            torch.cuda.synchronize(dev)
+            t_eager = st.elapsed_time(en) / reps
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for i, pl in enumerate(plans):
+                    pme.pme_enqueue(pl, *views[i])
+            g.replay()
+            torch.cuda.synchronize(dev)
+            st.record(stream)
+            for _ in range(reps):
+                g.replay()
+            en.record(stream)
+            torch.cuda.synchronize(dev)
+            t_graph = st.elapsed_time(en) / reps
+            for pl in plans:
+                pme.pme_sync(pl)
+        same = bool(torch.equal(F, Fb) and torch.equal(ev, evb))
+        nsys, atoms = len(systems), int(sum(ns))
+        out = {"batched": {
+            "workload": "64 water-like boxes, N log-uniform in [1024, 32768] (seed 4), 0.1 atoms/A^3, K in {32,40,48,64} "
+                        "by 1.4 A spacing, p=4, one persistent launch per step (CUDA graph)",
+            "systems": nsys, "atoms": atoms, "meshes": sorted({s.K[0] for s in systems}),
+            "evals_per_s": round(nsys / (t_batch * 1e-3), 1), "us_per_batch": round(t_batch * 1e3, 2),
+            "atom_evals_per_s": round(atoms / (t_batch * 1e-3), 1),
+            "one_system_per_launch": {"eager_evals_per_s": round(nsys / (t_eager * 1e-3), 1),
+                                      "graph_evals_per_s": round(nsys / (t_graph * 1e-3), 1)},
+            "speedup_vs_graph_of_single_launches": round(t_graph / t_batch, 3),
+            "bit_identical_to_single": same, "gpu_launches_per_step": 2}}
+    finally:
+        pme.pme_batch_destroy(b)
+        for pl in plans:
+            pme.pme_destroy(pl)
+    return out
+
+
+def leg_serving(args, sampler, n_req: int = 4000):
+    """Poisson arrivals (20k requests/s, seed 5) drawing 90% from 64 config-4 systems and 10% from 8
+    65536-atom / 64^3 systems, all with resident plans; every request uses a freshly jittered frame. The
+    server admits by a 40 GB device budget and 128 slots; the comparison serves the same stream one system
+    per launch, synchronously, in arrival order."""
+    import collections
+
+    import torch
+
+    from paper_2009_12617_gb300 import pme
+    from paper_2009_12617_gb300 import workloads as wl
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    small = wl.batch_systems(64, seed=4)
+    big = [wl.headline_system(seed=10 + i) for i in range(8)]
+    pool = small + big
+    plans = [pme.pme_create(s.K, s.p, s.beta, s.box) for s in pool]
+    NF, NBUF = 2, 4
+    frames, qs, outs = [], [], []
+    for i, s in enumerate(pool):
+        L = float(s.box[0, 0])
+        f1 = wl.jitter(s.pos, L, 500 + i, 0)
+        frames.append([torch.from_numpy(s.pos).to(dev), torch.from_numpy(f1).to(dev)])
+        qs.append(torch.from_numpy(s.q).to(dev))
+        outs.append([torch.empty((s.n, 3), dtype=torch.float32, device=dev) for _ in range(NBUF)])
+        pme.pme_reserve(plans[i], s.n)
+    rng = np.random.Generator(np.random.PCG64(5))
+    gaps = rng.exponential(1.0 / 20000.0, n_req)
+    arrival = np.cumsum(gaps)
+    which = np.where(rng.random(n_req) < 0.9, rng.integers(0, 64, n_req), 64 + rng.integers(0, 8, n_req))
+    srv = pme.pme_server_create(40 * (1 << 30), 128)
+    lat = np.zeros(n_req)
+    uses = collections.Counter()
+    try:
+        # warm every plan once through the server
+        for i in range(len(pool)):
+            t = pme.pme_submit(srv, plans[i], frames[i][0], qs[i], outs[i][0])
+            pme.pme_poll(srv, t, block=True)
+        inflight = collections.deque()
+        busy_bufs = collections.Counter()
+        done = 0
+        nxt = 0
+        t0 = time.perf_counter()
+        while done < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrival[nxt] <= now:
+                i = int(which[nxt])
+                if busy_bufs[i] >= NBUF:
+                    break
+                k = uses[i]
+                t = pme.pme_submit(srv, plans[i], frames[i][k % NF], qs[i], outs[i][k % NBUF])
+                if t is None:  # PME_EAGAIN: all slots busy; retry after completions
+                    break
+                uses[i] += 1
+                busy_bufs[i] += 1
+                inflight.append((nxt, i, t))
+                nxt += 1
+            progressed = False
+            while inflight:
+                r, i, t = inflight[0]
+                if pme.pme_poll(srv, t, block=False) != pme.PME_OK:
+                    break
+                inflight.popleft()
+                lat[r] = (time.perf_counter() - t0) - arrival[r]
+                busy_bufs[i] -= 1
+                done += 1
+                progressed = True
+            if not progressed and nxt < n_req and arrival[nxt] > time.perf_counter() - t0 + 20e-6:
+                time.sleep(5e-6)
+        elapsed = time.perf_counter() - t0
+        sampler.window(time.time() - elapsed, time.time())
+        stats = pme.pme_server_stats(srv)
+    finally:
+        pme.pme_server_destroy(srv)
+    atoms = np.array([pool[i].n for i in which])
+    # the same stream, one system per launch, synchronous, in arrival order
+    lat1 = np.zeros(n_req)
+    for i in range(len(pool)):
+        pme.pme_compute(plans[i], frames[i][0], qs[i], outs[i][0])
+    t0 = time.perf_counter()
+    for r in range(n_req):
+        while time.perf_counter() - t0 < arrival[r]:
+            pass
+        i = int(which[r])
+        pme.pme_compute(plans[i], frames[i][r % NF], qs[i], outs[i][0])
+        lat1[r] = (time.perf_counter() - t0) - arrival[r]
+    elapsed1 = time.perf_counter() - t0
+    for pl in plans:
+        pme.pme_destroy(pl)
+    return {"serving": {
+        "workload": "Poisson arrivals 20k req/s (seed 5), 90% from 64 config-4 boxes, 10% from 8 65536-atom 64^3 boxes, "
+                    "resident plans, jittered frames, budget 40 GB, 128 slots",
+        "requests": n_req, "offered_req_per_s": round(n_req / arrival[-1], 1),
+        "throughput_req_per_s": round(n_req / elapsed, 1), "atom_evals_per_s": round(atoms.sum() / elapsed, 1),
+        "p50_us": round(1e6 * float(np.percentile(lat, 50)), 2), "p99_us": round(1e6 * float(np.percentile(lat, 99)), 2),
+        "latency_from": "request arrival time to completion seen by the client",
+        "server_p50_us": round(stats["p50_us"], 2), "server_p99_us": round(stats["p99_us"], 2),
+        "waves": stats["waves"],
+        "one_system_per_launch": {"throughput_req_per_s": round(n_req / elapsed1, 1),
+                                  "p50_us": round(1e6 * float(np.percentile(lat1, 50)), 2),
+                                  "p99_us": round(1e6 * float(np.percentile(lat1, 99)), 2)}}}
+
+
 def _extras():
-    """Batched and served legs (added as they are built)."""
-    return []
+    """Batched and served legs."""
+    return [leg_batched, leg_serving]
 
 
 if __name__ == "__main__":

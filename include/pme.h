@@ -144,7 +144,7 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
 /* Batched evaluation: many independent systems in ONE persistent kernel launch                            */
 
 /* Build a batch over nsys existing plans (not owned by the batch; each must outlive it and must not be
- * used elsewhere while the batch runs). Atom counts n[s] are fixed for the batch. Atom arrays of all
+ * used elsewhere while the batch runs). All plans must use the same B-spline order p. Atom counts n[s] are fixed for the batch. Atom arrays of all
  * systems are packed back to back in the order given: system s owns atoms [off_s, off_s + n[s]) with
  * off_s = n[0] + ... + n[s-1]. The batch runs on cuda_stream and captures its launch in a CUDA graph on
  * first use. */

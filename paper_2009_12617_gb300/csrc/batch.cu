@@ -1,20 +1,499 @@
-// Batched evaluation of many systems in one persistent launch (filled in below).
+// Batched evaluation of many independent systems in ONE persistent kernel launch.
+//
+// A host-built work list holds, stage by stage, the work items of every system: all binning items of all
+// systems, then all spreading items, and so on. CTAs take list entries in order with one atomic; an
+// entry waits until its system's previous stage has finished every item, so different systems overlap
+// freely (one system's FFT runs beside another's spreading) and the only barriers are per system. Each
+// entry depends only on entries earlier in the list, all of them already taken by running CTAs, so the
+// launch makes progress whatever number of CTAs is resident. Waits are bounded: past the deadline a wait
+// sets an error bit and an abort flag, and every later wait returns at once, so a launch always ends.
+// The last CTA to leave resets every counter, which lets a CUDA graph replay the launch.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "../../include/pme.h"
+#include "batch_internal.h"
+#include "host_tables.h"
+#include "kernels.h"
 #include "plan_internal.h"
+#include "stages.cuh"
+
+namespace pme {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait (thread 0 of the CTA) until *counter >= target; false if the wait gave up or the launch aborted.
+__device__ bool bounded_wait(const unsigned *counter, unsigned target, BatchCtrl *ctrl, unsigned long long limit_ns) {
+    if (ld_acquire(counter) >= target) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (ld_acquire(&ctrl->abort)) return false;
+        if (ld_acquire(counter) >= target) return true;
+        if (globaltimer_ns() - t0 > limit_ns) {
+            atomicExch(&ctrl->abort, 1u);
+            return false;
+        }
+        __nanosleep(200);
+    }
+}
+
+// Each stage is a separate (not inlined) call, so the register allocation of one stage does not inflate
+// the others and the persistent kernel keeps the occupancy of its most demanding stage.
+__device__ __noinline__ void call_bin(const SysDev &d, int item, void *smem) { stage_bin(d, item, smem); }
+template <int P>
+__device__ __noinline__ void call_spread(const SysDev &d, int item, void *smem) { stage_spread<P>(d, item, smem); }
+__device__ __noinline__ void call_fwd(const SysDev &d, int item, void *smem) { stage_fwd(d, item, smem); }
+__device__ __noinline__ void call_conv(const SysDev &d, int item, void *smem) { stage_conv(d, item, smem); }
+__device__ __noinline__ void call_inv(const SysDev &d, int item, void *smem) { stage_inv(d, item, smem); }
+template <int P>
+__device__ __noinline__ void call_gather(const SysDev &d, int item, void *smem) { stage_gather<P>(d, item, smem); }
+
+template <int P>
+__device__ __forceinline__ void run_stage(const SysDev &d, int stage, int item, void *smem) {
+    switch (stage) {
+        case STAGE_BIN: call_bin(d, item, smem); break;
+        case STAGE_SPREAD: call_spread<P>(d, item, smem); break;
+        case STAGE_FWD: call_fwd(d, item, smem); break;
+        case STAGE_CONV: call_conv(d, item, smem); break;
+        case STAGE_INV: call_inv(d, item, smem); break;
+        default: call_gather<P>(d, item, smem); break;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(NT_BATCH, 4) k_batch(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SysDev sd;
+    __shared__ int s_entry, s_ok;
+    const int tid = threadIdx.x;
+    while (true) {
+        if (tid == 0) s_entry = (int)atomicAdd(&a.ctrl->head, 1u);
+        __syncthreads();
+        const int e = s_entry;
+        if (e >= a.nentries) break;
+        const BatchEntry w = a.entries[e];
+        const int sys = w.sys, stage = w.stage;
+        if (tid < (int)(sizeof(SysDev) / 4)) ((int *)&sd)[tid] = ((const int *)(a.sys + sys))[tid];
+        if (tid == 0) {
+            bool ok = true;
+            if (stage > 0) {
+                unsigned target = a.count[sys * NUM_STAGES + stage - 1];
+                if (a.stall_entry == e) target += 1u;  // test hook: a dependency nothing completes
+                ok = bounded_wait(&a.done[sys * NUM_STAGES + stage - 1], target, a.ctrl, a.wait_ns);
+            }
+            s_ok = ok;
+            if (!ok) atomicOr(&a.sys[sys].ctl->status, ST_TIMEOUT);
+        }
+        __syncthreads();
+        if (s_ok) {
+            for (int it = w.begin; it < w.end; ++it) {
+                run_stage<P>(sd, stage, it, smem);
+                __syncthreads();
+            }
+        }
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(&a.done[sys * NUM_STAGES + stage], (unsigned)(w.end - w.begin));
+        }
+        __syncthreads();
+    }
+    // the last CTA out resets every counter for the next launch (all entries are finished by then)
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&a.ctrl->exited, 1u) == gridDim.x - 1u) {
+            for (int i = 0; i < a.nsys * NUM_STAGES; ++i) a.done[i] = 0u;
+            a.ctrl->head = 0u;
+            a.ctrl->abort = 0u;
+            __threadfence();
+            a.ctrl->exited = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// host side
+
+int stage_items(const SysDev &d, int stage) {
+    switch (stage) {
+        case STAGE_BIN: return d.nbin;
+        case STAGE_SPREAD: return d.ntiles + OVF_ITEMS;
+        case STAGE_FWD: return d.K1;
+        case STAGE_CONV: return d.nconv;
+        case STAGE_INV: return d.K1;
+        default: return d.ntiles + OVF_ITEMS;
+    }
+}
+
+// items of one stage grouped per list entry (fewer, larger entries for the many small tile items)
+static int stage_group(int stage) {
+    return (stage == STAGE_SPREAD || stage == STAGE_GATHER) ? 4 : (stage == STAGE_CONV ? 2 : 1);
+}
+
+void build_work_list(const std::vector<SysDev> &sys, std::vector<BatchEntry> &entries, std::vector<unsigned> &count) {
+    entries.clear();
+    count.assign(sys.size() * NUM_STAGES, 0u);
+    for (int stage = 0; stage < NUM_STAGES; ++stage)
+        for (size_t s = 0; s < sys.size(); ++s) {
+            const int n = stage_items(sys[s], stage), g = stage_group(stage);
+            count[s * NUM_STAGES + stage] = (unsigned)n;
+            for (int b = 0; b < n; b += g) {
+                BatchEntry e;
+                e.sys = (unsigned short)s;
+                e.stage = (unsigned short)stage;
+                e.begin = b;
+                e.end = std::min(n, b + g);
+                entries.push_back(e);
+            }
+        }
+}
+
+size_t batch_smem(const std::vector<SysDev> &sys) {
+    size_t m = smem_bin(NT_BATCH);
+    for (const SysDev &d : sys) {
+        m = std::max(m, smem_spread(d.p));
+        m = std::max(m, smem_gather(d.p));
+        m = std::max(m, smem_slab(d.K2, d.K3));
+        m = std::max(m, smem_conv(d.K1, NT_BATCH));
+    }
+    return m;
+}
+
+static const void *batch_kernel(int p) {
+    return p == 4 ? (const void *)k_batch<4> : (p == 6 ? (const void *)k_batch<6> : (const void *)k_batch<8>);
+}
+
+cudaError_t configure_batch_kernel() {
+    for (int p : {4, 6, 8}) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel(p), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(MAX_SMEM_BYTES - sizeof(SysDev) - 64));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int batch_grid(int dev, int p, size_t smem) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(p), NT_BATCH, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return sms * per_sm;
+}
+
+cudaError_t launch_batch(const BatchArgs &a, int p, int grid, size_t smem, cudaStream_t s) {
+    if (p == 4) k_batch<4><<<grid, NT_BATCH, smem, s>>>(a);
+    else if (p == 6) k_batch<6><<<grid, NT_BATCH, smem, s>>>(a);
+    else k_batch<8><<<grid, NT_BATCH, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// first list entry that waits on a dependency (for the stall test hook)
+int first_waiting_entry(const std::vector<BatchEntry> &entries) {
+    for (size_t i = 0; i < entries.size(); ++i)
+        if (entries[i].stage > 0) return (int)i;
+    return -1;
+}
+
+// Device state of one persistent launch over up to cap_sys systems and cap_entries list entries.
+pme_status WaveState::init(int dev_, int cap_sys_, size_t cap_entries_) {
+    dev = dev_;
+    cap_sys = cap_sys_;
+    cap_entries = cap_entries_;
+    size_t off = 0;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_sys = off;  off = al(off + sizeof(SysDev) * cap_sys);
+    const size_t o_cnt = off;  off = al(off + sizeof(unsigned) * cap_sys * NUM_STAGES);
+    const size_t o_ent = off;  off = al(off + sizeof(BatchEntry) * cap_entries);
+    const size_t o_done = off; off = al(off + sizeof(unsigned) * cap_sys * NUM_STAGES);
+    const size_t o_ctrl = off; off = al(off + sizeof(BatchCtrl));
+    const size_t o_ev = off;   off = al(off + sizeof(double) * 8 * cap_sys);
+    const size_t o_st = off;   off = al(off + sizeof(unsigned) * cap_sys);
+    cudaError_t e = cudaMalloc(&dmem, off);
+    if (e != cudaSuccess) {
+        dmem = nullptr;
+        return fail(PME_ENOMEM, "cudaMalloc(%zu bytes) for a batch: %s", off, cudaGetErrorString(e));
+    }
+    if ((e = cudaMemset(dmem, 0, off)) != cudaSuccess) return cuda_fail(e, "cudaMemset(batch state)");
+    if ((e = cudaMallocHost(&hmem, off)) != cudaSuccess) {
+        hmem = nullptr;
+        return cuda_fail(e, "cudaMallocHost(batch staging)");
+    }
+    memset(hmem, 0, off);
+    bytes = off;
+    char *b = (char *)dmem, *h = (char *)hmem;
+    d_sys = (SysDev *)(b + o_sys);
+    h_sys = (SysDev *)(h + o_sys);
+    d_entries = (BatchEntry *)(b + o_ent);
+    h_entries = (BatchEntry *)(h + o_ent);
+    d_count = (unsigned *)(b + o_cnt);
+    h_count = (unsigned *)(h + o_cnt);
+    d_done = (unsigned *)(b + o_done);
+    d_ctrl = (BatchCtrl *)(b + o_ctrl);
+    d_ev = (double *)(b + o_ev);
+    h_ev = (double *)(h + o_ev);
+    d_status = (unsigned *)(b + o_st);
+    h_status = (unsigned *)(h + o_st);
+    head_bytes = o_ent;  // descriptors and counts; the used part of the list follows at o_ent
+    return PME_OK;
+}
+
+void WaveState::release() {
+    if (dmem) cudaFree(dmem);
+    if (hmem) cudaFreeHost(hmem);
+    dmem = hmem = nullptr;
+}
+
+cudaError_t WaveState::upload(size_t nentries, cudaStream_t s) const {
+    cudaError_t e = cudaMemcpyAsync(dmem, hmem, head_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nentries)
+        e = cudaMemcpyAsync(d_entries, h_entries, sizeof(BatchEntry) * nentries, cudaMemcpyHostToDevice, s);
+    return e;
+}
+
+BatchArgs WaveState::args(int nsys, int nentries, unsigned long long wait_ns, int stall_entry) const {
+    BatchArgs a;
+    a.sys = d_sys;
+    a.entries = d_entries;
+    a.count = d_count;
+    a.done = d_done;
+    a.ctrl = d_ctrl;
+    a.nsys = nsys;
+    a.nentries = nentries;
+    a.wait_ns = wait_ns;
+    a.stall_entry = stall_entry;
+    return a;
+}
+
+// Status words of every system in the wave -> h_status (device kernel, so it can sit in a graph).
+__global__ void k_collect_status(const SysDev *sys, int nsys, unsigned *out) {
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+        out[s] = sys[s].ctl->status;
+        sys[s].ctl->status = 0u;
+    }
+}
+
+cudaError_t launch_collect_status(const SysDev *sys, int nsys, unsigned *out, cudaStream_t s) {
+    k_collect_status<<<1, 128, 0, s>>>(sys, nsys, out);
+    return cudaGetLastError();
+}
+
+// Reset the resident state of a plan after an aborted launch (counters, buckets, the int64 mesh).
+pme_status plan_recover(pme_plan *pl, cudaStream_t s) {
+    SysDev &d = pl->d;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d.grid, 0, (size_t)d.K1 * d.K2 * d.K3 * 8, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d.bcount, 0, bcount_bytes(d.ntiles), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(recover)");
+    return PME_OK;
+}
+
+}  // namespace pme
 
 using namespace pme;
 
+struct pme_batch {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<pme_plan *> plans;
+    std::vector<int64_t> n, off;
+    std::vector<SysDev> sys;
+    std::vector<BatchEntry> entries;
+    std::vector<unsigned> count;
+    WaveState wave;
+    size_t smem = 0;
+    int grid = 0;
+    // graph of (descriptor upload, persistent kernel, status collection) for the last pointer set
+    cudaGraphExec_t exec = nullptr;
+    const void *g_pos = nullptr, *g_q = nullptr, *g_forces = nullptr, *g_ev = nullptr;
+    int stall = 0;
+    int64_t stall_ns = 0;
+};
+
+static pme_status batch_record(pme_batch *b, const float *pos, const float *q, float *forces, double *ev_dev) {
+    const int nsys = (int)b->sys.size();
+    for (int s = 0; s < nsys; ++s) {
+        SysDev d = b->sys[s];
+        d.pos = pos + 3 * b->off[s];
+        d.q = q + b->off[s];
+        d.forces = forces + 3 * b->off[s];
+        d.ev = ev_dev + 7 * s;
+        b->wave.h_sys[s] = d;
+    }
+    memcpy(b->wave.h_entries, b->entries.data(), sizeof(BatchEntry) * b->entries.size());
+    memcpy(b->wave.h_count, b->count.data(), sizeof(unsigned) * b->count.size());
+    cudaError_t e;
+    if ((e = b->wave.upload(b->entries.size(), b->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(batch descriptors)");
+    const int stall_entry = b->stall ? first_waiting_entry(b->entries) : -1;
+    const unsigned long long wait_ns = b->stall ? (unsigned long long)b->stall_ns : 1000000000ull;
+    BatchArgs a = b->wave.args(nsys, (int)b->entries.size(), wait_ns, stall_entry);
+    if ((e = launch_batch(a, b->sys[0].p, b->grid, b->smem, b->stream)) != cudaSuccess)
+        return cuda_fail(e, "persistent kernel launch");
+    if ((e = launch_collect_status(b->wave.d_sys, nsys, b->wave.d_status, b->stream)) != cudaSuccess)
+        return cuda_fail(e, "status kernel launch");
+    return PME_OK;
+}
+
 extern "C" {
-pme_status pme_batch_create(int, pme_plan *const *, const int64_t *, void *, pme_batch **out) {
-    if (out) *out = nullptr;
-    return fail(PME_EUNSUPPORTED, "batched evaluation not built yet");
+
+pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, void *cuda_stream, pme_batch **out) {
+    if (!out) return fail(PME_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nsys < 1 || nsys > 4096 || !plans || !n) return fail(PME_EINVAL, "need 1..4096 systems, plans and n");
+    pme_batch *b = new (std::nothrow) pme_batch();
+    if (!b) return fail(PME_ENOMEM, "host allocation failed");
+    b->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&b->dev);
+    int64_t off = 0;
+    for (int s = 0; s < nsys; ++s) {
+        pme_plan *pl = plans[s];
+        if (!pl || n[s] < 0 || n[s] > (int64_t)0x3fffffff) {
+            delete b;
+            return fail(PME_EINVAL, "system %d: NULL plan or n out of range", s);
+        }
+        if (pl->dev != b->dev) {
+            delete b;
+            return fail(PME_EINVAL, "system %d: plan lives on device %d, batch on %d", s, pl->dev, b->dev);
+        }
+        if (pl->p != plans[0]->p) {
+            delete b;
+            return fail(PME_EINVAL, "system %d has B-spline order %d, system 0 has %d: one order per batch", s, pl->p,
+                        plans[0]->p);
+        }
+        for (int t = 0; t < s; ++t)
+            if (plans[t] == pl) {
+                delete b;
+                return fail(PME_EINVAL, "systems %d and %d share a plan; each system needs its own", t, s);
+            }
+        pme_status st = plan_reserve(pl, n[s]);
+        if (st != PME_OK) {
+            delete b;
+            return st;
+        }
+        b->plans.push_back(pl);
+        b->n.push_back(n[s]);
+        b->off.push_back(off);
+        b->sys.push_back(plan_descriptor(pl, nullptr, nullptr, n[s], nullptr, nullptr));
+        off += n[s];
+    }
+    build_work_list(b->sys, b->entries, b->count);
+    pme_status st = b->wave.init(b->dev, nsys, b->entries.size());
+    if (st != PME_OK) {
+        b->wave.release();
+        delete b;
+        return st;
+    }
+    cudaError_t e = configure_batch_kernel();
+    if (e != cudaSuccess) {
+        b->wave.release();
+        delete b;
+        return cuda_fail(e, "configure persistent kernel");
+    }
+    b->smem = batch_smem(b->sys);
+    b->grid = batch_grid(b->dev, b->sys[0].p, b->smem);
+    *out = b;
+    return PME_OK;
 }
-pme_status pme_batch_enqueue(pme_batch *, const float *, const float *, float *, double *) {
-    return fail(PME_EUNSUPPORTED, "batched evaluation not built yet");
+
+pme_status pme_batch_enqueue(pme_batch *b, const float *pos, const float *q, float *forces, double *ev_dev) {
+    if (!b) return fail(PME_EINVAL, "batch is NULL");
+    if (!ev_dev) return fail(PME_EINVAL, "ev_dev must be non-NULL");
+    int64_t ntot = b->off.back() + b->n.back();
+    if (ntot > 0 && (!pos || !q || !forces)) return fail(PME_EINVAL, "pos, q and forces must be non-NULL");
+    DeviceGuard g(b->dev);
+    cudaError_t e;
+    if (!b->exec || b->g_pos != pos || b->g_q != q || b->g_forces != forces || b->g_ev != ev_dev) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        // capture on a private stream so the caller's stream may itself be capturing or busy
+        cudaStream_t cs;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        cudaStream_t keep = b->stream;
+        b->stream = cs;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        pme_status st = PME_OK;
+        if (e == cudaSuccess) st = batch_record(b, pos, q, forces, ev_dev);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        b->stream = keep;
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        if (st != PME_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        b->g_pos = pos;
+        b->g_q = q;
+        b->g_forces = forces;
+        b->g_ev = ev_dev;
+    }
+    if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return PME_OK;
 }
-pme_status pme_batch_sync(pme_batch *) { return fail(PME_EUNSUPPORTED, "batched evaluation not built yet"); }
-void pme_batch_destroy(pme_batch *) {}
-pme_status pme_batch_debug_stall(pme_batch *, int, int64_t) {
-    return fail(PME_EUNSUPPORTED, "batched evaluation not built yet");
+
+pme_status pme_batch_sync(pme_batch *b) {
+    if (!b) return fail(PME_EINVAL, "batch is NULL");
+    DeviceGuard g(b->dev);
+    const int nsys = (int)b->sys.size();
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->wave.h_status, b->wave.d_status, sizeof(unsigned) * nsys, cudaMemcpyDeviceToHost,
+                             b->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(status)");
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned bits = 0;
+    for (int s = 0; s < nsys; ++s) bits |= b->wave.h_status[s];
+    if (bits & ST_TIMEOUT) {
+        // an aborted launch skipped work whose consumers reset resident state: restore it
+        for (pme_plan *pl : b->plans) plan_recover(pl, b->stream);
+        cudaStreamSynchronize(b->stream);
+    }
+    memset(b->wave.h_status, 0, sizeof(unsigned) * nsys);
+    cudaMemsetAsync(b->wave.d_status, 0, sizeof(unsigned) * nsys, b->stream);
+    return status_from_bits(bits);
 }
+
+pme_status pme_batch_debug_stall(pme_batch *b, int enable, int64_t wait_limit_ns) {
+    if (!b) return fail(PME_EINVAL, "batch is NULL");
+    if (enable && (wait_limit_ns <= 0 || wait_limit_ns > 2000000000ll))
+        return fail(PME_EINVAL, "wait_limit_ns must be in (0, 2e9]");
+    b->stall = enable ? 1 : 0;
+    b->stall_ns = wait_limit_ns;
+    if (b->exec) {  // re-record with the new setting on the next enqueue
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return PME_OK;
 }
+
+void pme_batch_destroy(pme_batch *b) {
+    if (!b) return;
+    DeviceGuard g(b->dev);
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->wave.release();
+    delete b;
+}
+
+}  // extern "C"

@@ -42,9 +42,24 @@ constexpr float FIX_INV = 9.094947017729282379150390625e-13f;  // 2^-40
 // bounds every mesh value and every partial sum, so larger totals are refused.
 constexpr float QABS_SCALE = 16777216.0f;                // 2^24
 constexpr unsigned long long QABS_LIMIT = 1ull << 46;    // 2^22 e in 2^24 units
-constexpr int BIN_CHUNK = 256;   // atoms per binning work item
+constexpr int BIN_PER_THREAD = 4;           // atoms per thread in the binning stage (for memory-level parallelism)
+constexpr int BIN_CHUNK = 256 * BIN_PER_THREAD;  // atoms per binning work item
 constexpr int OVF_ITEMS = 8;     // extra spread / gather work items that handle bucket-overflow atoms
 constexpr int MAX_K = 128;
+// Tile counters sit on separate 128-byte lines so the binning atomics spread over the L2 slices.
+constexpr int BCOUNT_STRIDE = 32;
+// Shared-memory accumulation splits each fixed-point contribution v into hi = floor(v / 2^20) and
+// lo = v - hi 2^20 in [0, 2^20], summed in two int32 arrays with native 32-bit atomics. With at most
+// CAP_MAX atoms per tile and |q| <= Q_TILE_MAX (|v| <= 2^41), neither sum can overflow; atoms with larger
+// charges take the 64-bit global path instead.
+constexpr float Q_TILE_MAX = 2.0f;
+constexpr int CAP_MAX = 512;
+// Columns m3 per influence-stage work item.
+constexpr int CONV_COLS = 8;
+// Independent global loads each thread keeps in flight when staging data into shared memory.
+constexpr int LOAD_BATCH = 8;
+// Slots of the fixed-order final energy / virial reduction (a power of two).
+constexpr int REDUCE_SLOTS = 64;
 
 enum StatusBits : unsigned {
     ST_NONFINITE = 1u,   // a position or charge is NaN / Inf, or absurdly far outside the cell
@@ -73,6 +88,9 @@ struct SysDev {
     int cap;                     // bucket capacity (atoms per tile)
     int n;                       // atoms
     int nbin;                    // binning work items = ceil(n / BIN_CHUNK)
+    int nchunk3;                 // influence-stage column chunks = ceil(H3 / CONV_COLS)
+    int nconv;                   // influence-stage work items = K2 * nchunk3
+    float kinv[3];               // 1 / K_alpha
     // u_alpha = sum_j r_j C[j][alpha], C[j][alpha] = K_alpha a*_alpha[j], as an unevaluated float sum
     // chi + clo (about 48 significant bits), index 3*j + alpha.
     float chi[9], clo[9];
@@ -93,10 +111,10 @@ struct SysDev {
     const float2 *tw3h, *tw3;    // exp(-2 pi i k / (K3/2)), exp(-2 pi i k / K3) for k <= K3/2
     float4 *bka;                 // bucket records (w1, w2, w3, q), [tile][cap]
     int2 *bkb;                   // bucket records (packed base, atom index)
-    unsigned *bcount;            // atoms binned per tile
+    unsigned *bcount;            // atoms binned per tile, at tile * BCOUNT_STRIDE
     float4 *ova;                 // overflow records, capacity n
     int2 *ovb;
-    double *partials;            // 8 doubles per k1-pencil item
+    double *partials;            // 8 double-float (hi, lo) slots per influence-stage work item
     Ctl *ctl;
 };
 
@@ -106,6 +124,8 @@ struct SysDev {
 #if defined(PME_HOST_EMULATION)
 template <class T> inline T ldcg(const T *p) { return *p; }
 inline unsigned atomic_add_u32(unsigned *p, unsigned v) { unsigned o = *p; *p = o + v; return o; }
+inline void atomic_add_u32_nr(unsigned *p, unsigned v) { *p += v; }
+inline void atomic_add_i32(int *p, int v) { *p += v; }
 inline void atomic_or_u32(unsigned *p, unsigned v) { *p |= v; }
 inline void atomic_add_u64(unsigned long long *p, unsigned long long v) { *p += v; }
 inline void red_add_u64(unsigned long long *p, unsigned long long v) { *p += v; }
@@ -116,6 +136,8 @@ inline long long f2ll_rn(float x) { return llrintf(x); }
 #else
 template <class T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned atomic_add_u32(unsigned *p, unsigned v) { return atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_u32_nr(unsigned *p, unsigned v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_i32(int *p, int v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_or_u32(unsigned *p, unsigned v) { atomicOr(p, v); }
 __device__ __forceinline__ void atomic_add_u64(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
@@ -126,6 +148,20 @@ __device__ __forceinline__ long long f2ll_rn(float x) { return __float2ll_rn(x);
 #endif
 
 PME_DEV int imin(int a, int b) { return a < b ? a : b; }
+
+// floor(a / b) for 0 <= a < 2^20 and 1 <= b <= 2^12 from a precomputed float reciprocal: (a + 0.5) / b is
+// at least 1/(2b) away from an integer, far more than the float rounding, so the truncation is exact.
+PME_DEV int fdiv(int a, float binv) { return (int)(((float)a + 0.5f) * binv); }
+
+#if defined(PME_HOST_EMULATION)
+inline unsigned long long warp_sum_u64(unsigned long long v) { return v; }
+#else
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+#endif
 
 PME_DEV float qnan_f() {
     union {
@@ -189,20 +225,22 @@ PME_DEV bool scaled_coord(const SysDev &d, const float r[3], int al, int K, int 
     const float s = fadd_rn(uh, ul);
     ul = fsub_rn(ul, fsub_rn(s, uh));
     uh = s;
-    if (!(fabsf(uh) < 1.0e9f)) return false;  // also rejects NaN
-    const float fl = floorf(uh);
+    if (!(fabsf(uh) < 8388608.0f)) return false;  // |u| < 2^23 (also rejects NaN)
+    float fl = floorf(uh);
     float ww = fadd_rn(fsub_rn(uh, fl), ul);
-    long long bi = (long long)fl;
     if (ww >= 1.f) {
         ww -= 1.f;
-        bi += 1;
+        fl += 1.f;
     } else if (ww < 0.f) {
         ww += 1.f;
-        bi -= 1;
+        fl -= 1.f;
     }
-    long long m = bi % K;
+    // fl mod K in exact float arithmetic (|fl| <= 2^23 + 1, so fl - K floor(fl / K) is exact)
+    const float qk = floorf(fl * d.kinv[al]);
+    int m = (int)(fl - qk * (float)K);
     if (m < 0) m += K;
-    b = (int)m;
+    else if (m >= K) m -= K;
+    b = m;
     w = ww;
     return true;
 }

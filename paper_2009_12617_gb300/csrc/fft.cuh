@@ -148,18 +148,20 @@ PME_DEV void fft_stage(const float2 *src, float2 *dst, int N, int Ns, int ntr, i
     const int nb = N / R;           // butterflies per transform
     const int total = ntr * nb;
     const int tstep = nb / Ns;      // = N / (Ns R): twiddle index step
+    const float inv_nb = 1.0f / (float)nb, inv_ntr = 1.0f / (float)ntr, inv_ns = 1.0f / (float)Ns;
     for (int idx = PME_TID; idx < total; idx += PME_NTH) {
         int t, j;
         if (es == 1) {  // rows contiguous: consecutive threads walk one transform
-            t = idx / nb;
+            t = fdiv(idx, inv_nb);
             j = idx - t * nb;
         } else {        // columns: consecutive threads walk consecutive transforms
-            j = idx / ntr;
+            j = fdiv(idx, inv_ntr);
             t = idx - j * ntr;
         }
         const float2 *s = src + t * bs;
         float2 *o = dst + t * bs;
-        const int k = j % Ns;
+        const int jq = fdiv(j, inv_ns);
+        const int k = j - jq * Ns;
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * es];
@@ -172,7 +174,7 @@ PME_DEV void fft_stage(const float2 *src, float2 *dst, int N, int Ns, int ntr, i
             }
         }
         dft_small<R, INV>(v);
-        const int od = (j / Ns) * Ns * R + k;
+        const int od = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) o[(od + r * Ns) * es] = v[r];
     }

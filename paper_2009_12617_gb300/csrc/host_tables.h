@@ -80,6 +80,9 @@ inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const d
     d.nt2 = (K[1] + TILE - 1) / TILE;
     d.nt3 = (K[2] + TILE - 1) / TILE;
     d.ntiles = d.nt1 * d.nt2 * d.nt3;
+    d.nchunk3 = (d.H3 + CONV_COLS - 1) / CONV_COLS;
+    d.nconv = d.K2 * d.nchunk3;
+    for (int a = 0; a < 3; ++a) d.kinv[a] = 1.0f / (float)K[a];
     for (int j = 0; j < 3; ++j)
         for (int al = 0; al < 3; ++al) {
             const double c = (double)K[al] * recip[3 * al + j];  // K_alpha a*_alpha[j]
@@ -162,9 +165,14 @@ inline void make_influence(const int K[3], int p, double beta, const double reci
 // Atoms beyond it go to the overflow list (handled by global-memory paths), so this only tunes speed.
 inline int bucket_capacity(int64_t n, int ntiles) {
     const double mean = (double)n / (double)ntiles;
-    int cap = (int)(2.0 * mean + 32.0);
+    const double want = 2.0 * mean + 32.0;
+    int cap = want > (double)CAP_MAX ? CAP_MAX : (int)want;
     cap = (cap + 31) / 32 * 32;
-    return cap < 32 ? 32 : cap;
+    return cap < 32 ? 32 : (cap > CAP_MAX ? CAP_MAX : cap);
 }
+
+// Bytes of the padded tile-counter array and of the influence-stage partials.
+inline size_t bcount_bytes(int ntiles) { return (size_t)ntiles * BCOUNT_STRIDE * sizeof(unsigned); }
+inline size_t partials_bytes(const SysDev &d) { return (size_t)d.nconv * 8 * sizeof(double); }
 
 }  // namespace pme

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(NT_MESH) k_fwd(SysDev d) {
     stage_fwd(d, blockIdx.x, smem);
 }
 
-__global__ void __launch_bounds__(NT_MESH) k_conv(SysDev d) {
+__global__ void __launch_bounds__(NT_CONV) k_conv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     stage_conv(d, blockIdx.x, smem);
 }
@@ -75,7 +75,7 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             k_fwd<<<d.K1, NT_MESH, smem_slab(d.K2, d.K3), s>>>(d);
             break;
         case STAGE_CONV:
-            k_conv<<<d.K2, NT_MESH, smem_conv(d.K1, d.K3, NT_MESH), s>>>(d);
+            k_conv<<<d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s>>>(d);
             break;
         case STAGE_INV:
             k_inv<<<d.K1, NT_MESH, smem_slab(d.K2, d.K3), s>>>(d);

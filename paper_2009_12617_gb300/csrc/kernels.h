@@ -9,6 +9,7 @@ namespace pme {
 
 constexpr int NT_MESH = 256;   // threads per CTA for binning and the FFT / influence stages
 constexpr int NT_TILE = 128;   // threads per CTA for spreading and force interpolation
+constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
 constexpr size_t MAX_SMEM_BYTES = 226 * 1024;  // opt-in limit is 227 KB including static shared memory
 
 // Raise the dynamic shared-memory limit of the large-footprint kernels (once per device).

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_eval_noalloc(NoallocArgs A)
     grid.sync();
     for (int it = blockIdx.x; it < d.K1; it += gridDim.x) stage_fwd(d, it, smem);
     grid.sync();
-    for (int it = blockIdx.x; it < d.K2; it += gridDim.x) stage_conv(d, it, smem);
+    for (int it = blockIdx.x; it < d.nconv; it += gridDim.x) stage_conv(d, it, smem);
     grid.sync();
     for (int it = blockIdx.x; it < d.K1; it += gridDim.x) stage_inv(d, it, smem);
     grid.sync();
@@ -158,7 +158,7 @@ static size_t noalloc_smem(int K[3], int p) {
     s = s > smem_spread(p) ? s : smem_spread(p);
     s = s > smem_gather(p) ? s : smem_gather(p);
     s = s > smem_slab(K[1], K[2]) ? s : smem_slab(K[1], K[2]);
-    s = s > smem_conv(K[0], K[2], NOALLOC_THREADS) ? s : smem_conv(K[0], K[2], NOALLOC_THREADS);
+    s = s > smem_conv(K[0], NOALLOC_THREADS) ? s : smem_conv(K[0], NOALLOC_THREADS);
     return s;
 }
 
@@ -237,8 +237,8 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     const int cap = bucket_capacity(ncap, d.ntiles);
     size_t off = 0;
     const size_t o_ctl = off;  off = al256(off + sizeof(Ctl));
-    const size_t o_cnt = off;  off = al256(off + (size_t)d.ntiles * 4);
-    const size_t o_par = off;  off = al256(off + K2 * 8 * 8);
+    const size_t o_cnt = off;  off = al256(off + bcount_bytes(d.ntiles));
+    const size_t o_par = off;  off = al256(off + partials_bytes(d));
     const size_t o_grid = off; off = al256(off + K1 * K2 * K3 * 8);
     const size_t zero_bytes = off;
     const size_t o_bmod = off; off = al256(off + (K1 + K2 + K3) * 8);

@@ -94,8 +94,8 @@ static pme_status alloc_mesh(pme_plan *pl) {
     const size_t o_phi = off;  off = align256(off + K1 * K2 * K3 * 4);
     const size_t o_bc = off;   off = align256(off + K1 * K2 * H3 * 8);
     const size_t o_tw = off;   off = align256(off + (K1 + K2 + Nh + Nh + 1) * 8);
-    const size_t o_cnt = off;  off = align256(off + (size_t)d.ntiles * 4);
-    const size_t o_par = off;  off = align256(off + K2 * 8 * 8);
+    const size_t o_cnt = off;  off = align256(off + bcount_bytes(d.ntiles));
+    const size_t o_par = off;  off = align256(off + partials_bytes(d));
     const size_t o_ctl = off;  off = align256(off + sizeof(Ctl));
     cudaError_t e = cudaMalloc(&pl->mesh_mem, off);
     if (e != cudaSuccess) {

@@ -1,15 +1,16 @@
 // Stage bodies of the reciprocal-space SPME pipeline (paper Sec. III-A, Fig. "LRPipe"): binning with
 // B-spline set-up, charge spreading, forward 3D FFT, influence-function multiply with energy / virial,
 // inverse 3D FFT, and force interpolation. Each body handles one work item of one system and is called
-// both from the per-stage kernels and from the persistent batched kernel.
+// both from the per-stage kernels and from the batched / cooperative kernels.
 //
 // Work items per system:
-//   bin     nbin items        atoms [item*BIN_CHUNK, ...): fractional coordinates, tile key, bucket insert
-//   spread  ntiles+OVF_ITEMS  one tile each, then bucket-overflow atoms
-//   fwd     K1 items          slab k1: int64 -> float, real FFT along k3, complex FFT along k2
-//   conv    K2 items          pencils m2: FFT along k1, times B*C, energy / virial, inverse FFT along k1
-//   inv     K1 items          slab k1: inverse FFT along k2, complex-to-real FFT along k3 -> phi
-//   gather  ntiles+OVF_ITEMS  one tile each (forces), then bucket-overflow atoms
+//   bin     nbin items          atoms [item*BIN_CHUNK, ...): fractional coordinates, tile key, bucket insert
+//   spread  ntiles+OVF_ITEMS    one tile each, then bucket-overflow atoms
+//   fwd     K1 items            slab k1: int64 -> float, real FFT along k3, complex FFT along k2
+//   conv    K2*nchunk3 items    pencils (m2, CONV_COLS columns m3): FFT along k1, times B*C, energy /
+//                               virial, inverse FFT along k1
+//   inv     K1 items            slab k1: inverse FFT along k2, complex-to-real FFT along k3 -> phi
+//   gather  ntiles+OVF_ITEMS    one tile each (forces), then bucket-overflow atoms
 #pragma once
 
 #include "common.cuh"
@@ -17,105 +18,161 @@
 
 namespace pme {
 
+// Tile region edge (mesh points) for spline order P: the tile plus the p - 1 points below it.
+template <int P>
+struct Region {
+    static constexpr int R = TILE + P - 1;
+    static constexpr int VOL = R * R * R;
+};
+
 // ---------------------------------------------------------------------------------------------------------
 // shared-memory sizes (bytes) of each stage for a given system and block size
 
-inline size_t smem_bin(int nth) { return (size_t)nth * sizeof(unsigned long long); }
+inline size_t smem_bin(int nth) { return (size_t)((nth + 31) / 32) * sizeof(unsigned long long) + 16; }
 inline size_t smem_tile_region(int p) { return (size_t)(TILE + p - 1) * (TILE + p - 1) * (TILE + p - 1); }
-inline size_t smem_spread(int p) { return smem_tile_region(p) * sizeof(unsigned long long); }
+inline size_t smem_spread(int p) { return smem_tile_region(p) * 2 * sizeof(int); }
 inline size_t smem_gather(int p) { return smem_tile_region(p) * sizeof(float); }
 inline size_t smem_slab(int K2, int K3) {
     const int H3 = K3 / 2 + 1;
     return (2 * (size_t)K2 * H3 + (K3 / 2) + (K3 / 2 + 1) + K2) * sizeof(float2);
 }
-inline size_t smem_conv(int K1, int K3, int nth) {
-    const int H3 = K3 / 2 + 1;
-    size_t fft = (2 * (size_t)K1 * H3 + K1) * sizeof(float2);
-    size_t red = (size_t)nth * 7 * sizeof(DF);
-    return fft > red ? fft : red;
+inline size_t smem_conv(int K1, int nth) {
+    size_t fft = (2 * (size_t)K1 * CONV_COLS + K1) * sizeof(float2);
+    size_t red = (size_t)((nth + 31) / 32) * 7 * sizeof(DF);
+    size_t fin = (size_t)REDUCE_SLOTS * 7 * sizeof(DF);
+    size_t m = fft > red ? fft : red;
+    return m > fin ? m : fin;
 }
+
+// global -> shared copy of n elements with LOAD_BATCH independent loads in flight per thread
+template <class T>
+PME_DEV void copy_batched(T *dst, const T *src, int n) {
+    const int tid = PME_TID, nth = PME_NTH;
+    for (int base = tid; base < n; base += LOAD_BATCH * nth) {
+        T v[LOAD_BATCH];
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u)
+            if (base + u * nth < n) v[u] = ldcg(src + base + u * nth);
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u)
+            if (base + u * nth < n) dst[base + u * nth] = v[u];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// 64-bit fixed point (scale 2^40) as (hi, lo): v ~ hi * 2^20 + lo with lo in [0, 2^20]. The split is a
+// deterministic function of the float v, used identically by the shared-memory and the global paths, so
+// the mesh does not depend on which path an atom takes.
+
+PME_DEV void fix_split(float v, int &h, unsigned &l) {
+    const float fh = floorf(v * 9.5367431640625e-07f);  // v / 2^20
+    h = (int)fh;
+    l = (unsigned)(int)rintf(fmaf(-fh, 1048576.0f, v));
+}
+PME_DEV unsigned long long fix_join(long long h, long long l) { return (unsigned long long)(h * 1048576ll + l); }
 
 // ---------------------------------------------------------------------------------------------------------
 // a1: bin atoms by spread tile (replaces the paper's hardware atom reordering, Sec. III-A / V-C; with
 // order-independent fixed-point accumulation the order inside a tile no longer matters)
 
 PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
-    unsigned long long *red = (unsigned long long *)smem;
+    unsigned long long *red = (unsigned long long *)smem;  // one slot per warp
     const int tid = PME_TID, nth = PME_NTH;
     const int i0 = item * BIN_CHUNK;
     const int i1 = imin(d.n, i0 + BIN_CHUNK);
     unsigned long long qacc = 0;
     unsigned bad = 0;
-    for (int i = i0 + tid; i < i1; i += nth) {
-        const float r[3] = {d.pos[3 * (size_t)i], d.pos[3 * (size_t)i + 1], d.pos[3 * (size_t)i + 2]};
-        const float q = d.q[i];
-        int b[3];
-        float w[3];
-        bool ok = isfinite(q) && fabsf(q) < 4194304.0f;  // |q| < 2^22 e
-        if (ok) ok = scaled_coord(d, r, 0, d.K1, b[0], w[0]) && scaled_coord(d, r, 1, d.K2, b[1], w[1]) &&
-                     scaled_coord(d, r, 2, d.K3, b[2], w[2]);
-        if (!ok) {
-            bad |= ST_NONFINITE;
-            const float nan = qnan_f();
-            d.forces[3 * (size_t)i] = nan;
-            d.forces[3 * (size_t)i + 1] = nan;
-            d.forces[3 * (size_t)i + 2] = nan;
-            continue;
+    for (int base = i0 + tid; base < i1; base += BIN_PER_THREAD * nth) {
+        float r[BIN_PER_THREAD][3], qv[BIN_PER_THREAD];
+#pragma unroll
+        for (int k = 0; k < BIN_PER_THREAD; ++k) {  // issue every load first
+            const int i = base + k * nth;
+            if (i < i1) {
+                r[k][0] = d.pos[3 * (size_t)i];
+                r[k][1] = d.pos[3 * (size_t)i + 1];
+                r[k][2] = d.pos[3 * (size_t)i + 2];
+                qv[k] = d.q[i];
+            }
         }
-        qacc += (unsigned long long)f2ll_rn(fabsf(q) * QABS_SCALE);
-        const int tile = ((b[0] / TILE) * d.nt2 + (b[1] / TILE)) * d.nt3 + (b[2] / TILE);
-        const float4 ra = make_float4(w[0], w[1], w[2], q);
-        const int2 rb = make_int2(b[0] | (b[1] << 10) | (b[2] << 20), i);
-        const unsigned rank = atomic_add_u32(&d.bcount[tile], 1u);
-        if (rank < (unsigned)d.cap) {
-            d.bka[(size_t)tile * d.cap + rank] = ra;
-            d.bkb[(size_t)tile * d.cap + rank] = rb;
-        } else {
-            const unsigned j = atomic_add_u32(&d.ctl->novf, 1u);
-            if (j < (unsigned)d.n) {
-                d.ova[j] = ra;
-                d.ovb[j] = rb;
-            } else {
-                bad |= ST_INTERNAL;
+        int tile[BIN_PER_THREAD];
+        float4 ra[BIN_PER_THREAD];
+        int2 rb[BIN_PER_THREAD];
+        int kind[BIN_PER_THREAD];  // 0: absent, 1: bucket, 2: overflow list, 3: invalid
+#pragma unroll
+        for (int k = 0; k < BIN_PER_THREAD; ++k) {
+            const int i = base + k * nth;
+            kind[k] = 0;
+            if (i >= i1) continue;
+            const float q = qv[k];
+            int b0, b1, b2;
+            float w0, w1, w2;
+            bool ok = isfinite(q) && fabsf(q) < 4194304.0f;  // |q| < 2^22 e
+            if (ok) ok = scaled_coord(d, r[k], 0, d.K1, b0, w0) && scaled_coord(d, r[k], 1, d.K2, b1, w1) &&
+                         scaled_coord(d, r[k], 2, d.K3, b2, w2);
+            if (!ok) {
+                kind[k] = 3;
+                continue;
+            }
+            qacc += (unsigned long long)f2ll_rn(fabsf(q) * QABS_SCALE);
+            tile[k] = ((b0 / TILE) * d.nt2 + (b1 / TILE)) * d.nt3 + (b2 / TILE);
+            ra[k] = make_float4(w0, w1, w2, q);
+            rb[k] = make_int2(b0 | (b1 << 10) | (b2 << 20), i);
+            kind[k] = fabsf(q) <= Q_TILE_MAX ? 1 : 2;
+        }
+        unsigned rank[BIN_PER_THREAD];
+#pragma unroll
+        for (int k = 0; k < BIN_PER_THREAD; ++k)  // independent atomics, all in flight together
+            if (kind[k] == 1) rank[k] = atomic_add_u32(&d.bcount[(size_t)tile[k] * BCOUNT_STRIDE], 1u);
+#pragma unroll
+        for (int k = 0; k < BIN_PER_THREAD; ++k) {
+            const int i = base + k * nth;
+            if (kind[k] == 3) {
+                bad |= ST_NONFINITE;
+                const float nan = qnan_f();
+                d.forces[3 * (size_t)i] = nan;
+                d.forces[3 * (size_t)i + 1] = nan;
+                d.forces[3 * (size_t)i + 2] = nan;
+            } else if (kind[k] == 1 && rank[k] < (unsigned)d.cap) {
+                d.bka[(size_t)tile[k] * d.cap + rank[k]] = ra[k];
+                d.bkb[(size_t)tile[k] * d.cap + rank[k]] = rb[k];
+            } else if (kind[k] != 0) {
+                const unsigned j = atomic_add_u32(&d.ctl->novf, 1u);
+                if (j < (unsigned)d.n) {
+                    d.ova[j] = ra[k];
+                    d.ovb[j] = rb[k];
+                } else {
+                    bad |= ST_INTERNAL;
+                }
             }
         }
     }
     if (bad) atomic_or_u32(&d.ctl->status, bad);
-    // CTA sum of |q| (fixed point, so the total is exact and order-independent)
-    red[tid] = qacc;
+    // CTA sum of |q| in fixed point (exact and order-independent)
+    qacc = warp_sum_u64(qacc);
+    if ((tid & 31) == 0) red[tid >> 5] = qacc;
     PME_SYNC();
-    for (int s = nth / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        PME_SYNC();
-    }
-    if (tid == 0 && red[0]) {
-        if (red[0] >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
-        else atomic_add_u64(&d.ctl->qabs, red[0]);
+    if (tid == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < (nth + 31) / 32; ++w) s += red[w];
+        if (s) {
+            if (s >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+            else atomic_add_u64(&d.ctl->qabs, s);
+        }
     }
 }
 
 // ---------------------------------------------------------------------------------------------------------
 // a2: charge spreading Q(k) = sum_i q_i theta1 theta2 theta3 (paper Sec. III-A "Charge Spreading": each
 // charge goes to the p^3 mesh points around it). A tile accumulates its atoms into a shared-memory region
-// (TILE + p - 1)^3 with 64-bit fixed-point atomics, then adds the region (including the p - 1 halo that
+// R^3 (R = TILE + p - 1) as split 32-bit fixed point, then adds the region (including the p - 1 halo that
 // overlaps neighbouring tiles, the analogue of the paper's atoms processed by every pipeline they touch)
-// into the global mesh with 64-bit integer reductions.
+// into the global int64 mesh with 64-bit integer reductions.
 
-struct TileGeom {
-    int o1, o2, o3;   // tile origin
-    int R1, R2, R3;   // region extents (tile extent + p - 1)
-};
-
-PME_DEV TileGeom tile_geom(const SysDev &d, int tile) {
-    TileGeom g;
+PME_DEV void tile_origin(const SysDev &d, int tile, int &o1, int &o2, int &o3) {
     const int t3 = tile % d.nt3, t2 = (tile / d.nt3) % d.nt2, t1 = tile / (d.nt3 * d.nt2);
-    g.o1 = t1 * TILE;
-    g.o2 = t2 * TILE;
-    g.o3 = t3 * TILE;
-    g.R1 = imin(TILE, d.K1 - g.o1) + d.p - 1;
-    g.R2 = imin(TILE, d.K2 - g.o2) + d.p - 1;
-    g.R3 = imin(TILE, d.K3 - g.o3) + d.p - 1;
-    return g;
+    o1 = t1 * TILE;
+    o2 = t2 * TILE;
+    o3 = t3 * TILE;
 }
 
 PME_DEV int wrapk(int k, int K) { return k < 0 ? k + K : (k >= K ? k - K : k); }
@@ -127,15 +184,21 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
     bspline_w<P>(ra.y, th2);
     bspline_w<P>(ra.z, th3);
     const int b1 = rb.x & 1023, b2 = (rb.x >> 10) & 1023, b3 = (rb.x >> 20) & 1023;
+#pragma unroll
     for (int j1 = 0; j1 < P; ++j1) {
         const int k1 = wrapk(b1 - j1, d.K1);
+#pragma unroll
         for (int j2 = 0; j2 < P; ++j2) {
             const int k2 = wrapk(b2 - j2, d.K2);
             const float c = ra.w * th1[j1] * th2[j2];
             unsigned long long *row = d.grid + ((size_t)k1 * d.K2 + k2) * d.K3;
 #pragma unroll
-            for (int j3 = 0; j3 < P; ++j3)
-                red_add_u64(row + wrapk(b3 - j3, d.K3), (unsigned long long)f2ll_rn(c * th3[j3] * FIX_SCALE));
+            for (int j3 = 0; j3 < P; ++j3) {
+                int h;
+                unsigned l;
+                fix_split(c * th3[j3] * FIX_SCALE, h, l);
+                red_add_u64(row + wrapk(b3 - j3, d.K3), fix_join(h, l));
+            }
         }
     }
 }
@@ -149,11 +212,16 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
             spread_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
         return;
     }
-    unsigned long long *reg = (unsigned long long *)smem;
-    const TileGeom g = tile_geom(d, item);
-    const int vol = g.R1 * g.R2 * g.R3;
-    for (int i = tid; i < vol; i += nth) reg[i] = 0ull;
-    const int cnt = imin((int)ldcg(&d.bcount[item]), d.cap);
+    constexpr int R = Region<P>::R, VOL = Region<P>::VOL, H = P - 1;
+    int *hi = (int *)smem;
+    unsigned *lo = (unsigned *)(hi + VOL);
+    int o1, o2, o3;
+    tile_origin(d, item, o1, o2, o3);
+    for (int i = tid; i < VOL; i += nth) {
+        hi[i] = 0;
+        lo[i] = 0u;
+    }
+    const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
     PME_SYNC();
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
@@ -165,29 +233,34 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
         bspline_w<P>(ra.y, th2);
         bspline_w<P>(ra.z, th3);
         // local index of the atom's highest support point; its points are l - j, j < P
-        const int l1 = (rb.x & 1023) - g.o1 + P - 1;
-        const int l2 = ((rb.x >> 10) & 1023) - g.o2 + P - 1;
-        const int l3 = ((rb.x >> 20) & 1023) - g.o3 + P - 1;
+        const int l1 = (rb.x & 1023) - o1 + H;
+        const int l2 = ((rb.x >> 10) & 1023) - o2 + H;
+        const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
 #pragma unroll
         for (int j1 = 0; j1 < P; ++j1) {
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
                 const float c = ra.w * th1[j1] * th2[j2];
-                unsigned long long *row = reg + ((l1 - j1) * g.R2 + (l2 - j2)) * g.R3 + l3;
+                const int row = ((l1 - j1) * R + (l2 - j2)) * R + l3;
 #pragma unroll
-                for (int j3 = 0; j3 < P; ++j3)
-                    atomic_add_u64(row - j3, (unsigned long long)f2ll_rn(c * th3[j3] * FIX_SCALE));
+                for (int j3 = 0; j3 < P; ++j3) {
+                    int h;
+                    unsigned l;
+                    fix_split(c * th3[j3] * FIX_SCALE, h, l);
+                    atomic_add_i32(hi + row - j3, h);
+                    atomic_add_u32_nr(lo + row - j3, l);
+                }
             }
         }
     }
     PME_SYNC();
-    const int H = P - 1;
-    for (int i = tid; i < vol; i += nth) {
-        const unsigned long long v = reg[i];
-        if (v == 0ull) continue;
-        const int i3 = i % g.R3, i2 = (i / g.R3) % g.R2, i1 = i / (g.R3 * g.R2);
-        const int k1 = wrapk(g.o1 - H + i1, d.K1), k2 = wrapk(g.o2 - H + i2, d.K2), k3 = wrapk(g.o3 - H + i3, d.K3);
-        red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, v);
+    for (int i = tid; i < VOL; i += nth) {
+        const int h = hi[i];
+        const unsigned l = lo[i];
+        if ((h | (int)l) == 0) continue;
+        const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
+        const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
+        red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
     }
 }
 
@@ -199,16 +272,27 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
 PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     const int K2 = d.K2, K3 = d.K3, H3 = d.H3, Nh = K3 / 2;
+    const float inv_h3 = 1.0f / (float)H3;
     float2 *A = (float2 *)smem;
     float2 *B = A + K2 * H3;
     float2 *twh = B + K2 * H3;   // Nh
     float2 *tw3 = twh + Nh;      // Nh + 1
     float2 *tw2 = tw3 + Nh + 1;  // K2
     ulonglong2 *g = (ulonglong2 *)(d.grid + (size_t)k1 * K2 * K3);
-    for (int i = tid; i < K2 * Nh; i += nth) {  // row k2 pairs (2n, 2n+1) -> complex z[n]
-        const ulonglong2 v = ldcg(g + i);
-        A[i] = make_float2(fix_to_float((long long)v.x), fix_to_float((long long)v.y));
-        g[i] = make_ulonglong2(0ull, 0ull);
+    const int tot = K2 * Nh;
+    for (int base = tid; base < tot; base += LOAD_BATCH * nth) {  // row k2 pairs (2n, 2n+1) -> complex z[n]
+        ulonglong2 v[LOAD_BATCH];
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u)  // all loads in flight before any use
+            if (base + u * nth < tot) v[u] = ldcg(g + base + u * nth);
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int i = base + u * nth;
+            if (i < tot) {
+                A[i] = make_float2(fix_to_float((long long)v[u].x), fix_to_float((long long)v[u].y));
+                g[i] = make_ulonglong2(0ull, 0ull);
+            }
+        }
     }
     for (int i = tid; i < Nh; i += nth) twh[i] = d.tw3h[i];
     for (int i = tid; i <= Nh; i += nth) tw3[i] = d.tw3[i];
@@ -218,7 +302,7 @@ PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
     float2 *X = (Z == A) ? B : A;
     // split: X[m] = E[m] + W_K3^m O[m], E = (Z[m] + conj Z[Nh-m]) / 2, O = -i (Z[m] - conj Z[Nh-m]) / 2
     for (int i = tid; i < K2 * H3; i += nth) {
-        const int k2 = i / H3, m = i - k2 * H3;
+        const int k2 = fdiv(i, inv_h3), m = i - k2 * H3;
         const float2 *z = Z + k2 * Nh;
         const float2 zm = z[m == Nh ? 0 : m];
         const float2 zc = cconj(z[m == 0 ? 0 : Nh - m]);
@@ -233,8 +317,9 @@ PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
 }
 
 // ---------------------------------------------------------------------------------------------------------
-// a4: pencils m2 — FFT along k1, multiply by the influence function B*C (the paper's "Green's function"
-// step between Z and Z^-1, Sec. III-A "FFT"), reduce energy and virial, inverse FFT along k1.
+// a4: pencils (m2, a chunk of m3 columns) — FFT along k1, multiply by the influence function B*C (the
+// paper's "Green's function" step between Z and Z^-1, Sec. III-A "FFT"), reduce energy and virial, inverse
+// FFT along k1.
 //
 // Energy and virial over the half spectrum: each m3 in (0, K3/2) stands for itself and its conjugate
 // partner (weight 2), m3 = 0 and K3/2 have weight 1. Per-thread sums are double-float (about 44 bits);
@@ -259,27 +344,56 @@ PME_DEV void virial_weights(const SysDev &d, float mt1, float mt2, float mt3, fl
 // signed frequency of index m on a K-point axis: m for m <= K/2, else m - K (K/2 maps to +K/2)
 PME_DEV int signed_freq(int m, int K) { return 2 * m <= K ? m : m - K; }
 
-PME_DEV void stage_conv(const SysDev &d, int m2, void *smem) {
+#if defined(PME_HOST_EMULATION)
+inline DF warp_sum_df(DF v) { return v; }
+#else
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF other;
+        other.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        other.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, other);
+    }
+    return v;
+}
+#endif
+
+PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     const int K1 = d.K1, K2 = d.K2, K3 = d.K3, H3 = d.H3;
+    const int m2 = item / d.nchunk3;
+    const int c0 = (item - m2 * d.nchunk3) * CONV_COLS;
+    const int C = imin(CONV_COLS, H3 - c0);
+    const float inv_c = 1.0f / (float)C;
     float2 *A = (float2 *)smem;
-    float2 *B = A + K1 * H3;
-    float2 *tw1 = B + K1 * H3;
-    for (int i = tid; i < K1 * H3; i += nth) {
-        const int k1 = i / H3, m3 = i - k1 * H3;
-        A[i] = ldcg(d.spec + ((size_t)k1 * K2 + m2) * H3 + m3);
+    float2 *B = A + K1 * CONV_COLS;
+    float2 *tw1 = B + K1 * CONV_COLS;
+    for (int base = tid; base < K1 * C; base += LOAD_BATCH * nth) {
+        float2 v[LOAD_BATCH];
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int i = base + u * nth;
+            if (i < K1 * C) {
+                const int k1 = fdiv(i, inv_c), mc = i - k1 * C;
+                v[u] = ldcg(d.spec + ((size_t)k1 * K2 + m2) * H3 + c0 + mc);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u)
+            if (base + u * nth < K1 * C) A[base + u * nth] = v[u];
     }
     for (int i = tid; i < K1; i += nth) tw1[i] = d.tw1[i];
     PME_SYNC();
-    float2 *X = fft_batch<false>(A, B, K1, H3, H3, 1, tw1);
+    float2 *X = fft_batch<false>(A, B, K1, C, C, 1, tw1);
     DF acc[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) acc[c].hi = acc[c].lo = 0.f;
-    const float2 *bc = d.bc + (size_t)m2 * K1 * H3;
+    const float2 *bc = d.bc + (size_t)m2 * K1 * H3 + c0;
     const int mt2 = signed_freq(m2, K2);
-    for (int i = tid; i < K1 * H3; i += nth) {
-        const int m1 = i / H3, m3 = i - m1 * H3;
-        const float2 t = bc[i];  // B*C as hi + lo
+    for (int i = tid; i < K1 * C; i += nth) {
+        const int m1 = fdiv(i, inv_c), mc = i - m1 * C, m3 = c0 + mc;
+        const float2 t = bc[(size_t)m1 * H3 + mc];  // B*C as hi + lo
         float2 x = X[i];
         if ((m1 | m2 | m3) != 0) {
             const bool self = (m3 == 0 || 2 * m3 == K3);  // conjugate partner is another point of this plane
@@ -307,49 +421,68 @@ PME_DEV void stage_conv(const SysDev &d, int m2, void *smem) {
         X[i] = x;
     }
     PME_SYNC();
-    float2 *Y = fft_batch<true>(X, (X == A) ? B : A, K1, H3, H3, 1, tw1);
-    for (int i = tid; i < K1 * H3; i += nth) {
-        const int k1 = i / H3, m3 = i - k1 * H3;
-        d.spec[((size_t)k1 * K2 + m2) * H3 + m3] = Y[i];
+    float2 *Y = fft_batch<true>(X, (X == A) ? B : A, K1, C, C, 1, tw1);
+    for (int i = tid; i < K1 * C; i += nth) {
+        const int k1 = fdiv(i, inv_c), mc = i - k1 * C;
+        d.spec[((size_t)k1 * K2 + m2) * H3 + c0 + mc] = Y[i];
     }
     PME_SYNC();
-    // CTA reduction of the 7 double-float sums (fixed tree order)
+    // CTA reduction of the 7 double-float sums: warp shuffles, then one slot per warp
     DF *red = (DF *)smem;
 #pragma unroll
-    for (int c = 0; c < 7; ++c) red[c * nth + tid] = acc[c];
-    PME_SYNC();
-    for (int s = nth / 2; s > 0; s >>= 1) {
-        if (tid < s) {
+    for (int c = 0; c < 7; ++c) acc[c] = warp_sum_df(acc[c]);
+    if ((tid & 31) == 0) {
 #pragma unroll
-            for (int c = 0; c < 7; ++c) red[c * nth + tid] = df_add(red[c * nth + tid], red[c * nth + tid + s]);
-        }
-        PME_SYNC();
+        for (int c = 0; c < 7; ++c) red[(tid >> 5) * 7 + c] = acc[c];
     }
+    PME_SYNC();
     PME_SHARED unsigned last_flag;
+    DF *part = (DF *)d.partials;  // 8 double-float slots per item
     if (tid == 0) {
-        for (int c = 0; c < 7; ++c) d.partials[(size_t)m2 * 8 + c] = (double)red[c * nth].hi + (double)red[c * nth].lo;
+        const int nw = (nth + 31) / 32;
+        for (int c = 0; c < 7; ++c) {
+            DF s = red[c];
+            for (int w = 1; w < nw; ++w) s = df_add(s, red[w * 7 + c]);
+            part[(size_t)item * 8 + c] = s;
+        }
         PME_FENCE();
         const unsigned done = atomic_add_u32(&d.ctl->conv_done, 1u);
-        last_flag = (done == (unsigned)K2 - 1u) ? 1u : 0u;
+        last_flag = (done == (unsigned)d.nconv - 1u) ? 1u : 0u;
     }
     PME_SYNC();
     if (last_flag) {
-        // last item: FP64 sum over the K2 partials in a fixed two-level order
+        // Last item: sum all item partials. Slot v (of REDUCE_SLOTS) takes items v, v + REDUCE_SLOTS, ...
+        // in order; the slots then meet in a fixed binary tree. The order does not depend on the block
+        // size, so every launch configuration gives the same bits.
         PME_FENCE();
-        double *dred = (double *)smem;  // 7 x 8 partial sums
-        for (int r = tid; r < 56; r += nth) {
-            const int c = r >> 3, part = r & 7;
-            double s = 0.0;
-            for (int it = part; it < K2; it += 8) s += ldcg(d.partials + (size_t)it * 8 + c);
-            dred[r] = s;
+        DF *slot = (DF *)smem;  // REDUCE_SLOTS x 7
+        for (int v = tid; v < REDUCE_SLOTS; v += nth) {
+            DF s[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) s[c].hi = s[c].lo = 0.f;
+            for (int it = v; it < d.nconv; it += REDUCE_SLOTS) {
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    const float2 p2 = ldcg((const float2 *)(part + (size_t)it * 8 + c));
+                    DF pv;
+                    pv.hi = p2.x;
+                    pv.lo = p2.y;
+                    s[c] = df_add(s[c], pv);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 7; ++c) slot[v * 7 + c] = s[c];
         }
         PME_SYNC();
-        if (tid == 0) {
-            for (int c = 0; c < 7; ++c) {
-                double s = 0.0;
-                for (int part = 0; part < 8; ++part) s += dred[c * 8 + part];
-                d.ev[c] = s;
+        for (int h = REDUCE_SLOTS / 2; h > 0; h >>= 1) {
+            for (int r = tid; r < h * 7; r += nth) {
+                const int v = r / 7, c = r - v * 7;
+                slot[v * 7 + c] = df_add(slot[v * 7 + c], slot[(v + h) * 7 + c]);
             }
+            PME_SYNC();
+        }
+        if (tid == 0) {
+            for (int c = 0; c < 7; ++c) d.ev[c] = (double)slot[c].hi + (double)slot[c].lo;
             if (ldcg(&d.ctl->qabs) >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
             d.ctl->qabs = 0ull;
             d.ctl->conv_done = 0u;
@@ -364,13 +497,14 @@ PME_DEV void stage_conv(const SysDev &d, int m2, void *smem) {
 PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     const int K2 = d.K2, K3 = d.K3, H3 = d.H3, Nh = K3 / 2;
+    const float inv_nh = 1.0f / (float)Nh;
     float2 *A = (float2 *)smem;
     float2 *B = A + K2 * H3;
     float2 *twh = B + K2 * H3;
     float2 *tw3 = twh + Nh;
     float2 *tw2 = tw3 + Nh + 1;
     const float2 *in = d.spec + (size_t)k1 * K2 * H3;
-    for (int i = tid; i < K2 * H3; i += nth) A[i] = ldcg(in + i);
+    copy_batched(A, in, K2 * H3);
     for (int i = tid; i < Nh; i += nth) twh[i] = d.tw3h[i];
     for (int i = tid; i <= Nh; i += nth) tw3[i] = d.tw3[i];
     for (int i = tid; i < K2; i += nth) tw2[i] = d.tw2[i];
@@ -379,7 +513,7 @@ PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
     float2 *Z = (Y == A) ? B : A;
     // Z[m] = (X[m] + conj X[Nh-m]) + i (X[m] - conj X[Nh-m]) exp(+2 pi i m / K3), m < Nh
     for (int i = tid; i < K2 * Nh; i += nth) {
-        const int k2 = i / Nh, m = i - k2 * Nh;
+        const int k2 = fdiv(i, inv_nh), m = i - k2 * Nh;
         const float2 *x = Y + k2 * H3;
         const float2 xm = x[m], xc = cconj(x[Nh - m]);
         const float2 a = cadd(xm, xc);
@@ -413,8 +547,10 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
     bspline_wd<P>(ra.z, th3, dth3);
     const int b1 = rb.x & 1023, b2 = (rb.x >> 10) & 1023, b3 = (rb.x >> 20) & 1023;
     float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
     for (int j1 = 0; j1 < P; ++j1) {
         const int k1 = wrapk(b1 - j1, d.K1);
+#pragma unroll
         for (int j2 = 0; j2 < P; ++j2) {
             const int k2 = wrapk(b2 - j2, d.K2);
             const float *row = d.phi + ((size_t)k1 * d.K2 + k2) * d.K3;
@@ -441,18 +577,28 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         for (unsigned a = (unsigned)((item - d.ntiles) * nth + tid); a < novf; a += (unsigned)(OVF_ITEMS * nth))
             gather_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
     } else {
+        constexpr int R = Region<P>::R, VOL = Region<P>::VOL, H = P - 1;
         float *reg = (float *)smem;
-        const TileGeom g = tile_geom(d, item);
-        const int vol = g.R1 * g.R2 * g.R3;
-        const int H = P - 1;
-        for (int i = tid; i < vol; i += nth) {
-            const int i3 = i % g.R3, i2 = (i / g.R3) % g.R2, i1 = i / (g.R3 * g.R2);
-            const int k1 = wrapk(g.o1 - H + i1, d.K1), k2 = wrapk(g.o2 - H + i2, d.K2), k3 = wrapk(g.o3 - H + i3, d.K3);
-            reg[i] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
+        int o1, o2, o3;
+        tile_origin(d, item, o1, o2, o3);
+        for (int base = tid; base < VOL; base += LOAD_BATCH * nth) {
+            float v[LOAD_BATCH];
+#pragma unroll
+            for (int u = 0; u < LOAD_BATCH; ++u) {
+                const int i = base + u * nth;
+                if (i < VOL) {
+                    const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
+                    const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
+                    v[u] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < LOAD_BATCH; ++u)
+                if (base + u * nth < VOL) reg[base + u * nth] = v[u];
         }
-        const int cnt = imin((int)ldcg(&d.bcount[item]), d.cap);
+        const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
         PME_SYNC();
-        if (tid == 0) d.bcount[item] = 0u;  // consumed: ready for the next evaluation's binning
+        if (tid == 0) d.bcount[(size_t)item * BCOUNT_STRIDE] = 0u;  // consumed: ready for the next binning
         const float4 *A = d.bka + (size_t)item * d.cap;
         const int2 *B = d.bkb + (size_t)item * d.cap;
         for (int a = tid; a < cnt; a += nth) {
@@ -462,15 +608,15 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
             bspline_wd<P>(ra.x, th1, dth1);
             bspline_wd<P>(ra.y, th2, dth2);
             bspline_wd<P>(ra.z, th3, dth3);
-            const int l1 = (rb.x & 1023) - g.o1 + H;
-            const int l2 = ((rb.x >> 10) & 1023) - g.o2 + H;
-            const int l3 = ((rb.x >> 20) & 1023) - g.o3 + H;
+            const int l1 = (rb.x & 1023) - o1 + H;
+            const int l2 = ((rb.x >> 10) & 1023) - o2 + H;
+            const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
             float g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
             for (int j1 = 0; j1 < P; ++j1) {
 #pragma unroll
                 for (int j2 = 0; j2 < P; ++j2) {
-                    const float *row = reg + ((l1 - j1) * g.R2 + (l2 - j2)) * g.R3 + l3;
+                    const float *row = reg + ((l1 - j1) * R + (l2 - j2)) * R + l3;
                     float s = 0.f, ds = 0.f;
 #pragma unroll
                     for (int j3 = 0; j3 < P; ++j3) {

@@ -58,14 +58,14 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     make_twiddles(K[1], K[1], s.tw.data() + K1);
     make_twiddles((int)Nh, (int)Nh, s.tw.data() + K1 + K2);
     make_twiddles(K[2], (int)Nh + 1, s.tw.data() + K1 + K2 + Nh);
-    s.bcount.assign(d.ntiles, 0u);
-    s.partials.assign(K2 * 8, 0.0);
+    s.bcount.assign(bcount_bytes(d.ntiles) / sizeof(unsigned), 0u);
+    s.partials.assign(partials_bytes(d) / sizeof(double), 0.0);
     const int cap = cap_override > 0 ? cap_override : bucket_capacity(n > 0 ? n : 1, d.ntiles);
     s.bka.resize((size_t)d.ntiles * cap);
     s.bkb.resize((size_t)d.ntiles * cap);
     s.ova.resize(n > 0 ? n : 1);
     s.ovb.resize(n > 0 ? n : 1);
-    size_t sm = std::max({smem_bin(1), smem_spread(p), smem_gather(p), smem_slab(K[1], K[2]), smem_conv(K[0], K[2], 1)});
+    size_t sm = std::max({smem_bin(1), smem_spread(p), smem_gather(p), smem_slab(K[1], K[2]), smem_conv(K[0], 1)});
     s.smem.assign(sm, 0);
     d.grid = s.grid.data();
     d.spec = s.spec.data();
@@ -102,7 +102,7 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
         }
         if (grid_out) memcpy(grid_out, s.grid.data(), s.grid.size() * 8);
         for (int it = 0; it < K[0]; ++it) stage_fwd(d, it, sp);
-        for (int it = 0; it < K[1]; ++it) stage_conv(d, it, sp);
+        for (int it = 0; it < d.nconv; ++it) stage_conv(d, it, sp);
         for (int it = 0; it < K[0]; ++it) stage_inv(d, it, sp);
         for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
             switch (p) {

@@ -1,0 +1,183 @@
+"""GPU tests of the batched persistent launch (many uneven systems in one kernel) and the serving loop.
+
+Each system's result in a batch or a served mix must equal its result alone (pme_compute) within the
+parity tolerances; the work decomposition of a system is the same in every launch, so the results are
+expected to be bit-identical, which the tests also check.
+"""
+import numpy as np
+import pytest
+
+from paper_2009_12617_gb300 import workloads as wl
+
+from helpers import E_REL_TOL, F_RMS_TOL, V_TOL, rel_energy, rel_virial, rms_force
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pme():
+    from paper_2009_12617_gb300 import build
+    from paper_2009_12617_gb300 import pme as p
+
+    build.build_library()
+    p.load_library()
+    return p
+
+
+@pytest.fixture(scope="module")
+def systems(pme):
+    """12 uneven water-like boxes (atom counts log-uniform in [1024, 32768]; meshes 32..64), each with its
+    own plan and its single-system result."""
+    dev = torch.device("cuda:0")
+    out = []
+    for s in wl.batch_systems(count=12, seed=7):
+        plan = pme.pme_create(s.K, s.p, s.beta, s.box)
+        pos = torch.from_numpy(s.pos).to(dev)
+        q = torch.from_numpy(s.q).to(dev)
+        F = torch.empty_like(pos)
+        E, V = pme.pme_compute(plan, pos, q, F)
+        out.append(dict(sys=s, plan=plan, pos=pos, q=q, F=F.cpu().numpy(), E=E, V=V))
+    yield out
+    for o in out:
+        pme.pme_destroy(o["plan"])
+
+
+def packed(systems):
+    pos = torch.cat([o["pos"] for o in systems])
+    q = torch.cat([o["q"] for o in systems])
+    return pos, q, [o["sys"].n for o in systems]
+
+
+def check_same(o, F, E, V, exact):
+    assert rel_energy(E, o["E"]) < E_REL_TOL
+    assert rms_force(F, o["F"].astype(np.float64)) < F_RMS_TOL
+    assert rel_virial(V, o["V"]) < V_TOL
+    if exact:
+        assert E == o["E"] and np.array_equal(V, o["V"]) and np.array_equal(F, o["F"])
+
+
+def test_batch_matches_single_systems(pme, systems, oracle_mod):
+    pos, q, ns = packed(systems)
+    F = torch.full_like(pos, float("nan"))
+    ev = torch.zeros((len(systems), 7), dtype=torch.float64, device="cuda:0")
+    b = pme.pme_batch_create([o["plan"] for o in systems], ns)
+    try:
+        for rep in range(3):  # graph replays reuse and reset every counter
+            pme.pme_batch_enqueue(b, pos, q, F, ev)
+            pme.pme_batch_sync(b)
+            Fh, evh = F.cpu().numpy(), ev.cpu().numpy()
+            off = 0
+            for i, o in enumerate(systems):
+                check_same(o, Fh[off:off + ns[i]], evh[i, 0], evh[i, 1:], exact=True)
+                off += ns[i]
+        # and the batch agrees with the oracle on one system
+        s = systems[0]["sys"]
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
+        assert rel_energy(evh[0, 0], r["energy"]) < E_REL_TOL
+        assert rms_force(Fh[:ns[0]], r["forces"]) < F_RMS_TOL
+    finally:
+        pme.pme_batch_destroy(b)
+
+
+def test_batch_new_pointers_recapture(pme, systems):
+    sub = systems[:4]
+    pos, q, ns = packed(sub)
+    b = pme.pme_batch_create([o["plan"] for o in sub], ns)
+    try:
+        for _ in range(2):  # fresh output buffers each time: the launch is re-recorded
+            F = torch.empty_like(pos)
+            ev = torch.zeros((len(sub), 7), dtype=torch.float64, device="cuda:0")
+            pme.pme_batch_enqueue(b, pos, q, F, ev)
+            pme.pme_batch_sync(b)
+            off = 0
+            for i, o in enumerate(sub):
+                check_same(o, F.cpu().numpy()[off:off + ns[i]], ev[i, 0].item(), ev[i, 1:].cpu().numpy(), exact=True)
+                off += ns[i]
+    finally:
+        pme.pme_batch_destroy(b)
+
+
+def test_batch_rejects_shared_plan_and_mixed_order(pme, systems):
+    p0 = systems[0]["plan"]
+    with pytest.raises(pme.PMEError) as ei:
+        pme.pme_batch_create([p0, p0], [10, 10])
+    assert ei.value.status == pme.PME_EINVAL
+    other = pme.pme_create((32, 32, 32), 6, 0.34, np.eye(3) * 30.0)
+    try:
+        with pytest.raises(pme.PMEError) as ei:
+            pme.pme_batch_create([p0, other], [10, 10])
+        assert ei.value.status == pme.PME_EINVAL
+    finally:
+        pme.pme_destroy(other)
+
+
+def test_batch_stuck_dependency_times_out_and_recovers(pme, systems):
+    """Test hook: one list entry waits on a counter nothing advances. The bounded wait gives up after 50 ms,
+    the launch ends, pme_batch_sync reports PME_ETIMEOUT, and the next launch is correct again."""
+    sub = systems[:3]
+    pos, q, ns = packed(sub)
+    F = torch.empty_like(pos)
+    ev = torch.zeros((len(sub), 7), dtype=torch.float64, device="cuda:0")
+    b = pme.pme_batch_create([o["plan"] for o in sub], ns)
+    try:
+        pme.pme_batch_debug_stall(b, True, 50_000_000)
+        pme.pme_batch_enqueue(b, pos, q, F, ev)
+        with pytest.raises(pme.PMEError) as ei:
+            pme.pme_batch_sync(b)
+        assert ei.value.status == pme.PME_ETIMEOUT
+        pme.pme_batch_debug_stall(b, False)
+        pme.pme_batch_enqueue(b, pos, q, F, ev)
+        pme.pme_batch_sync(b)
+        off = 0
+        for i, o in enumerate(sub):
+            check_same(o, F.cpu().numpy()[off:off + ns[i]], ev[i, 0].item(), ev[i, 1:].cpu().numpy(), exact=True)
+            off += ns[i]
+    finally:
+        pme.pme_batch_destroy(b)
+
+
+def test_server_results_same_alone_and_in_mix(pme, systems):
+    """Every system submitted twice (so requests on one plan queue behind each other) into a server whose
+    waves mix all systems; each result equals the system's result alone."""
+    srv = pme.pme_server_create(1 << 34, 64)
+    try:
+        tickets = []
+        for rep in range(2):
+            for o in systems:
+                F = torch.full_like(o["pos"], float("nan"))
+                t = pme.pme_submit(srv, o["plan"], o["pos"], o["q"], F)
+                assert t is not None
+                tickets.append((o, F, t))
+        for o, F, t in tickets:
+            assert pme.pme_poll(srv, t, block=True) == pme.PME_OK
+            check_same(o, F.cpu().numpy(), t.energy.value, np.array(t.virial[:]), exact=True)
+        st = pme.pme_server_stats(srv)
+        assert st["completed"] == len(tickets) and st["waves"] >= 2 and st["p99_us"] >= st["p50_us"] > 0
+    finally:
+        pme.pme_server_destroy(srv)
+
+
+def test_server_admission_limits(pme, systems):
+    o = systems[0]
+    nbytes = pme.pme_plan_device_bytes(o["plan"])
+    srv = pme.pme_server_create(nbytes - 1, 4)  # budget below one plan
+    try:
+        F = torch.empty_like(o["pos"])
+        with pytest.raises(pme.PMEError) as ei:
+            pme.pme_submit(srv, o["plan"], o["pos"], o["q"], F)
+        assert ei.value.status == pme.PME_ENOMEM
+    finally:
+        pme.pme_server_destroy(srv)
+    srv = pme.pme_server_create(nbytes, 2)  # one plan at a time, two slots
+    try:
+        outs = [torch.empty_like(o["pos"]) for _ in range(3)]
+        t1 = pme.pme_submit(srv, o["plan"], o["pos"], o["q"], outs[0])
+        t2 = pme.pme_submit(srv, o["plan"], o["pos"], o["q"], outs[1])
+        assert t1 is not None and t2 is not None
+        assert pme.pme_submit(srv, o["plan"], o["pos"], o["q"], outs[2]) is None  # PME_EAGAIN: slots full
+        for t, F in ((t1, outs[0]), (t2, outs[1])):
+            assert pme.pme_poll(srv, t, block=True) == pme.PME_OK
+            check_same(o, F.cpu().numpy(), t.energy.value, np.array(t.virial[:]), exact=True)
+    finally:
+        pme.pme_server_destroy(srv)
