@@ -164,8 +164,9 @@ size_t batch_smem(const std::vector<SysDev> &sys) {
     size_t m = smem_bin(NT_BATCH);
     for (const SysDev &d : sys) {
         m = std::max(m, smem_spread(d.p));
-        m = std::max(m, smem_gather(d.p));
+        m = std::max(m, smem_gather_all(d.p));
         m = std::max(m, smem_slab(d.K2, d.K3));
+        m = std::max(m, smem_inv(d.K2, d.K3));
         m = std::max(m, smem_conv(d.K1, NT_BATCH));
     }
     return m;

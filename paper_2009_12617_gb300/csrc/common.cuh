@@ -43,7 +43,7 @@ constexpr float FIX_INV = 9.094947017729282379150390625e-13f;  // 2^-40
 constexpr float QABS_SCALE = 16777216.0f;                // 2^24
 constexpr unsigned long long QABS_LIMIT = 1ull << 46;    // 2^22 e in 2^24 units
 constexpr int BIN_PER_THREAD = 4;           // atoms per thread in the binning stage (for memory-level parallelism)
-constexpr int BIN_CHUNK = 256 * BIN_PER_THREAD;  // atoms per binning work item
+constexpr int BIN_CHUNK = 128 * BIN_PER_THREAD;  // atoms per binning work item
 constexpr int OVF_ITEMS = 8;     // extra spread / gather work items that handle bucket-overflow atoms
 constexpr int MAX_K = 128;
 // Tile counters sit on separate 128-byte lines so the binning atomics spread over the L2 slices.
@@ -58,7 +58,7 @@ constexpr int CAP_MAX = 512;
 constexpr int CONV_COLS = 8;
 // Independent global loads each thread keeps in flight when staging data into shared memory.
 constexpr int LOAD_BATCH = 8;
-// Slots of the fixed-order final energy / virial reduction (a power of two).
+// Slots of the fixed-order final energy / virial reduction (a power of two, >= MAX_K / 2).
 constexpr int REDUCE_SLOTS = 64;
 
 enum StatusBits : unsigned {
@@ -74,9 +74,8 @@ struct Ctl {
     unsigned status;            // StatusBits, latched until the host reads and clears it
     unsigned novf;              // atoms that did not fit in their tile's bucket
     unsigned long long qabs;    // sum |q| in 2^-24 e units
-    unsigned conv_done;         // finished k1-pencil items (the last one reduces energy / virial)
-    unsigned gather_done;       // finished gather items (the last one resets novf)
-    unsigned pad[2];
+    unsigned novf_gather;       // copy of novf taken by the spreading stage for the force stage
+    unsigned pad[3];
     double ev[8];               // energy, virial xx yy zz xy xz yz (internal copy for synchronous calls)
 };
 
@@ -90,6 +89,7 @@ struct SysDev {
     int nbin;                    // binning work items = ceil(n / BIN_CHUNK)
     int nchunk3;                 // influence-stage column chunks = ceil(H3 / CONV_COLS)
     int nconv;                   // influence-stage work items = K2 * nchunk3
+    int pdl_late;                // launch option of the per-stage kernels (see kernels.cu)
     float kinv[3];               // 1 / K_alpha
     // u_alpha = sum_j r_j C[j][alpha], C[j][alpha] = K_alpha a*_alpha[j], as an unevaluated float sum
     // chi + clo (about 48 significant bits), index 3*j + alpha.
@@ -114,7 +114,7 @@ struct SysDev {
     unsigned *bcount;            // atoms binned per tile, at tile * BCOUNT_STRIDE
     float4 *ova;                 // overflow records, capacity n
     int2 *ovb;
-    double *partials;            // 8 double-float (hi, lo) slots per influence-stage work item
+    double *partials;            // 8 double-float (hi, lo) slots per influence-stage item, then K1 level-1 slots
     Ctl *ctl;
 };
 
@@ -133,6 +133,8 @@ inline float fmul_rn(float a, float b) { return a * b; }
 inline float fadd_rn(float a, float b) { return a + b; }
 inline float fsub_rn(float a, float b) { return a - b; }
 inline long long f2ll_rn(float x) { return llrintf(x); }
+inline int f2i_rd(float x) { return (int)floorf(x); }
+inline int f2i_rn(float x) { return (int)rintf(x); }
 #else
 template <class T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned atomic_add_u32(unsigned *p, unsigned v) { return atomicAdd(p, v); }
@@ -145,6 +147,8 @@ __device__ __forceinline__ float fmul_rn(float a, float b) { return __fmul_rn(a,
 __device__ __forceinline__ float fadd_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fsub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ long long f2ll_rn(float x) { return __float2ll_rn(x); }
+__device__ __forceinline__ int f2i_rd(float x) { return __float2int_rd(x); }
+__device__ __forceinline__ int f2i_rn(float x) { return __float2int_rn(x); }
 #endif
 
 PME_DEV int imin(int a, int b) { return a < b ? a : b; }
@@ -263,7 +267,20 @@ PME_DEV void bspline_order_up(float w, float *th, int n) {
     th[0] = w * th[0];
 }
 
-PME_DEV constexpr float factorial_f(int k) { return k <= 1 ? 1.0f : (float)k * factorial_f(k - 1); }
+constexpr double factorial_d(int k) { return k <= 1 ? 1.0 : (double)k * factorial_d(k - 1); }
+
+// x / k! as x * (hi + lo), the reciprocal of k! split into two floats (about 48 bits): one rounding at the
+// end, so the result is unbiased (a single rounded reciprocal would scale every atom alike).
+template <int K>
+struct InvFact {
+    static constexpr double r = 1.0 / factorial_d(K);
+    static constexpr float hi = (float)r;
+    static constexpr float lo = (float)(r - (double)hi);
+};
+template <int K>
+PME_DEV float div_fact(float x) {
+    return fmaf(x, InvFact<K>::hi, x * InvFact<K>::lo);
+}
 
 template <int P>
 PME_DEV void bspline_w(float w, float *th) {
@@ -271,9 +288,8 @@ PME_DEV void bspline_w(float w, float *th) {
     th[1] = 1.0f - w;
 #pragma unroll
     for (int n = 3; n <= P; ++n) bspline_order_up<P>(w, th, n);
-    const float f = factorial_f(P - 1);
 #pragma unroll
-    for (int j = 0; j < P; ++j) th[j] = th[j] / f;
+    for (int j = 0; j < P; ++j) th[j] = div_fact<P - 1>(th[j]);
 }
 
 template <int P>
@@ -282,15 +298,13 @@ PME_DEV void bspline_wd(float w, float *th, float *dth) {
     th[1] = 1.0f - w;
 #pragma unroll
     for (int n = 3; n <= P - 1; ++n) bspline_order_up<P>(w, th, n);
-    const float fd = factorial_f(P - 2);
-    dth[0] = th[0] / fd;
+    dth[0] = div_fact<P - 2>(th[0]);
 #pragma unroll
-    for (int j = 1; j <= P - 2; ++j) dth[j] = (th[j] - th[j - 1]) / fd;
-    dth[P - 1] = -th[P - 2] / fd;
+    for (int j = 1; j <= P - 2; ++j) dth[j] = div_fact<P - 2>(th[j] - th[j - 1]);
+    dth[P - 1] = -div_fact<P - 2>(th[P - 2]);
     bspline_order_up<P>(w, th, P);
-    const float f = factorial_f(P - 1);
 #pragma unroll
-    for (int j = 0; j < P; ++j) th[j] = th[j] / f;
+    for (int j = 0; j < P; ++j) th[j] = div_fact<P - 1>(th[j]);
 }
 
 }  // namespace pme

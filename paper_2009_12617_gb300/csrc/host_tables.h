@@ -173,6 +173,6 @@ inline int bucket_capacity(int64_t n, int ntiles) {
 
 // Bytes of the padded tile-counter array and of the influence-stage partials.
 inline size_t bcount_bytes(int ntiles) { return (size_t)ntiles * BCOUNT_STRIDE * sizeof(unsigned); }
-inline size_t partials_bytes(const SysDev &d) { return (size_t)d.nconv * 8 * sizeof(double); }
+inline size_t partials_bytes(const SysDev &d) { return ((size_t)d.nconv + d.K1) * 8 * sizeof(float2); }
 
 }  // namespace pme

@@ -7,36 +7,81 @@
 
 namespace pme {
 
-__global__ void __launch_bounds__(NT_MESH) k_bin(SysDev d) {
+// Programmatic dependent launch (optional, launch_mode): a stage kernel launched with programmatic stream
+// serialisation waits for its predecessor to complete (with its memory visible) before touching any data,
+// and lets its successor start launching either at its own start (mode 1) or once each CTA has finished
+// its work (mode 2), so the successor's launch latency overlaps this kernel. Without the launch attribute
+// (mode 0) both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+struct PdlScope {  // trigger at entry (early) or at exit (late); the kernel argument picks
+    bool late;
+    __device__ explicit PdlScope(bool l) : late(l) {
+        if (!late) pdl_trigger();
+        pdl_wait();
+    }
+    __device__ ~PdlScope() {
+        if (late) pdl_trigger();
+    }
+};
+
+static int g_launch_mode = 2;  // measured fastest on GB300 (late trigger)
+void set_launch_mode(int mode) { g_launch_mode = mode; }
+int launch_mode() { return g_launch_mode; }
+
+__global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
     stage_bin(d, blockIdx.x, smem);
 }
 
 template <int P>
 __global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
     stage_spread<P>(d, blockIdx.x, smem);
 }
 
-__global__ void __launch_bounds__(NT_MESH) k_fwd(SysDev d) {
+__global__ void __launch_bounds__(NT_SLAB) k_fwd(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
     stage_fwd(d, blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_CONV) k_conv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
     stage_conv(d, blockIdx.x, smem);
 }
 
-__global__ void __launch_bounds__(NT_MESH) k_inv(SysDev d) {
+__global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
     stage_inv(d, blockIdx.x, smem);
 }
 
 template <int P>
 __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
     stage_gather<P>(d, blockIdx.x, smem);
+}
+
+static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       const SysDev &d0) {
+    SysDev d = d0;
+    d.pdl_late = g_launch_mode == 2 ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_launch_mode ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, d);
 }
 
 static cudaError_t set_smem_limit(const void *fn, size_t bytes) {
@@ -54,17 +99,17 @@ cudaError_t configure_kernels() {
 
 template <int P>
 static void launch_tiles_spread(const SysDev &d, cudaStream_t s) {
-    k_spread<P><<<d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P), s>>>(d);
+    launch_pdl(k_spread<P>, d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P), s, d);
 }
 template <int P>
 static void launch_tiles_gather(const SysDev &d, cudaStream_t s) {
-    k_gather<P><<<d.ntiles + OVF_ITEMS, NT_TILE, smem_gather(P), s>>>(d);
+    launch_pdl(k_gather<P>, d.ntiles + OVF_ITEMS, NT_TILE, smem_gather_all(P), s, d);
 }
 
 void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
     switch (stage) {
         case STAGE_BIN:
-            k_bin<<<d.nbin > 0 ? d.nbin : 1, NT_MESH, smem_bin(NT_MESH), s>>>(d);
+            launch_pdl(k_bin, d.nbin > 0 ? d.nbin : 1, NT_BIN, smem_bin(NT_BIN), s, d);
             break;
         case STAGE_SPREAD:
             if (d.p == 4) launch_tiles_spread<4>(d, s);
@@ -72,13 +117,13 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             else launch_tiles_spread<8>(d, s);
             break;
         case STAGE_FWD:
-            k_fwd<<<d.K1, NT_MESH, smem_slab(d.K2, d.K3), s>>>(d);
+            launch_pdl(k_fwd, d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d);
             break;
         case STAGE_CONV:
-            k_conv<<<d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s>>>(d);
+            launch_pdl(k_conv, d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d);
             break;
         case STAGE_INV:
-            k_inv<<<d.K1, NT_MESH, smem_slab(d.K2, d.K3), s>>>(d);
+            launch_pdl(k_inv, d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d);
             break;
         default:
             if (d.p == 4) launch_tiles_gather<4>(d, s);

@@ -7,10 +7,16 @@
 
 namespace pme {
 
-constexpr int NT_MESH = 256;   // threads per CTA for binning and the FFT / influence stages
-constexpr int NT_TILE = 128;   // threads per CTA for spreading and force interpolation
+constexpr int NT_BIN = 128;    // threads per CTA for binning (BIN_CHUNK atoms per CTA)
+constexpr int NT_SLAB = 512;   // threads per CTA for the forward / inverse slab FFT stages
+constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interpolation (two per atom)
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
 constexpr size_t MAX_SMEM_BYTES = 226 * 1024;  // opt-in limit is 227 KB including static shared memory
+
+// Launch mode of the per-stage kernels: 0 plain, 1 programmatic dependent launch triggered at kernel entry,
+// 2 triggered at CTA exit. Process-wide; affects launches recorded afterwards.
+void set_launch_mode(int mode);
+int launch_mode();
 
 // Raise the dynamic shared-memory limit of the large-footprint kernels (once per device).
 cudaError_t configure_kernels();

@@ -156,8 +156,9 @@ static NoallocDevice g_noalloc_dev[64];
 static size_t noalloc_smem(int K[3], int p) {
     size_t s = smem_bin(NOALLOC_THREADS);
     s = s > smem_spread(p) ? s : smem_spread(p);
-    s = s > smem_gather(p) ? s : smem_gather(p);
+    s = s > smem_gather_all(p) ? s : smem_gather_all(p);
     s = s > smem_slab(K[1], K[2]) ? s : smem_slab(K[1], K[2]);
+    s = s > smem_inv(K[1], K[2]) ? s : smem_inv(K[1], K[2]);
     s = s > smem_conv(K[0], NOALLOC_THREADS) ? s : smem_conv(K[0], NOALLOC_THREADS);
     return s;
 }

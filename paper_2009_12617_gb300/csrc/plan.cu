@@ -401,6 +401,12 @@ pme_status pme_profile_stages(pme_plan *pl, const float *pos, const float *q, in
     return collect_status(pl, false);
 }
 
+pme_status pme_set_launch_mode(int mode) {
+    if (mode < 0 || mode > 2) return fail(PME_EINVAL, "launch mode must be 0, 1 or 2");
+    set_launch_mode(mode);
+    return PME_OK;
+}
+
 size_t pme_plan_device_bytes(const pme_plan *pl) {
     return pl ? pl->mesh_bytes + pl->atom_bytes + (pl->host_mem ? align256((size_t)pl->host_cap * 12) * 2 +
                                                                           align256((size_t)pl->host_cap * 4)

@@ -38,10 +38,14 @@ inline size_t smem_slab(int K2, int K3) {
 }
 inline size_t smem_conv(int K1, int nth) {
     size_t fft = (2 * (size_t)K1 * CONV_COLS + K1) * sizeof(float2);
-    size_t red = (size_t)((nth + 31) / 32) * 7 * sizeof(DF);
+    size_t red = (size_t)7 * nth * sizeof(float) + 7 * 16 * sizeof(DF);
+    return fft > red ? fft : red;
+}
+inline size_t smem_inv(int K2, int K3) { return smem_slab(K2, K3); }
+// the force stage's first overflow item also runs the final energy / virial reduction
+inline size_t smem_gather_all(int p) {
     size_t fin = (size_t)REDUCE_SLOTS * 7 * sizeof(DF);
-    size_t m = fft > red ? fft : red;
-    return m > fin ? m : fin;
+    return smem_gather(p) > fin ? smem_gather(p) : fin;
 }
 
 // global -> shared copy of n elements with LOAD_BATCH independent loads in flight per thread
@@ -65,9 +69,8 @@ PME_DEV void copy_batched(T *dst, const T *src, int n) {
 // the mesh does not depend on which path an atom takes.
 
 PME_DEV void fix_split(float v, int &h, unsigned &l) {
-    const float fh = floorf(v * 9.5367431640625e-07f);  // v / 2^20
-    h = (int)fh;
-    l = (unsigned)(int)rintf(fmaf(-fh, 1048576.0f, v));
+    h = f2i_rd(v * 9.5367431640625e-07f);  // floor(v / 2^20)
+    l = (unsigned)f2i_rn(fmaf(-(float)h, 1048576.0f, v));
 }
 PME_DEV unsigned long long fix_join(long long h, long long l) { return (unsigned long long)(h * 1048576ll + l); }
 
@@ -147,18 +150,13 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
         }
     }
     if (bad) atomic_or_u32(&d.ctl->status, bad);
-    // CTA sum of |q| in fixed point (exact and order-independent)
+    // warp sums of |q| in fixed point (exact, so the order of the atomics does not matter)
     qacc = warp_sum_u64(qacc);
-    if ((tid & 31) == 0) red[tid >> 5] = qacc;
-    PME_SYNC();
-    if (tid == 0) {
-        unsigned long long s = 0;
-        for (int w = 0; w < (nth + 31) / 32; ++w) s += red[w];
-        if (s) {
-            if (s >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
-            else atomic_add_u64(&d.ctl->qabs, s);
-        }
+    if ((tid & 31) == 0 && qacc) {
+        if (qacc >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+        else atomic_add_u64(&d.ctl->qabs, qacc);
     }
+    (void)red;
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -208,6 +206,8 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {  // bucket-overflow atoms, straight to the global mesh
         const unsigned novf = imin((int)ldcg(&d.ctl->novf), d.n);
+        // the force stage reads this copy; the forward FFT stage resets the counter for the next binning
+        if (item == d.ntiles && tid == 0) d.ctl->novf_gather = novf;
         for (unsigned a = (unsigned)((item - d.ntiles) * nth + tid); a < novf; a += (unsigned)(OVF_ITEMS * nth))
             spread_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
         return;
@@ -225,7 +225,9 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
     PME_SYNC();
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
-    for (int a = tid; a < cnt; a += nth) {
+    // two threads per atom: half h takes the planes j1 in [h P/2, (h + 1) P/2)
+    for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
+        const int a = a2 >> 1, half = a2 & 1;
         const float4 ra = ldcg(A + a);
         const int2 rb = ldcg(B + a);
         float th1[P], th2[P], th3[P];
@@ -237,10 +239,12 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
         const int l2 = ((rb.x >> 10) & 1023) - o2 + H;
         const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
 #pragma unroll
-        for (int j1 = 0; j1 < P; ++j1) {
+        for (int jj = 0; jj < P / 2; ++jj) {
+            const int j1 = half * (P / 2) + jj;
+            const float t1 = half ? th1[P / 2 + jj] : th1[jj];
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
-                const float c = ra.w * th1[j1] * th2[j2];
+                const float c = ra.w * t1 * th2[j2];
                 const int row = ((l1 - j1) * R + (l2 - j2)) * R + l3;
 #pragma unroll
                 for (int j3 = 0; j3 < P; ++j3) {
@@ -297,6 +301,7 @@ PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
     for (int i = tid; i < Nh; i += nth) twh[i] = d.tw3h[i];
     for (int i = tid; i <= Nh; i += nth) tw3[i] = d.tw3[i];
     for (int i = tid; i < K2; i += nth) tw2[i] = d.tw2[i];
+    if (k1 == 0 && tid == 0) d.ctl->novf = 0u;  // spreading (its last reader) has finished
     PME_SYNC();
     float2 *Z = fft_batch<false>(A, B, Nh, K2, 1, Nh, twh);  // rows, stride Nh
     float2 *X = (Z == A) ? B : A;
@@ -386,9 +391,9 @@ PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
     for (int i = tid; i < K1; i += nth) tw1[i] = d.tw1[i];
     PME_SYNC();
     float2 *X = fft_batch<false>(A, B, K1, C, C, 1, tw1);
-    DF acc[7];
+    float acc[7];
 #pragma unroll
-    for (int c = 0; c < 7; ++c) acc[c].hi = acc[c].lo = 0.f;
+    for (int c = 0; c < 7; ++c) acc[c] = 0.f;
     const float2 *bc = d.bc + (size_t)m2 * K1 * H3 + c0;
     const int mt2 = signed_freq(m2, K2);
     for (int i = tid; i < K1 * C; i += nth) {
@@ -410,9 +415,9 @@ PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) W[c] = 0.5f * (W[c] + Wp[c]);
             }
-            acc[0] = df_add(acc[0], e);
+            acc[0] += e;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[1 + c] = df_add(acc[1 + c], e * W[c]);
+            for (int c = 0; c < 6; ++c) acc[1 + c] = fmaf(e, W[c], acc[1 + c]);
             x.x *= t.x;
             x.y *= t.x;
         } else {
@@ -427,67 +432,97 @@ PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
         d.spec[((size_t)k1 * K2 + m2) * H3 + c0 + mc] = Y[i];
     }
     PME_SYNC();
-    // CTA reduction of the 7 double-float sums: warp shuffles, then one slot per warp
-    DF *red = (DF *)smem;
+    // Item partial of the 7 sums: each thread holds a few FP32 terms; they meet in a double-float tree
+    // (16 lanes per component, then one lane), written to this item's slot. The inverse-FFT stage, which
+    // starts only after every item of this stage, reduces the slots.
+    float *red = (float *)smem;  // 7 x nth
+    DF *red2 = (DF *)(red + 7 * nth);  // 7 x 16
 #pragma unroll
-    for (int c = 0; c < 7; ++c) acc[c] = warp_sum_df(acc[c]);
-    if ((tid & 31) == 0) {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) red[(tid >> 5) * 7 + c] = acc[c];
+    for (int c = 0; c < 7; ++c) red[c * nth + tid] = acc[c];
+    PME_SYNC();
+    for (int r = tid; r < 7 * 16; r += nth) {
+        const int c = r >> 4, lane = r & 15;
+        DF s;
+        s.hi = s.lo = 0.f;
+        for (int t = lane; t < nth; t += 16) s = df_add(s, red[c * nth + t]);
+        red2[r] = s;
     }
     PME_SYNC();
-    PME_SHARED unsigned last_flag;
     DF *part = (DF *)d.partials;  // 8 double-float slots per item
-    if (tid == 0) {
-        const int nw = (nth + 31) / 32;
-        for (int c = 0; c < 7; ++c) {
-            DF s = red[c];
-            for (int w = 1; w < nw; ++w) s = df_add(s, red[w * 7 + c]);
-            part[(size_t)item * 8 + c] = s;
-        }
-        PME_FENCE();
-        const unsigned done = atomic_add_u32(&d.ctl->conv_done, 1u);
-        last_flag = (done == (unsigned)d.nconv - 1u) ? 1u : 0u;
+    for (int c = tid; c < 7; c += nth) {
+        DF s = red2[c * 16];
+        for (int lane = 1; lane < 16; ++lane) s = df_add(s, red2[c * 16 + lane]);
+        part[(size_t)item * 8 + c] = s;
     }
-    PME_SYNC();
-    if (last_flag) {
-        // Last item: sum all item partials. Slot v (of REDUCE_SLOTS) takes items v, v + REDUCE_SLOTS, ...
-        // in order; the slots then meet in a fixed binary tree. The order does not depend on the block
-        // size, so every launch configuration gives the same bits.
-        PME_FENCE();
-        DF *slot = (DF *)smem;  // REDUCE_SLOTS x 7
-        for (int v = tid; v < REDUCE_SLOTS; v += nth) {
-            DF s[7];
+}
+
+// Energy and virial of the whole system, in two fixed-order levels off the critical path. Level 1 (inverse
+// slab item k1): the influence-stage item partials k1, k1 + K1, k1 + 2 K1, ... in order -> slot k1. Level 2
+// (the first overflow item of the force stage, otherwise idle when no bucket overflowed): the K1 slots in a
+// fixed binary tree -> FP64 energy and virial. Neither order depends on the block size.
+PME_DEV void reduce_level1(const SysDev &d, int k1) {
+    const int tid = PME_TID, nth = PME_NTH;
+    const DF *part = (const DF *)d.partials;
+    DF *slot = (DF *)d.partials + (size_t)d.nconv * 8;  // K1 level-1 slots of 8 after the item partials
+    for (int c = tid; c < 7; c += nth) {
+        DF s;
+        s.hi = s.lo = 0.f;
+        for (int it0 = k1; it0 < d.nconv; it0 += LOAD_BATCH * d.K1) {
+            float2 p2[LOAD_BATCH];
 #pragma unroll
-            for (int c = 0; c < 7; ++c) s[c].hi = s[c].lo = 0.f;
-            for (int it = v; it < d.nconv; it += REDUCE_SLOTS) {
-#pragma unroll
-                for (int c = 0; c < 7; ++c) {
-                    const float2 p2 = ldcg((const float2 *)(part + (size_t)it * 8 + c));
-                    DF pv;
-                    pv.hi = p2.x;
-                    pv.lo = p2.y;
-                    s[c] = df_add(s[c], pv);
-                }
+            for (int u = 0; u < LOAD_BATCH; ++u) {
+                const int it = it0 + u * d.K1;
+                if (it < d.nconv) p2[u] = ldcg((const float2 *)(part + (size_t)it * 8 + c));
             }
 #pragma unroll
-            for (int c = 0; c < 7; ++c) slot[v * 7 + c] = s[c];
+            for (int u = 0; u < LOAD_BATCH; ++u)
+                if (it0 + u * d.K1 < d.nconv) {
+                    DF pv;
+                    pv.hi = p2[u].x;
+                    pv.lo = p2[u].y;
+                    s = df_add(s, pv);
+                }
+        }
+        slot[(size_t)k1 * 8 + c] = s;
+    }
+}
+
+PME_DEV void reduce_level2(const SysDev &d, void *smem) {
+    const int tid = PME_TID, nth = PME_NTH;
+    const DF *slot = (const DF *)d.partials + (size_t)d.nconv * 8;
+    DF *t = (DF *)smem;  // REDUCE_SLOTS x 7: slot v holds level-1 slots v, v + REDUCE_SLOTS (K1 <= 2 * REDUCE_SLOTS)
+    for (int r = tid; r < REDUCE_SLOTS * 7; r += nth) {
+        const int v = r / 7, c = r - v * 7;
+        DF s;
+        s.hi = s.lo = 0.f;
+        if (v < d.K1) {
+            const float2 a = ldcg((const float2 *)(slot + (size_t)v * 8 + c));
+            s.hi = a.x;
+            s.lo = a.y;
+        }
+        if (v + REDUCE_SLOTS < d.K1) {
+            const float2 b = ldcg((const float2 *)(slot + (size_t)(v + REDUCE_SLOTS) * 8 + c));
+            DF bv;
+            bv.hi = b.x;
+            bv.lo = b.y;
+            s = df_add(s, bv);
+        }
+        t[r] = s;
+    }
+    PME_SYNC();
+    for (int h = REDUCE_SLOTS / 2; h > 0; h >>= 1) {
+        for (int r = tid; r < h * 7; r += nth) {
+            const int v = r / 7, c = r - v * 7;
+            t[v * 7 + c] = df_add(t[v * 7 + c], t[(v + h) * 7 + c]);
         }
         PME_SYNC();
-        for (int h = REDUCE_SLOTS / 2; h > 0; h >>= 1) {
-            for (int r = tid; r < h * 7; r += nth) {
-                const int v = r / 7, c = r - v * 7;
-                slot[v * 7 + c] = df_add(slot[v * 7 + c], slot[(v + h) * 7 + c]);
-            }
-            PME_SYNC();
-        }
-        if (tid == 0) {
-            for (int c = 0; c < 7; ++c) d.ev[c] = (double)slot[c].hi + (double)slot[c].lo;
-            if (ldcg(&d.ctl->qabs) >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
-            d.ctl->qabs = 0ull;
-            d.ctl->conv_done = 0u;
-        }
     }
+    if (tid == 0) {
+        for (int c = 0; c < 7; ++c) d.ev[c] = (double)t[c].hi + (double)t[c].lo;
+        if (ldcg(&d.ctl->qabs) >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+        d.ctl->qabs = 0ull;
+    }
+    PME_SYNC();
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -496,6 +531,7 @@ PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
 
 PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
+    reduce_level1(d, k1);  // every influence item has finished
     const int K2 = d.K2, K3 = d.K3, H3 = d.H3, Nh = K3 / 2;
     const float inv_nh = 1.0f / (float)Nh;
     float2 *A = (float2 *)smem;
@@ -573,7 +609,8 @@ template <int P>
 PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {
-        const unsigned novf = imin((int)ldcg(&d.ctl->novf), d.n);
+        if (item == d.ntiles) reduce_level2(d, smem);  // every inverse-slab item has finished
+        const unsigned novf = imin((int)ldcg(&d.ctl->novf_gather), d.n);
         for (unsigned a = (unsigned)((item - d.ntiles) * nth + tid); a < novf; a += (unsigned)(OVF_ITEMS * nth))
             gather_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
     } else {
@@ -601,7 +638,13 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         if (tid == 0) d.bcount[(size_t)item * BCOUNT_STRIDE] = 0u;  // consumed: ready for the next binning
         const float4 *A = d.bka + (size_t)item * d.cap;
         const int2 *B = d.bkb + (size_t)item * d.cap;
-        for (int a = tid; a < cnt; a += nth) {
+#if defined(PME_HOST_EMULATION)
+        float e1 = 0.f, e2 = 0.f, e3 = 0.f;  // the even half's partial sums, combined on the odd half
+#endif
+        // two threads per atom (adjacent lanes): half h sums the planes j1 in [h P/2, (h + 1) P/2); the
+        // halves are added in a fixed order, so both lanes hold the same total
+        for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
+            const int a = a2 >> 1, half = a2 & 1;
             const float4 ra = ldcg(A + a);
             const int2 rb = ldcg(B + a);
             float th1[P], th2[P], th3[P], dth1[P], dth2[P], dth3[P];
@@ -613,7 +656,10 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
             const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
             float g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-            for (int j1 = 0; j1 < P; ++j1) {
+            for (int jj = 0; jj < P / 2; ++jj) {
+                const int j1 = half * (P / 2) + jj;
+                const float t1 = half ? th1[P / 2 + jj] : th1[jj];
+                const float dt1 = half ? dth1[P / 2 + jj] : dth1[jj];
 #pragma unroll
                 for (int j2 = 0; j2 < P; ++j2) {
                     const float *row = reg + ((l1 - j1) * R + (l2 - j2)) * R + l3;
@@ -624,21 +670,28 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
                         s = fmaf(th3[j3], ph, s);
                         ds = fmaf(dth3[j3], ph, ds);
                     }
-                    g1 = fmaf(dth1[j1] * th2[j2], s, g1);
-                    g2 = fmaf(th1[j1] * dth2[j2], s, g2);
-                    g3 = fmaf(th1[j1] * th2[j2], ds, g3);
+                    g1 = fmaf(dt1 * th2[j2], s, g1);
+                    g2 = fmaf(t1 * dth2[j2], s, g2);
+                    g3 = fmaf(t1 * th2[j2], ds, g3);
                 }
             }
+#if defined(PME_HOST_EMULATION)
+            if (!half) {
+                e1 = g1;
+                e2 = g2;
+                e3 = g3;
+                continue;
+            }
+            g1 = e1 + g1;
+            g2 = e2 + g2;
+            g3 = e3 + g3;
             force_from_grad<P>(d, ra.w, rb.y, g1, g2, g3);
-        }
-    }
-    PME_SYNC();
-    if (tid == 0) {
-        PME_FENCE();
-        const unsigned done = atomic_add_u32(&d.ctl->gather_done, 1u);
-        if (done == (unsigned)(d.ntiles + OVF_ITEMS) - 1u) {  // every gather item has read novf
-            d.ctl->novf = 0u;
-            d.ctl->gather_done = 0u;
+#else
+            const unsigned mask = __activemask();  // both lanes of every pair are active together
+            const float o1f = __shfl_xor_sync(mask, g1, 1), o2f = __shfl_xor_sync(mask, g2, 1),
+                        o3f = __shfl_xor_sync(mask, g3, 1);
+            if (!half) force_from_grad<P>(d, ra.w, rb.y, g1 + o1f, g2 + o2f, g3 + o3f);
+#endif
         }
     }
 }

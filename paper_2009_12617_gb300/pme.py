@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "PME_OK", 1: "PME_EINVAL", 2: "PME_EUNSUPPORTED", 3: "PME_ENO
 
 # every symbol include/pme.h declares
 EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme_enqueue", "pme_reserve", "pme_sync", "pme_compute_host",
-           "pme_profile_stages", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
+           "pme_profile_stages", "pme_set_launch_mode", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
            "pme_batch_destroy", "pme_server_create", "pme_submit", "pme_poll", "pme_server_stats",
            "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall",
            "pme_compute_noalloc")
@@ -67,6 +67,7 @@ def load_library(path: str | None = None):
         "pme_sync": (_st, [_vp]),
         "pme_compute_host": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "pme_profile_stages": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "pme_set_launch_mode": (_st, [ctypes.c_int]),
         "pme_plan_device_bytes": (ctypes.c_size_t, [_vp]),
         "pme_destroy": (None, [_vp]),
         "pme_batch_create": (_st, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp, ctypes.POINTER(_vp)]),
@@ -210,6 +211,11 @@ def pme_profile_stages(plan: int, pos, q, forces, reps: int = 10) -> dict:
     check(load_library().pme_profile_stages(_vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")),
                                             int(q.shape[0]), _vp(_f32(forces, (3,), "forces")), int(reps), out))
     return dict(zip(STAGE_NAMES, out[:]))
+
+
+def pme_set_launch_mode(mode: int) -> None:
+    """0 plain, 1 programmatic dependent launch triggered at kernel entry, 2 triggered at CTA exit."""
+    check(load_library().pme_set_launch_mode(int(mode)))
 
 
 def pme_plan_device_bytes(plan: int) -> int:

@@ -65,7 +65,7 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     s.bkb.resize((size_t)d.ntiles * cap);
     s.ova.resize(n > 0 ? n : 1);
     s.ovb.resize(n > 0 ? n : 1);
-    size_t sm = std::max({smem_bin(1), smem_spread(p), smem_gather(p), smem_slab(K[1], K[2]), smem_conv(K[0], 1)});
+    size_t sm = std::max({smem_bin(1), smem_spread(p), smem_gather_all(p), smem_slab(K[1], K[2]), smem_inv(K[1], K[2]), smem_conv(K[0], 1)});
     s.smem.assign(sm, 0);
     d.grid = s.grid.data();
     d.spec = s.spec.data();
@@ -117,7 +117,7 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     for (int c = 0; c < 7; ++c) ev[c] = s.ctl.ev[c];
     if (phi_out) memcpy(phi_out, s.phi.data(), s.phi.size() * 4);
     // every self-resetting counter must be back at zero after an evaluation
-    bool clean = s.ctl.novf == 0 && s.ctl.qabs == 0 && s.ctl.conv_done == 0 && s.ctl.gather_done == 0;
+    bool clean = s.ctl.novf == 0 && s.ctl.qabs == 0;
     for (unsigned c : s.bcount) clean = clean && c == 0;
     for (unsigned long long g : s.grid) clean = clean && g == 0;
     if (!clean) status |= 0x100u;
