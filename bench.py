@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, batch, serving and CPU baseline legs")
+    ap.add_argument("--legs", default="", help="comma list of extra legs to run alone (batched, serving, large); "
+                                               "skips the headline (for profiling one leg)")
     return ap.parse_args()
 
 
@@ -423,6 +425,24 @@ def main():
         if args.impl == "reference":
             run_reference(args, dist)
             return
+        if args.legs:
+            import torch
+
+            from paper_2009_12617_gb300 import build as libbuild
+            from paper_2009_12617_gb300 import pme
+
+            libbuild.build_library()
+            pme.load_library()
+            torch.cuda.set_device(dist.local)
+            sampler = ClockSampler(dist.local)
+            out = {}
+            table = {"batched": leg_batched, "serving": leg_serving, "large": leg_large}
+            for name in args.legs.split(","):
+                out.update(table[name](args, sampler))
+            out["clocks"] = sampler.summary()
+            if dist.rank == 0:
+                print(json.dumps(out), flush=True)
+            return
         result, sampler, plan, ctx = run_ours(args, dist)
         from paper_2009_12617_gb300 import pme
 
@@ -513,6 +533,9 @@ def leg_batched(args, sampler):
                 pme.pme_sync(pl)
         same = bool(torch.equal(F, Fb) and torch.equal(ev, evb))
         nsys, atoms = len(systems), int(sum(ns))
+        alg = sum(sum(stage_bytes(s.n, s.K, s.p).values()) for s in systems)
+        peak, src = measured_peaks()
+        achieved = alg / (t_batch * 1e-3) / 1e9
         out = {"batched": {
             "workload": "64 water-like boxes, N log-uniform in [1024, 32768] (seed 4), 0.1 atoms/A^3, K in {32,40,48,64} "
                         "by 1.4 A spacing, p=4, one persistent launch per step (CUDA graph)",
@@ -522,7 +545,11 @@ def leg_batched(args, sampler):
             "one_system_per_launch": {"eager_evals_per_s": round(nsys / (t_eager * 1e-3), 1),
                                       "graph_evals_per_s": round(nsys / (t_graph * 1e-3), 1)},
             "speedup_vs_graph_of_single_launches": round(t_graph / t_batch, 3),
-            "bit_identical_to_single": same, "gpu_launches_per_step": 2}}
+            "bit_identical_to_single": same, "gpu_launches_per_step": 2,
+            "roofline": {"kernel": "k_batch (all six stages of 64 systems, one launch)", "bound": "hbm",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "algorithmic_bytes": int(alg),
+                         "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)"}}}
     finally:
         pme.pme_batch_destroy(b)
         for pl in plans:

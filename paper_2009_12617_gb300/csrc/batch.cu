@@ -54,12 +54,18 @@ __device__ bool bounded_wait(const unsigned *counter, unsigned target, BatchCtrl
 // the others and the persistent kernel keeps the occupancy of its most demanding stage.
 __device__ __noinline__ void call_bin(const SysDev &d, int item, void *smem) { stage_bin(d, item, smem); }
 template <int P>
-__device__ __noinline__ void call_spread(const SysDev &d, int item, void *smem) { stage_spread<P>(d, item, smem); }
+__device__ __noinline__ void call_spread(const SysDev &d, int item, void *smem) {
+    if (d.tlog == 4) stage_spread<P, 16>(d, item, smem);
+    else stage_spread<P, 8>(d, item, smem);
+}
 __device__ __noinline__ void call_fwd(const SysDev &d, int item, void *smem) { stage_fwd(d, item, smem); }
 __device__ __noinline__ void call_conv(const SysDev &d, int item, void *smem) { stage_conv(d, item, smem); }
 __device__ __noinline__ void call_inv(const SysDev &d, int item, void *smem) { stage_inv(d, item, smem); }
 template <int P>
-__device__ __noinline__ void call_gather(const SysDev &d, int item, void *smem) { stage_gather<P>(d, item, smem); }
+__device__ __noinline__ void call_gather(const SysDev &d, int item, void *smem) {
+    if (d.tlog == 4) stage_gather<P, 16>(d, item, smem);
+    else stage_gather<P, 8>(d, item, smem);
+}
 
 template <int P>
 __device__ __forceinline__ void run_stage(const SysDev &d, int stage, int item, void *smem) {
@@ -163,8 +169,8 @@ void build_work_list(const std::vector<SysDev> &sys, std::vector<BatchEntry> &en
 size_t batch_smem(const std::vector<SysDev> &sys) {
     size_t m = smem_bin(NT_BATCH);
     for (const SysDev &d : sys) {
-        m = std::max(m, smem_spread(d.p));
-        m = std::max(m, smem_gather_all(d.p));
+        m = std::max(m, smem_spread(d.p, d.tlog));
+        m = std::max(m, smem_gather_all(d.p, d.tlog));
         m = std::max(m, smem_slab(d.K2, d.K3));
         m = std::max(m, smem_inv(d.K2, d.K3));
         m = std::max(m, smem_conv(d.K1, NT_BATCH));

@@ -31,9 +31,10 @@
 
 namespace pme {
 
-// Mesh edge of one spread / gather tile. Atoms are binned by the tile that holds their highest support
-// point; the tile's shared-memory region is (TILE + p - 1)^3 mesh points.
-constexpr int TILE = 8;
+// Mesh edge of a spread / gather tile: 2^tlog with tlog 3 or 4, chosen per plan from the atom density
+// (about a hundred atoms or more per tile). Atoms are binned by the tile that holds their highest support
+// point; the tile's shared-memory region is (T + p - 1)^3 mesh points. Results do not depend on the choice.
+constexpr int TILE_MIN_LOG = 3, TILE_MAX_LOG = 4;
 // Fixed-point scale of the charge mesh: Q is accumulated as round(q theta1 theta2 theta3 * 2^40) in int64,
 // so the mesh is bit-identical whatever order the atoms are added in.
 constexpr float FIX_SCALE = 1099511627776.0f;            // 2^40
@@ -83,6 +84,7 @@ struct Ctl {
 struct SysDev {
     int K1, K2, K3, H3;          // mesh; H3 = K3/2 + 1 (half spectrum along k3)
     int p;                       // B-spline order
+    int tlog;                    // tile edge 2^tlog mesh points
     int nt1, nt2, nt3, ntiles;   // spread / gather tiles per dimension
     int cap;                     // bucket capacity (atoms per tile)
     int n;                       // atoms

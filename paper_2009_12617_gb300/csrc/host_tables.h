@@ -69,6 +69,26 @@ inline bool cell_reciprocal(const double box[9], double recip[9], double *vol) {
     return true;
 }
 
+// Tile edge 2^tlog: tiles per dimension (the last one ragged) and their count. Needs d.K1..K3.
+inline void set_tiling(SysDev &d, int tlog) {
+    const int T = 1 << tlog;
+    d.tlog = tlog;
+    d.nt1 = (d.K1 + T - 1) / T;
+    d.nt2 = (d.K2 + T - 1) / T;
+    d.nt3 = (d.K3 + T - 1) / T;
+    d.ntiles = d.nt1 * d.nt2 * d.nt3;
+}
+
+// Tile edge for n atoms. 8^3 tiles measured faster than 16^3 on GB300 even where they hold few atoms
+// (128^3 at p = 6: 187 vs 331 us per evaluation): many light CTAs hide latency better than few heavy ones,
+// and fuller tiles overflow the bucket cap on small meshes. So the edge is 8; 16 stays available (results
+// do not depend on it).
+inline int choose_tile_log(int64_t n, const int K[3]) {
+    (void)n;
+    (void)K;
+    return TILE_MIN_LOG;
+}
+
 // Mesh geometry, coordinate transform and tiling of a system.
 inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const double recip[9]) {
     d.K1 = K[0];
@@ -76,10 +96,7 @@ inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const d
     d.K3 = K[2];
     d.H3 = K[2] / 2 + 1;
     d.p = p;
-    d.nt1 = (K[0] + TILE - 1) / TILE;
-    d.nt2 = (K[1] + TILE - 1) / TILE;
-    d.nt3 = (K[2] + TILE - 1) / TILE;
-    d.ntiles = d.nt1 * d.nt2 * d.nt3;
+    set_tiling(d, TILE_MIN_LOG);
     d.nchunk3 = (d.H3 + CONV_COLS - 1) / CONV_COLS;
     d.nconv = d.K2 * d.nchunk3;
     for (int a = 0; a < 3; ++a) d.kinv[a] = 1.0f / (float)K[a];
@@ -173,6 +190,10 @@ inline int bucket_capacity(int64_t n, int ntiles) {
 
 // Bytes of the padded tile-counter array and of the influence-stage partials.
 inline size_t bcount_bytes(int ntiles) { return (size_t)ntiles * BCOUNT_STRIDE * sizeof(unsigned); }
+// counters for the finest tiling (the most tiles any choice can need)
+inline size_t bcount_bytes_max(const int K[3]) {
+    return bcount_bytes(((K[0] + 7) / 8) * ((K[1] + 7) / 8) * ((K[2] + 7) / 8));
+}
 inline size_t partials_bytes(const SysDev &d) { return ((size_t)d.nconv + d.K1) * 8 * sizeof(float2); }
 
 }  // namespace pme

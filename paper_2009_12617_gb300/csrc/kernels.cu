@@ -35,11 +35,11 @@ __global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
     stage_bin(d, blockIdx.x, smem);
 }
 
-template <int P>
+template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late != 0);
-    stage_spread<P>(d, blockIdx.x, smem);
+    stage_spread<P, T>(d, blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_SLAB) k_fwd(SysDev d) {
@@ -60,11 +60,11 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
     stage_inv(d, blockIdx.x, smem);
 }
 
-template <int P>
+template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late != 0);
-    stage_gather<P>(d, blockIdx.x, smem);
+    stage_gather<P, T>(d, blockIdx.x, smem);
 }
 
 static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
@@ -90,20 +90,27 @@ static cudaError_t set_smem_limit(const void *fn, size_t bytes) {
 
 cudaError_t configure_kernels() {
     const size_t big = MAX_SMEM_BYTES;
-    cudaError_t e;
-    if ((e = set_smem_limit((const void *)k_fwd, big)) != cudaSuccess) return e;
-    if ((e = set_smem_limit((const void *)k_conv, big)) != cudaSuccess) return e;
-    if ((e = set_smem_limit((const void *)k_inv, big)) != cudaSuccess) return e;
+    const void *fns[] = {(const void *)k_fwd, (const void *)k_conv, (const void *)k_inv,
+                         (const void *)k_spread<4, 8>, (const void *)k_spread<6, 8>, (const void *)k_spread<8, 8>,
+                         (const void *)k_spread<4, 16>, (const void *)k_spread<6, 16>, (const void *)k_spread<8, 16>,
+                         (const void *)k_gather<4, 8>, (const void *)k_gather<6, 8>, (const void *)k_gather<8, 8>,
+                         (const void *)k_gather<4, 16>, (const void *)k_gather<6, 16>, (const void *)k_gather<8, 16>};
+    for (const void *f : fns) {
+        cudaError_t e = set_smem_limit(f, big);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
 template <int P>
 static void launch_tiles_spread(const SysDev &d, cudaStream_t s) {
-    launch_pdl(k_spread<P>, d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P), s, d);
+    if (d.tlog == 4) launch_pdl(k_spread<P, 16>, d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P, 4), s, d);
+    else launch_pdl(k_spread<P, 8>, d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P, 3), s, d);
 }
 template <int P>
 static void launch_tiles_gather(const SysDev &d, cudaStream_t s) {
-    launch_pdl(k_gather<P>, d.ntiles + OVF_ITEMS, NT_TILE, smem_gather_all(P), s, d);
+    if (d.tlog == 4) launch_pdl(k_gather<P, 16>, d.ntiles + OVF_ITEMS, NT_TILE, smem_gather_all(P, 4), s, d);
+    else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, NT_TILE, smem_gather_all(P, 3), s, d);
 }
 
 void launch_stage(const SysDev &d, int stage, cudaStream_t s) {

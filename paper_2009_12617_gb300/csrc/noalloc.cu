@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_eval_noalloc(NoallocArgs A)
     const int nbin = d.nbin;
     for (int it = blockIdx.x; it < nbin; it += gridDim.x) stage_bin(d, it, smem);
     grid.sync();
-    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) stage_spread<P>(d, it, smem);
+    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) stage_spread<P, 8>(d, it, smem);
     grid.sync();
     for (int it = blockIdx.x; it < d.K1; it += gridDim.x) stage_fwd(d, it, smem);
     grid.sync();
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_eval_noalloc(NoallocArgs A)
     grid.sync();
     for (int it = blockIdx.x; it < d.K1; it += gridDim.x) stage_inv(d, it, smem);
     grid.sync();
-    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) stage_gather<P>(d, it, smem);
+    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) stage_gather<P, 8>(d, it, smem);
 }
 
 struct NoallocDevice {
@@ -155,8 +155,8 @@ static NoallocDevice g_noalloc_dev[64];
 
 static size_t noalloc_smem(int K[3], int p) {
     size_t s = smem_bin(NOALLOC_THREADS);
-    s = s > smem_spread(p) ? s : smem_spread(p);
-    s = s > smem_gather_all(p) ? s : smem_gather_all(p);
+    s = s > smem_spread(p, 3) ? s : smem_spread(p, 3);  // this path always uses 8^3 tiles
+    s = s > smem_gather_all(p, 3) ? s : smem_gather_all(p, 3);
     s = s > smem_slab(K[1], K[2]) ? s : smem_slab(K[1], K[2]);
     s = s > smem_inv(K[1], K[2]) ? s : smem_inv(K[1], K[2]);
     s = s > smem_conv(K[0], NOALLOC_THREADS) ? s : smem_conv(K[0], NOALLOC_THREADS);
@@ -185,6 +185,8 @@ static pme_status noalloc_setup(int dev, NoallocDevice **out) {
         for (int i = 0; i < 3; ++i) {
             int K[3] = {64, 64, 64};  // the largest shared-memory footprint the size limits allow
             const size_t smem = noalloc_smem(K, ps[i]);
+            if ((e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return cuda_fail(e, "cudaFuncSetAttribute(k_eval_noalloc)");
             int per_sm = 0;
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], NOALLOC_THREADS, smem)) != cudaSuccess)
                 return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");

@@ -94,7 +94,7 @@ static pme_status alloc_mesh(pme_plan *pl) {
     const size_t o_phi = off;  off = align256(off + K1 * K2 * K3 * 4);
     const size_t o_bc = off;   off = align256(off + K1 * K2 * H3 * 8);
     const size_t o_tw = off;   off = align256(off + (K1 + K2 + Nh + Nh + 1) * 8);
-    const size_t o_cnt = off;  off = align256(off + bcount_bytes(d.ntiles));
+    const size_t o_cnt = off;  off = align256(off + bcount_bytes_max(pl->K));
     const size_t o_par = off;  off = align256(off + partials_bytes(d));
     const size_t o_ctl = off;  off = align256(off + sizeof(Ctl));
     cudaError_t e = cudaMalloc(&pl->mesh_mem, off);
@@ -126,6 +126,9 @@ pme_status plan_reserve(pme_plan *pl, int64_t n) {
     if (n <= pl->n_cap && pl->atom_mem) return PME_OK;
     SysDev &d = pl->d;
     const int64_t ncap = n > 0 ? n : 1;
+    // tile edge from the atom density (every tile counter is zero between evaluations, so the tiling may
+    // change here; results do not depend on it)
+    set_tiling(d, choose_tile_log(ncap, pl->K));
     const int cap = bucket_capacity(ncap, d.ntiles);
     const size_t nb = (size_t)d.ntiles * cap;
     size_t off = 0;

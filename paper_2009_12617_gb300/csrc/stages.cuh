@@ -18,10 +18,10 @@
 
 namespace pme {
 
-// Tile region edge (mesh points) for spline order P: the tile plus the p - 1 points below it.
-template <int P>
+// Tile region edge (mesh points) for spline order P and tile edge T: the tile plus the p - 1 points below.
+template <int P, int T>
 struct Region {
-    static constexpr int R = TILE + P - 1;
+    static constexpr int R = T + P - 1;
     static constexpr int VOL = R * R * R;
 };
 
@@ -29,9 +29,12 @@ struct Region {
 // shared-memory sizes (bytes) of each stage for a given system and block size
 
 inline size_t smem_bin(int nth) { return (size_t)((nth + 31) / 32) * sizeof(unsigned long long) + 16; }
-inline size_t smem_tile_region(int p) { return (size_t)(TILE + p - 1) * (TILE + p - 1) * (TILE + p - 1); }
-inline size_t smem_spread(int p) { return smem_tile_region(p) * 2 * sizeof(int); }
-inline size_t smem_gather(int p) { return smem_tile_region(p) * sizeof(float); }
+inline size_t smem_tile_region(int p, int tlog) {
+    const size_t r = (size_t)(1 << tlog) + p - 1;
+    return r * r * r;
+}
+inline size_t smem_spread(int p, int tlog) { return smem_tile_region(p, tlog) * 2 * sizeof(int); }
+inline size_t smem_gather(int p, int tlog) { return smem_tile_region(p, tlog) * sizeof(float); }
 inline size_t smem_slab(int K2, int K3) {
     const int H3 = K3 / 2 + 1;
     return (2 * (size_t)K2 * H3 + (K3 / 2) + (K3 / 2 + 1) + K2) * sizeof(float2);
@@ -43,9 +46,9 @@ inline size_t smem_conv(int K1, int nth) {
 }
 inline size_t smem_inv(int K2, int K3) { return smem_slab(K2, K3); }
 // the force stage's first overflow item also runs the final energy / virial reduction
-inline size_t smem_gather_all(int p) {
+inline size_t smem_gather_all(int p, int tlog) {
     size_t fin = (size_t)REDUCE_SLOTS * 7 * sizeof(DF);
-    return smem_gather(p) > fin ? smem_gather(p) : fin;
+    return smem_gather(p, tlog) > fin ? smem_gather(p, tlog) : fin;
 }
 
 // global -> shared copy of n elements with LOAD_BATCH independent loads in flight per thread
@@ -117,7 +120,7 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
                 continue;
             }
             qacc += (unsigned long long)f2ll_rn(fabsf(q) * QABS_SCALE);
-            tile[k] = ((b0 / TILE) * d.nt2 + (b1 / TILE)) * d.nt3 + (b2 / TILE);
+            tile[k] = ((b0 >> d.tlog) * d.nt2 + (b1 >> d.tlog)) * d.nt3 + (b2 >> d.tlog);
             ra[k] = make_float4(w0, w1, w2, q);
             rb[k] = make_int2(b0 | (b1 << 10) | (b2 << 20), i);
             kind[k] = fabsf(q) <= Q_TILE_MAX ? 1 : 2;
@@ -162,15 +165,15 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
 // ---------------------------------------------------------------------------------------------------------
 // a2: charge spreading Q(k) = sum_i q_i theta1 theta2 theta3 (paper Sec. III-A "Charge Spreading": each
 // charge goes to the p^3 mesh points around it). A tile accumulates its atoms into a shared-memory region
-// R^3 (R = TILE + p - 1) as split 32-bit fixed point, then adds the region (including the p - 1 halo that
+// R^3 (R = tile edge + p - 1) as split 32-bit fixed point, then adds the region (including the p - 1 halo that
 // overlaps neighbouring tiles, the analogue of the paper's atoms processed by every pipeline they touch)
 // into the global int64 mesh with 64-bit integer reductions.
 
 PME_DEV void tile_origin(const SysDev &d, int tile, int &o1, int &o2, int &o3) {
     const int t3 = tile % d.nt3, t2 = (tile / d.nt3) % d.nt2, t1 = tile / (d.nt3 * d.nt2);
-    o1 = t1 * TILE;
-    o2 = t2 * TILE;
-    o3 = t3 * TILE;
+    o1 = t1 << d.tlog;
+    o2 = t2 << d.tlog;
+    o3 = t3 << d.tlog;
 }
 
 PME_DEV int wrapk(int k, int K) { return k < 0 ? k + K : (k >= K ? k - K : k); }
@@ -201,7 +204,7 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
     }
 }
 
-template <int P>
+template <int P, int T>
 PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {  // bucket-overflow atoms, straight to the global mesh
@@ -212,7 +215,7 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
             spread_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
         return;
     }
-    constexpr int R = Region<P>::R, VOL = Region<P>::VOL, H = P - 1;
+    constexpr int R = Region<P, T>::R, VOL = Region<P, T>::VOL, H = P - 1;
     int *hi = (int *)smem;
     unsigned *lo = (unsigned *)(hi + VOL);
     int o1, o2, o3;
@@ -575,6 +578,8 @@ PME_DEV void force_from_grad(const SysDev &d, float q, int idx, float g1, float 
         d.forces[3 * (size_t)idx + j] = -q * (d.chi[3 * j] * g1 + d.chi[3 * j + 1] * g2 + d.chi[3 * j + 2] * g3);
 }
 
+// Bucket-overflow atoms read phi from global memory but sum exactly like the tile path (two halves of the
+// j1 planes, then half 0 + half 1), so an atom's force has the same bits whichever path it takes.
 template <int P>
 PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
     float th1[P], th2[P], th3[P], dth1[P], dth2[P], dth3[P];
@@ -582,30 +587,38 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
     bspline_wd<P>(ra.y, th2, dth2);
     bspline_wd<P>(ra.z, th3, dth3);
     const int b1 = rb.x & 1023, b2 = (rb.x >> 10) & 1023, b3 = (rb.x >> 20) & 1023;
-    float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    float gh[2][3];
 #pragma unroll
-    for (int j1 = 0; j1 < P; ++j1) {
-        const int k1 = wrapk(b1 - j1, d.K1);
+    for (int half = 0; half < 2; ++half) {
+        float g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-        for (int j2 = 0; j2 < P; ++j2) {
-            const int k2 = wrapk(b2 - j2, d.K2);
-            const float *row = d.phi + ((size_t)k1 * d.K2 + k2) * d.K3;
-            float s = 0.f, ds = 0.f;
+        for (int jj = 0; jj < P / 2; ++jj) {
+            const int j1 = half * (P / 2) + jj;
+            const int k1 = wrapk(b1 - j1, d.K1);
 #pragma unroll
-            for (int j3 = 0; j3 < P; ++j3) {
-                const float ph = ldcg(row + wrapk(b3 - j3, d.K3));
-                s = fmaf(th3[j3], ph, s);
-                ds = fmaf(dth3[j3], ph, ds);
+            for (int j2 = 0; j2 < P; ++j2) {
+                const int k2 = wrapk(b2 - j2, d.K2);
+                const float *row = d.phi + ((size_t)k1 * d.K2 + k2) * d.K3;
+                float s = 0.f, ds = 0.f;
+#pragma unroll
+                for (int j3 = 0; j3 < P; ++j3) {
+                    const float ph = ldcg(row + wrapk(b3 - j3, d.K3));
+                    s = fmaf(th3[j3], ph, s);
+                    ds = fmaf(dth3[j3], ph, ds);
+                }
+                g1 = fmaf(dth1[j1] * th2[j2], s, g1);
+                g2 = fmaf(th1[j1] * dth2[j2], s, g2);
+                g3 = fmaf(th1[j1] * th2[j2], ds, g3);
             }
-            g1 = fmaf(dth1[j1] * th2[j2], s, g1);
-            g2 = fmaf(th1[j1] * dth2[j2], s, g2);
-            g3 = fmaf(th1[j1] * th2[j2], ds, g3);
         }
+        gh[half][0] = g1;
+        gh[half][1] = g2;
+        gh[half][2] = g3;
     }
-    force_from_grad<P>(d, ra.w, rb.y, g1, g2, g3);
+    force_from_grad<P>(d, ra.w, rb.y, gh[0][0] + gh[1][0], gh[0][1] + gh[1][1], gh[0][2] + gh[1][2]);
 }
 
-template <int P>
+template <int P, int T>
 PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {
@@ -614,7 +627,7 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         for (unsigned a = (unsigned)((item - d.ntiles) * nth + tid); a < novf; a += (unsigned)(OVF_ITEMS * nth))
             gather_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
     } else {
-        constexpr int R = Region<P>::R, VOL = Region<P>::VOL, H = P - 1;
+        constexpr int R = Region<P, T>::R, VOL = Region<P, T>::VOL, H = P - 1;
         float *reg = (float *)smem;
         int o1, o2, o3;
         tile_origin(d, item, o1, o2, o3);

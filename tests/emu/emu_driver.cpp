@@ -36,7 +36,8 @@ extern "C" {
 // ev[7], and optionally the fixed-point mesh as spread (grid_out, K1*K2*K3 int64) and phi (K1*K2*K3).
 // Returns the device status bits of the last evaluation, or -1 / -2 for invalid / unsupported input.
 int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p, double beta, const double box[9],
-             int cap_override, int repeat, float *forces, double *ev, long long *grid_out, float *phi_out) {
+             int cap_override, int repeat, float *forces, double *ev, long long *grid_out, float *phi_out,
+             int tile_log) {
     char msg[256];
     int v = validate_params(K, p, beta, box, msg, sizeof(msg));
     if (v) return -v;
@@ -58,6 +59,7 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     make_twiddles(K[1], K[1], s.tw.data() + K1);
     make_twiddles((int)Nh, (int)Nh, s.tw.data() + K1 + K2);
     make_twiddles(K[2], (int)Nh + 1, s.tw.data() + K1 + K2 + Nh);
+    set_tiling(d, tile_log > 0 ? tile_log : choose_tile_log(n > 0 ? n : 1, K));
     s.bcount.assign(bcount_bytes(d.ntiles) / sizeof(unsigned), 0u);
     s.partials.assign(partials_bytes(d) / sizeof(double), 0.0);
     const int cap = cap_override > 0 ? cap_override : bucket_capacity(n > 0 ? n : 1, d.ntiles);
@@ -65,7 +67,7 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     s.bkb.resize((size_t)d.ntiles * cap);
     s.ova.resize(n > 0 ? n : 1);
     s.ovb.resize(n > 0 ? n : 1);
-    size_t sm = std::max({smem_bin(1), smem_spread(p), smem_gather_all(p), smem_slab(K[1], K[2]), smem_inv(K[1], K[2]), smem_conv(K[0], 1)});
+    size_t sm = std::max({smem_bin(1), smem_spread(p, d.tlog), smem_gather_all(p, d.tlog), smem_slab(K[1], K[2]), smem_inv(K[1], K[2]), smem_conv(K[0], 1)});
     s.smem.assign(sm, 0);
     d.grid = s.grid.data();
     d.spec = s.spec.data();
@@ -94,10 +96,14 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     for (int rep = 0; rep < (repeat > 0 ? repeat : 1); ++rep) {
         for (int it = 0; it < (d.nbin > 0 ? d.nbin : 1); ++it) stage_bin(d, it, sp);
         for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
-            switch (p) {
-                case 4: stage_spread<4>(d, it, sp); break;
-                case 6: stage_spread<6>(d, it, sp); break;
-                default: stage_spread<8>(d, it, sp); break;
+            const int key = p * 10 + d.tlog;
+            switch (key) {
+                case 43: stage_spread<4, 8>(d, it, sp); break;
+                case 63: stage_spread<6, 8>(d, it, sp); break;
+                case 83: stage_spread<8, 8>(d, it, sp); break;
+                case 44: stage_spread<4, 16>(d, it, sp); break;
+                case 64: stage_spread<6, 16>(d, it, sp); break;
+                default: stage_spread<8, 16>(d, it, sp); break;
             }
         }
         if (grid_out) memcpy(grid_out, s.grid.data(), s.grid.size() * 8);
@@ -105,10 +111,14 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
         for (int it = 0; it < d.nconv; ++it) stage_conv(d, it, sp);
         for (int it = 0; it < K[0]; ++it) stage_inv(d, it, sp);
         for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
-            switch (p) {
-                case 4: stage_gather<4>(d, it, sp); break;
-                case 6: stage_gather<6>(d, it, sp); break;
-                default: stage_gather<8>(d, it, sp); break;
+            const int key = p * 10 + d.tlog;
+            switch (key) {
+                case 43: stage_gather<4, 8>(d, it, sp); break;
+                case 63: stage_gather<6, 8>(d, it, sp); break;
+                case 83: stage_gather<8, 8>(d, it, sp); break;
+                case 44: stage_gather<4, 16>(d, it, sp); break;
+                case 64: stage_gather<6, 16>(d, it, sp); break;
+                default: stage_gather<8, 16>(d, it, sp); break;
             }
         }
         status = s.ctl.status;

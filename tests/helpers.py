@@ -45,12 +45,12 @@ def build_emu(force=False):
     lib = ctypes.CDLL(EMU_LIB)
     dp, fp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
     lib.emu_spme.argtypes = [ctypes.c_int64, fp, fp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double, dp,
-                             ctypes.c_int, ctypes.c_int, fp, dp, ctypes.POINTER(ctypes.c_longlong), fp]
+                             ctypes.c_int, ctypes.c_int, fp, dp, ctypes.POINTER(ctypes.c_longlong), fp, ctypes.c_int]
     lib.emu_spme.restype = ctypes.c_int
     return lib
 
 
-def emu_spme(lib, pos, q, K, p, beta, box, cap=0, repeat=1):
+def emu_spme(lib, pos, q, K, p, beta, box, cap=0, repeat=1, tile_log=0):
     """Run the emulated pipeline; returns (status, forces, ev[7], mesh int64, phi float32)."""
     pos = np.ascontiguousarray(pos, np.float32)
     q = np.ascontiguousarray(q, np.float32)
@@ -63,7 +63,7 @@ def emu_spme(lib, pos, q, K, p, beta, box, cap=0, repeat=1):
     dp, fp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
     st = lib.emu_spme(n, pos.ctypes.data_as(fp), q.ctypes.data_as(fp), (ctypes.c_int * 3)(*K), p, beta,
                       bx.ctypes.data_as(dp), cap, repeat, F.ctypes.data_as(fp), ev.ctypes.data_as(dp),
-                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), phi.ctypes.data_as(fp))
+                      g.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), phi.ctypes.data_as(fp), tile_log)
     return st, F, ev, g, phi
 
 

@@ -53,18 +53,29 @@ def test_emulated_triclinic(oracle_mod, emu):
 
 
 def test_emulated_overflow_path_and_repeat(oracle_mod, emu):
-    """Tiny bucket capacity sends most atoms down the overflow path; two evaluations in a row must agree
-    bit for bit (every counter and the int64 mesh are reset by their consumers; status 0x100 flags a
-    leftover)."""
+    """Tiny bucket capacity sends most atoms down the overflow path: mesh, forces and energies match the
+    tile path bit for bit, and repeated evaluations agree (every counter and the int64 mesh are reset by
+    their consumers; status 0x100 flags a leftover)."""
     s = wl.parity_system()
     st1, F1, ev1, m1, _ = emu_spme(emu, s.pos, s.q, (32, 32, 32), 4, 0.34, s.box, cap=32, repeat=1)
     st2, F2, ev2, m2, _ = emu_spme(emu, s.pos, s.q, (32, 32, 32), 4, 0.34, s.box, cap=0, repeat=3)
     assert st1 == 0 and st2 == 0
     assert np.array_equal(m1, m2)
+    # an atom's force has the same bits on the overflow path and on the tile path
+    assert np.array_equal(F1, F2) and np.array_equal(ev1, ev2)
     r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), (32, 32, 32), 4, 0.34, s.box)
     for F, ev in ((F1, ev1), (F2, ev2)):
         assert rel_energy(ev[0], r["energy"]) < E_REL_TOL
         assert rms_force(F, r["forces"]) < F_RMS_TOL
+
+
+def test_emulated_results_do_not_depend_on_tiling(emu):
+    """8^3 and 16^3 tiles give bit-identical meshes, forces and energies (tiling only reorders exact sums)."""
+    s = wl.parity_system()
+    _, F8, ev8, m8, _ = emu_spme(emu, s.pos, s.q, (32, 40, 48), 6, 0.34, s.box, tile_log=3)
+    _, F16, ev16, m16, _ = emu_spme(emu, s.pos, s.q, (32, 40, 48), 6, 0.34, s.box, tile_log=4)
+    assert np.array_equal(m8, m16)
+    assert np.array_equal(F8, F16) and np.array_equal(ev8, ev16)
 
 
 def test_emulated_mesh_permutation_invariant(emu):
