@@ -145,7 +145,7 @@ def stage_bytes(n: int, K, p: int) -> dict:
         "bin": n * (12 + 4 + 24),            # position + charge in, bucket record out
         "spread": n * 24 + mesh * 8,         # bucket records in, int64 mesh out
         "fft_fwd": mesh * 8 + half * 8,      # int64 mesh in, complex half spectrum out
-        "influence": half * (8 + 8 + 8),     # spectrum in, influence table in, spectrum out
+        "influence": half * (8 + 16 + 8),    # spectrum in, influence table (float4) in, spectrum out
         "fft_inv": half * 8 + mesh * 4,      # spectrum in, phi out
         "gather": mesh * 4 + n * (24 + 12),  # phi in, records in, forces out
     }

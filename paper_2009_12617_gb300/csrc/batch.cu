@@ -67,19 +67,27 @@ __device__ __noinline__ void call_gather(const SysDev &d, int item, void *smem) 
     else stage_gather<P, 8>(d, item, smem);
 }
 
-template <int P>
+// One kernel for every order: the order-specific stages dispatch on the system's p, and the other stage
+// calls are compiled once.
 __device__ __forceinline__ void run_stage(const SysDev &d, int stage, int item, void *smem) {
     switch (stage) {
         case STAGE_BIN: call_bin(d, item, smem); break;
-        case STAGE_SPREAD: call_spread<P>(d, item, smem); break;
+        case STAGE_SPREAD:
+            if (d.p == 4) call_spread<4>(d, item, smem);
+            else if (d.p == 6) call_spread<6>(d, item, smem);
+            else call_spread<8>(d, item, smem);
+            break;
         case STAGE_FWD: call_fwd(d, item, smem); break;
         case STAGE_CONV: call_conv(d, item, smem); break;
         case STAGE_INV: call_inv(d, item, smem); break;
-        default: call_gather<P>(d, item, smem); break;
+        default:
+            if (d.p == 4) call_gather<4>(d, item, smem);
+            else if (d.p == 6) call_gather<6>(d, item, smem);
+            else call_gather<8>(d, item, smem);
+            break;
     }
 }
 
-template <int P>
 __global__ void __launch_bounds__(NT_BATCH, 4) k_batch(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
@@ -106,7 +114,7 @@ __global__ void __launch_bounds__(NT_BATCH, 4) k_batch(BatchArgs a) {
         __syncthreads();
         if (s_ok) {
             for (int it = w.begin; it < w.end; ++it) {
-                run_stage<P>(sd, stage, it, smem);
+                run_stage(sd, stage, it, smem);
                 __syncthreads();
             }
         }
@@ -178,31 +186,23 @@ size_t batch_smem(const std::vector<SysDev> &sys) {
     return m;
 }
 
-static const void *batch_kernel(int p) {
-    return p == 4 ? (const void *)k_batch<4> : (p == 6 ? (const void *)k_batch<6> : (const void *)k_batch<8>);
-}
-
 cudaError_t configure_batch_kernel() {
-    for (int p : {4, 6, 8}) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel(p), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(MAX_SMEM_BYTES - sizeof(SysDev) - 64));
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(MAX_SMEM_BYTES - sizeof(SysDev) - 64));
 }
 
 int batch_grid(int dev, int p, size_t smem) {
+    (void)p;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(p), NT_BATCH, smem) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_batch, NT_BATCH, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     return sms * per_sm;
 }
 
 cudaError_t launch_batch(const BatchArgs &a, int p, int grid, size_t smem, cudaStream_t s) {
-    if (p == 4) k_batch<4><<<grid, NT_BATCH, smem, s>>>(a);
-    else if (p == 6) k_batch<6><<<grid, NT_BATCH, smem, s>>>(a);
-    else k_batch<8><<<grid, NT_BATCH, smem, s>>>(a);
+    (void)p;
+    k_batch<<<grid, NT_BATCH, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -49,14 +49,25 @@ constexpr int OVF_ITEMS = 8;     // extra spread / gather work items that handle
 constexpr int MAX_K = 128;
 // Tile counters sit on separate 128-byte lines so the binning atomics spread over the L2 slices.
 constexpr int BCOUNT_STRIDE = 32;
-// Shared-memory accumulation splits each fixed-point contribution v into hi = floor(v / 2^20) and
-// lo = v - hi 2^20 in [0, 2^20], summed in two int32 arrays with native 32-bit atomics. With at most
-// CAP_MAX atoms per tile and |q| <= Q_TILE_MAX (|v| <= 2^41), neither sum can overflow; atoms with larger
-// charges take the 64-bit global path instead.
+// Shared-memory accumulation splits each fixed-point contribution v into hi = rn(v / 2^20) and
+// lo = rn(v - hi 2^20) in [-2^19, 2^19], summed in two int32 arrays with native 32-bit atomics. With at
+// most CAP_MAX atoms per tile and |q| <= Q_TILE_MAX (|v| <= 2^41), neither sum can overflow; atoms with
+// larger charges take the 64-bit global path instead.
 constexpr float Q_TILE_MAX = 2.0f;
 constexpr int CAP_MAX = 512;
-// Columns m3 per influence-stage work item.
+// Columns m3 per influence-stage work item (shared-memory transform path).
 constexpr int CONV_COLS = 8;
+// Lane plans of the register-resident transforms: plan c has length LANE_L[c] * LANE_E[c], L lanes of
+// E points each (fft.cuh, lane_fft). Lengths without a plan use the shared-memory Stockham path.
+constexpr int LANE_PLANS = 21;
+#define PME_LANE_CASES(X)                                                                               \
+    X(0, 1, 4) X(1, 1, 5) X(2, 1, 6) X(3, 1, 8) X(4, 2, 4) X(5, 2, 5) X(6, 2, 6) X(7, 2, 8) X(8, 4, 4) \
+        X(9, 4, 5) X(10, 4, 6) X(11, 4, 8) X(12, 8, 4) X(13, 8, 5) X(14, 8, 6) X(15, 8, 8) X(16, 16, 4) \
+            X(17, 16, 5) X(18, 16, 6) X(19, 16, 8) X(20, 32, 4)
+// Threads (lanes) per influence-stage work item on the register path: 128 / L columns of L lanes each.
+constexpr int CONV_UNITS = 128;
+// Threads of a slab-stage CTA (the register path picks its lane plans to fill about this many).
+constexpr int SLAB_THREADS = 512;
 // Independent global loads each thread keeps in flight when staging data into shared memory.
 constexpr int LOAD_BATCH = 8;
 // Slots of the fixed-order final energy / virial reduction (a power of two, >= MAX_K / 2).
@@ -89,8 +100,11 @@ struct SysDev {
     int cap;                     // bucket capacity (atoms per tile)
     int n;                       // atoms
     int nbin;                    // binning work items = ceil(n / BIN_CHUNK)
-    int nchunk3;                 // influence-stage column chunks = ceil(H3 / CONV_COLS)
-    int nconv;                   // influence-stage work items = K2 * nchunk3
+    int nchunk3;                 // influence-stage column chunks = ceil(H3 / CONV_COLS) (shared-memory path)
+    int nconv;                   // influence-stage work items: K2 * nchunk3, or the register path's
+                                 // ceil(K2 * H3 / columns per item)
+    int lp_rows, lp_cols, lp_k1; // lane plans (PME_LANE_CASES) of the K3/2, K2 and K1 transforms, -1: none
+    int lane_slab, lane_conv;    // slab stages / influence stage take the register path (1) or not (0)
     int pdl_late;                // launch option of the per-stage kernels (see kernels.cu)
     float kinv[3];               // 1 / K_alpha
     // u_alpha = sum_j r_j C[j][alpha], C[j][alpha] = K_alpha a*_alpha[j], as an unevaluated float sum
@@ -108,7 +122,10 @@ struct SysDev {
     unsigned long long *grid;    // K1*K2*K3 int64 fixed-point charge mesh, [k1][k2][k3]
     float2 *spec;                // K1*K2*H3 complex half spectrum, [k1][m2][m3]
     float *phi;                  // K1*K2*K3 potential mesh, [k1][k2][k3]
-    const float2 *bc;            // influence table B*C as (hi, lo) floats, [m2][m1][m3]
+    // influence table per half-spectrum point, [m2][m1][m3]: x, y = B*C as (hi, lo) floats; z = B*C f(m) and
+    // w = B*C f(m_p) with f = 2 (1 / |m'|^2 + pi^2 / beta^2), m_p the conjugate partner kept separately on
+    // Nyquist planes (w = 0 elsewhere), for the virial
+    const float4 *bc;
     const float2 *tw1, *tw2;     // exp(-2 pi i k / K1), exp(-2 pi i k / K2)
     const float2 *tw3h, *tw3;    // exp(-2 pi i k / (K3/2)), exp(-2 pi i k / K3) for k <= K3/2
     float4 *bka;                 // bucket records (w1, w2, w3, q), [tile][cap]
@@ -126,7 +143,6 @@ struct SysDev {
 #if defined(PME_HOST_EMULATION)
 template <class T> inline T ldcg(const T *p) { return *p; }
 inline unsigned atomic_add_u32(unsigned *p, unsigned v) { unsigned o = *p; *p = o + v; return o; }
-inline void atomic_add_u32_nr(unsigned *p, unsigned v) { *p += v; }
 inline void atomic_add_i32(int *p, int v) { *p += v; }
 inline void atomic_or_u32(unsigned *p, unsigned v) { *p |= v; }
 inline void atomic_add_u64(unsigned long long *p, unsigned long long v) { *p += v; }
@@ -140,7 +156,6 @@ inline int f2i_rn(float x) { return (int)rintf(x); }
 #else
 template <class T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned atomic_add_u32(unsigned *p, unsigned v) { return atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_add_u32_nr(unsigned *p, unsigned v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add_i32(int *p, int v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_or_u32(unsigned *p, unsigned v) { atomicOr(p, v); }
 __device__ __forceinline__ void atomic_add_u64(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
@@ -177,6 +192,17 @@ PME_DEV float qnan_f() {
     v.u = 0x7fc00000u;
     return v.f;
 }
+
+// The bits of a float as an int (a register move on the GPU).
+#if defined(PME_HOST_EMULATION)
+inline int float_bits(float f) {
+    int i;
+    memcpy(&i, &f, sizeof(i));
+    return i;
+}
+#else
+__device__ __forceinline__ int float_bits(float f) { return __float_as_int(f); }
+#endif
 
 // int64 fixed point (scale 2^40) -> float. Split into a signed high word and an unsigned low word so
 // only 32-bit conversions are used; the result is within one rounding of v * 2^-40.

@@ -132,6 +132,32 @@ PME_DEV void dft_small<5, true>(float2 *v) {
     dft5<true>(v);
 }
 
+// Length 6 as 3 x 2 (Cooley-Tukey): DFT3 of the even and of the odd points, twiddles W6^k, then DFT2.
+template <bool INV>
+PME_DEV void dft6(float2 *v) {
+    float2 a[3] = {v[0], v[2], v[4]}, b[3] = {v[1], v[3], v[5]};
+    dft3<INV>(a);
+    dft3<INV>(b);
+    const float s = 0.86602540378443864676f;  // sin(pi / 3)
+    // W6^1 = (1/2, -s) forward, (1/2, s) inverse; W6^2 = (-1/2, -s) forward, (-1/2, s) inverse
+    const float sg = INV ? s : -s;
+    b[1] = cmul(b[1], make_float2(0.5f, sg));
+    b[2] = cmul(b[2], make_float2(-0.5f, sg));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = cadd(a[k], b[k]);
+        v[k + 3] = csub(a[k], b[k]);
+    }
+}
+template <>
+PME_DEV void dft_small<6, false>(float2 *v) {
+    dft6<false>(v);
+}
+template <>
+PME_DEV void dft_small<6, true>(float2 *v) {
+    dft6<true>(v);
+}
+
 // Radix chosen for the remaining length rem = N / Ns: 8, then 4, 2, 3, 5.
 PME_DEV int fft_radix(int rem) {
     if (rem % 8 == 0) return 8;
@@ -201,5 +227,113 @@ PME_DEV float2 *fft_batch(float2 *a, float2 *b, int N, int ntr, int es, int bs, 
     }
     return a;
 }
+
+#if !defined(PME_HOST_EMULATION)
+// ---------------------------------------------------------------------------------------------------------
+// Lane-distributed transforms in registers, for lengths N = L * E with L in {1, 2, 4, 8, 16} and
+// E in {4, 5, 6, 8} (every lane plan below). The L lanes of one transform sit in one warp at lane ids
+// t + T j (T = 32 / L transforms per warp, j = 0 .. L - 1), so a transform's lanes exchange values with
+// shuffles and no CTA barrier. Lane j holds the E points x[j + L n], n < E, and the four-step
+// factorisation N = E x L runs as:
+//   1. an E-point DFT in each lane over n:          y_j[k] = sum_n x[j + L n] W_E^{n k}
+//   2. twiddles:                                    y_j[k] *= W_N^{j k}
+//   3. an L-point DFT across lanes over j, as log2 L radix-2 decimation-in-frequency rounds: the lane
+//      with bit h of j clear keeps a + b, its partner (bit h set) keeps (a - b) W_{2h}^{j mod h}.
+// Afterwards lane j holds X[k + E rev(j)], k < E, where rev reverses the log2 L bits of j. Inverse
+// transforms conjugate every twiddle. lane_fft_adjoint applies the conjugate transpose of the whole
+// sequence, which takes the bit-reversed distribution back to x[j + L n] and is the unnormalised
+// inverse DFT: a forward transform, a pointwise product and the adjoint need no reordering in between.
+
+template <int L>
+PME_DEV int lane_rev(int j) {
+    int r = 0;
+#pragma unroll
+    for (int b = 1; b < L; b <<= 1) r = (r << 1) | ((j & b) ? 1 : 0);
+    return r;
+}
+
+template <int L>
+struct Log2 {
+    static constexpr int v = L <= 1 ? 0 : 1 + Log2<L / 2>::v;
+};
+template <>
+struct Log2<1> {
+    static constexpr int v = 0;
+};
+
+// The twiddles one lane needs (forward sign), loaded once so their latency overlaps the data loads and
+// the inverse / adjoint transforms reuse them: w[k - 1] = W_N^{j k}, k = 1 .. E - 1, and r[i] =
+// W_{2h}^{j mod h} for the cross-lane round h = L / 2^(i + 1).
+template <int L, int E>
+struct LaneTw {
+    float2 w[E > 1 ? E - 1 : 1];
+    float2 r[Log2<L>::v > 0 ? Log2<L>::v : 1];
+};
+
+// tw[t] = exp(-2 pi i t / N), t < N, in global (read-only path) or shared memory.
+template <int L, int E, bool GLOBAL>
+PME_DEV LaneTw<L, E> lane_tw(const float2 *tw, int j) {
+    constexpr int N = L * E;
+    LaneTw<L, E> t;
+    if (L > 1) {
+#pragma unroll
+        for (int k = 1; k < E; ++k) t.w[k - 1] = GLOBAL ? __ldg(tw + j * k) : tw[j * k];
+#pragma unroll
+        for (int i = 0, h = L / 2; h >= 1; ++i, h >>= 1) {
+            const int idx = (j & (h - 1)) * (N / (2 * h));
+            t.r[i] = GLOBAL ? __ldg(tw + idx) : tw[idx];
+        }
+    }
+    return t;
+}
+
+PME_DEV float2 shfl_xor_c(float2 v, int mask) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask));
+}
+
+PME_DEV float2 cmul_c(float2 a, float2 w, bool conj) { return conj ? cmul(a, cconj(w)) : cmul(a, w); }
+
+template <int L, int E, bool INV>
+PME_DEV void lane_fft(float2 (&v)[E], int j, const LaneTw<L, E> &tw) {
+    constexpr int T = 32 / L;
+    dft_small<E, INV>(v);
+    if (L > 1) {
+#pragma unroll
+        for (int k = 1; k < E; ++k) v[k] = cmul_c(v[k], tw.w[k - 1], INV);
+#pragma unroll
+        for (int i = 0, h = L / 2; h >= 1; ++i, h >>= 1) {
+            const bool up = (j & h) != 0;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const float2 p = shfl_xor_c(v[k], h * T);
+                v[k] = up ? (h > 1 ? cmul_c(csub(p, v[k]), tw.r[i], INV) : csub(p, v[k])) : cadd(v[k], p);
+            }
+        }
+    }
+}
+
+template <int L, int E>
+PME_DEV void lane_fft_adjoint(float2 (&v)[E], int j, const LaneTw<L, E> &tw) {
+    constexpr int T = 32 / L;
+    if (L > 1) {
+#pragma unroll
+        for (int i = Log2<L>::v - 1, h = 1; h < L; --i, h <<= 1) {
+            const bool up = (j & h) != 0;
+            if (up && h > 1) {
+#pragma unroll
+                for (int k = 0; k < E; ++k) v[k] = cmul_c(v[k], tw.r[i], true);
+            }
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const float2 p = shfl_xor_c(v[k], h * T);
+                v[k] = up ? csub(p, v[k]) : cadd(v[k], p);
+            }
+        }
+#pragma unroll
+        for (int k = 1; k < E; ++k) v[k] = cmul_c(v[k], tw.w[k - 1], true);
+    }
+    dft_small<E, true>(v);
+}
+#endif  // !PME_HOST_EMULATION
 
 }  // namespace pme

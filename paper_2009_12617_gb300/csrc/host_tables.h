@@ -89,6 +89,73 @@ inline int choose_tile_log(int64_t n, const int K[3]) {
     return TILE_MIN_LOG;
 }
 
+// Lane plans (PME_LANE_CASES): lanes L and points per lane E of plan c.
+inline int lane_plan_lanes(int c) {
+    static const int Ls[LANE_PLANS] = {
+#define PME_LANE_L(c, L, E) L,
+        PME_LANE_CASES(PME_LANE_L)
+#undef PME_LANE_L
+    };
+    return Ls[c];
+}
+inline int lane_plan_points(int c) {
+    static const int Es[LANE_PLANS] = {
+#define PME_LANE_E(c, L, E) E,
+        PME_LANE_CASES(PME_LANE_E)
+#undef PME_LANE_E
+    };
+    return Es[c];
+}
+
+// Plan for ntr transforms of length N in one slab CTA: the fewest points per lane (the shortest serial
+// chain per thread) whose lanes still fit in SLAB_THREADS, else the plan with the fewest lanes; -1 when N
+// has no plan.
+inline int slab_lane_plan(int N, int ntr) {
+    int best = -1, fewest = -1;
+    for (int c = 0; c < LANE_PLANS; ++c) {
+        const int L = lane_plan_lanes(c), E = lane_plan_points(c);
+        if (L * E != N) continue;
+        const int T = 32 / L, units = ((ntr + T - 1) / T) * 32;
+        if (units <= SLAB_THREADS && (best < 0 || E < lane_plan_points(best))) best = c;
+        if (fewest < 0 || L < lane_plan_lanes(fewest)) fewest = c;
+    }
+    return best >= 0 ? best : fewest;
+}
+
+// Plan of the influence stage's K1-point transforms: the fewest points per lane, so that the work spreads
+// over as many threads as possible.
+inline int conv_lane_plan(int N) {
+    int best = -1;
+    for (int c = 0; c < LANE_PLANS; ++c)
+        if (lane_plan_lanes(c) * lane_plan_points(c) == N && (best < 0 || lane_plan_points(c) < lane_plan_points(best)))
+            best = c;
+    return best;
+}
+
+// Transform paths: the register path (lane plans) wherever both transforms of a slab stage, or the K1
+// transform of the influence stage, have a plan; the shared-memory Stockham path otherwise. The CPU
+// emulation of the stage bodies (one thread per CTA) has no lanes and always takes the shared-memory path.
+inline void choose_fft_paths(SysDev &d, bool lanes) {
+    d.lp_rows = lanes ? slab_lane_plan(d.K3 / 2, d.K2) : -1;
+    d.lp_cols = lanes ? slab_lane_plan(d.K2, d.H3) : -1;
+    d.lp_k1 = lanes ? conv_lane_plan(d.K1) : -1;
+    d.lane_slab = (d.lp_rows >= 0 && d.lp_cols >= 0) ? 1 : 0;
+    d.lane_conv = d.lp_k1 >= 0 ? 1 : 0;
+    d.nchunk3 = (d.H3 + CONV_COLS - 1) / CONV_COLS;
+    if (d.lane_conv) {
+        const int cols = CONV_UNITS / lane_plan_lanes(d.lp_k1);  // columns per work item
+        d.nconv = (d.K2 * d.H3 + cols - 1) / cols;
+    } else {
+        d.nconv = d.K2 * d.nchunk3;
+    }
+}
+
+#if defined(PME_HOST_EMULATION)
+constexpr bool LANE_FFT_DEFAULT = false;
+#else
+constexpr bool LANE_FFT_DEFAULT = true;
+#endif
+
 // Mesh geometry, coordinate transform and tiling of a system.
 inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const double recip[9]) {
     d.K1 = K[0];
@@ -97,8 +164,7 @@ inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const d
     d.H3 = K[2] / 2 + 1;
     d.p = p;
     set_tiling(d, TILE_MIN_LOG);
-    d.nchunk3 = (d.H3 + CONV_COLS - 1) / CONV_COLS;
-    d.nconv = d.K2 * d.nchunk3;
+    choose_fft_paths(d, LANE_FFT_DEFAULT);
     for (int a = 0; a < 3; ++a) d.kinv[a] = 1.0f / (float)K[a];
     for (int j = 0; j < 3; ++j)
         for (int al = 0; al < 3; ++al) {
@@ -149,32 +215,45 @@ inline std::vector<double> bspline_moduli(int K, int p) {
 
 inline int signed_freq_h(int m, int K) { return 2 * m <= K ? m : m - K; }
 
-// Influence table on the half spectrum, [m2][m1][m3] with m3 <= K3/2, as (hi, lo) floats of the FP64
-// value B(m) (C(m) + C(-m)) / 2 (the even part of B*C; the two halves differ only on Nyquist axes of
-// non-orthogonal cells, because index K/2 always means frequency +K/2). C(0) = 0.
-inline void make_influence(const int K[3], int p, double beta, const double recip[9], double vol, float2 *out) {
+// Influence table on the half spectrum, [m2][m1][m3] with m3 <= K3/2 (layout of SysDev::bc): the even part
+// B(m) (C(m) + C(-m)) / 2 of B*C as (hi, lo) floats of its FP64 value (the two halves differ only on Nyquist
+// axes of non-orthogonal cells, because index K/2 always means frequency +K/2; C(0) = 0), and the virial factors B C f(m), B C f(m_p) in FP64 rounded
+// once, f = 2 (1 / |m'|^2 + pi^2 / beta^2). m_p (the point's conjugate partner, whose frequencies keep +K/2 on
+// a Nyquist axis) gets its own factor only where it differs from -m: off the self-conjugate planes m3 = 0,
+// K3/2 and on a Nyquist plane m1 = K1/2 or m2 = K2/2; elsewhere w = 0.
+inline void make_influence(const int K[3], int p, double beta, const double recip[9], double vol, float4 *out) {
     const std::vector<double> b1 = bspline_moduli(K[0], p), b2 = bspline_moduli(K[1], p), b3 = bspline_moduli(K[2], p);
     const int H3 = K[2] / 2 + 1;
     const double fac = PI_D * PI_D / (beta * beta);
-    auto C = [&](int mt1, int mt2, int mt3) {
+    auto norm2 = [&](int mt1, int mt2, int mt3) {
         double mv[3];
         for (int j = 0; j < 3; ++j) mv[j] = mt1 * recip[j] + mt2 * recip[3 + j] + mt3 * recip[6 + j];
-        const double m2n = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
-        return exp(-fac * m2n) / (PI_D * vol * m2n);
+        return mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
     };
+    auto C = [&](double m2n) { return exp(-fac * m2n) / (PI_D * vol * m2n); };
+    auto f = [&](double m2n) { return 2.0 * (1.0 / m2n + fac); };
     for (int m2 = 0; m2 < K[1]; ++m2)
         for (int m1 = 0; m1 < K[0]; ++m1)
             for (int m3 = 0; m3 < H3; ++m3) {
-                double v = 0.0;
+                double v = 0.0, g = 0.0, gp = 0.0;
                 if (m1 | m2 | m3) {
-                    const double cm = C(signed_freq_h(m1, K[0]), signed_freq_h(m2, K[1]), signed_freq_h(m3, K[2]));
-                    const double cp = C(signed_freq_h((K[0] - m1) % K[0], K[0]), signed_freq_h((K[1] - m2) % K[1], K[1]),
-                                        signed_freq_h((K[2] - m3) % K[2], K[2]));
-                    v = b1[m1] * b2[m2] * b3[m3] * 0.5 * (cm + cp);
+                    const int mt1 = signed_freq_h(m1, K[0]), mt2 = signed_freq_h(m2, K[1]), mt3 = signed_freq_h(m3, K[2]);
+                    const double nm = norm2(mt1, mt2, mt3);
+                    const double np = norm2(signed_freq_h((K[0] - m1) % K[0], K[0]), signed_freq_h((K[1] - m2) % K[1], K[1]),
+                                            signed_freq_h((K[2] - m3) % K[2], K[2]));
+                    v = b1[m1] * b2[m2] * b3[m3] * 0.5 * (C(nm) + C(np));
+                    g = v * f(nm);
+                    const bool self = m3 == 0 || 2 * m3 == K[2];
+                    if (!self && (2 * m1 == K[0] || 2 * m2 == K[1])) {
+                        const double npart = norm2(2 * m1 == K[0] ? mt1 : -mt1, 2 * m2 == K[1] ? mt2 : -mt2, -mt3);
+                        gp = v * f(npart);
+                    }
                 }
-                float2 &o = out[((size_t)m2 * K[0] + m1) * H3 + m3];
+                float4 &o = out[((size_t)m2 * K[0] + m1) * H3 + m3];
                 o.x = (float)v;
                 o.y = (float)(v - (double)o.x);
+                o.z = (float)g;
+                o.w = (float)gp;
             }
 }
 

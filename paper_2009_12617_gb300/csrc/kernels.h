@@ -8,7 +8,7 @@
 namespace pme {
 
 constexpr int NT_BIN = 128;    // threads per CTA for binning (BIN_CHUNK atoms per CTA)
-constexpr int NT_SLAB = 512;   // threads per CTA for the forward / inverse slab FFT stages
+constexpr int NT_SLAB = SLAB_THREADS;  // threads per CTA for the forward / inverse slab FFT stages
 constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interpolation (two per atom)
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
 constexpr size_t MAX_SMEM_BYTES = 226 * 1024;  // opt-in limit is 227 KB including static shared memory

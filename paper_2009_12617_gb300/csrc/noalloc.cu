@@ -17,6 +17,9 @@
 
 #include <mutex>
 
+// The single cooperative kernel keeps only the shared-memory transforms (one code path per stage keeps it
+// small to build); its plans say so through choose_fft_paths(d, false).
+#define PME_NO_LANE_FFT 1
 #include "../../include/pme.h"
 #include "host_tables.h"
 #include "kernels.h"
@@ -45,20 +48,27 @@ struct NoallocArgs {
     double recip[9];  // a*_alpha[j] at 3*alpha + j
     double vol, beta;
     double *bmod;     // |b_1|^2 (K1), |b_2|^2 (K2), |b_3|^2 (K3)
-    float2 *bc;       // writable alias of d.bc
+    float4 *bc;       // writable alias of d.bc
     float2 *tw;       // writable alias of the twiddle block (K1 + K2 + K3/2 + K3/2 + 1)
     unsigned long long zero_bytes;  // bytes from the scratch start that must be zero before binning
 };
 
 __device__ double dev_signed_freq(int m, int K) { return (double)(2 * m <= K ? m : m - K); }
 
-__device__ double dev_influence_c(const NoallocArgs &A, double mt1, double mt2, double mt3) {
+__device__ double dev_norm2(const NoallocArgs &A, double mt1, double mt2, double mt3) {
     const double *r = A.recip;
     double mv[3];
     for (int j = 0; j < 3; ++j) mv[j] = mt1 * r[j] + mt2 * r[3 + j] + mt3 * r[6 + j];
-    const double m2n = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+    return mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
+}
+// C(m) and the virial factor f(m) = 2 (1 / |m'|^2 + pi^2 / beta^2) from |m'|^2
+__device__ double dev_influence_c(const NoallocArgs &A, double m2n) {
     const double pi = 3.14159265358979323846;
     return exp(-pi * pi * m2n / (A.beta * A.beta)) / (pi * A.vol * m2n);
+}
+__device__ double dev_virial_f(const NoallocArgs &A, double m2n) {
+    const double pi = 3.14159265358979323846;
+    return 2.0 * (1.0 / m2n + pi * pi / (A.beta * A.beta));
 }
 
 template <int P>
@@ -109,23 +119,29 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_eval_noalloc(NoallocArgs A)
         }
     }
     grid.sync();
-    // 1: influence table B(m) (C(m) + C(-m)) / 2 on the half spectrum, [m2][m1][m3], as (hi, lo) floats
+    // 1: influence table on the half spectrum, [m2][m1][m3] (SysDev::bc): B(m) (C(m) + C(-m)) / 2 as (hi, lo)
+    // floats, then B C f(m) and, off the self-conjugate planes on a Nyquist plane, B C f(m_p)
     {
         const int H3 = d.H3;
         const int tot = d.K1 * d.K2 * H3;
         for (int i = gtid; i < tot; i += gnth) {
             const int m3 = i % H3, m1 = (i / H3) % d.K1, m2 = i / (H3 * d.K1);
-            double v = 0.0;
+            double v = 0.0, g = 0.0, gp = 0.0;
             if (m1 | m2 | m3) {
-                const double cm = dev_influence_c(A, dev_signed_freq(m1, d.K1), dev_signed_freq(m2, d.K2),
-                                                  dev_signed_freq(m3, d.K3));
-                const double cp = dev_influence_c(A, dev_signed_freq((d.K1 - m1) % d.K1, d.K1),
-                                                  dev_signed_freq((d.K2 - m2) % d.K2, d.K2),
-                                                  dev_signed_freq((d.K3 - m3) % d.K3, d.K3));
-                v = A.bmod[m1] * A.bmod[d.K1 + m2] * A.bmod[d.K1 + d.K2 + m3] * 0.5 * (cm + cp);
+                const int mt1 = dev_signed_freq(m1, d.K1), mt2 = dev_signed_freq(m2, d.K2), mt3 = dev_signed_freq(m3, d.K3);
+                const double nm = dev_norm2(A, mt1, mt2, mt3);
+                const double np = dev_norm2(A, dev_signed_freq((d.K1 - m1) % d.K1, d.K1),
+                                            dev_signed_freq((d.K2 - m2) % d.K2, d.K2),
+                                            dev_signed_freq((d.K3 - m3) % d.K3, d.K3));
+                v = A.bmod[m1] * A.bmod[d.K1 + m2] * A.bmod[d.K1 + d.K2 + m3] * 0.5 *
+                    (dev_influence_c(A, nm) + dev_influence_c(A, np));
+                g = v * dev_virial_f(A, nm);
+                const bool self = m3 == 0 || 2 * m3 == d.K3;
+                if (!self && (2 * m1 == d.K1 || 2 * m2 == d.K2))
+                    gp = v * dev_virial_f(A, dev_norm2(A, 2 * m1 == d.K1 ? mt1 : -mt1, 2 * m2 == d.K2 ? mt2 : -mt2, -mt3));
             }
             const float hi = (float)v;
-            A.bc[i] = make_float2(hi, (float)(v - (double)hi));
+            A.bc[i] = make_float4(hi, (float)(v - (double)hi), (float)g, (float)gp);
         }
     }
     grid.sync();
@@ -235,6 +251,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     memset(&A, 0, sizeof(A));
     SysDev &d = A.d;
     fill_geometry(d, K, p, beta, recip);
+    choose_fft_paths(d, false);
     const size_t K1 = K[0], K2 = K[1], K3 = K[2], H3 = d.H3, Nh = K3 / 2;
     const int64_t ncap = n > 0 ? n : 1;
     const int cap = bucket_capacity(ncap, d.ntiles);
@@ -246,7 +263,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     const size_t zero_bytes = off;
     const size_t o_bmod = off; off = al256(off + (K1 + K2 + K3) * 8);
     const size_t o_tw = off;   off = al256(off + (K1 + K2 + Nh + Nh + 1) * 8);
-    const size_t o_bc = off;   off = al256(off + K1 * K2 * H3 * 8);
+    const size_t o_bc = off;   off = al256(off + K1 * K2 * H3 * sizeof(float4));
     const size_t o_spec = off; off = al256(off + K1 * K2 * H3 * 8);
     const size_t o_phi = off;  off = al256(off + K1 * K2 * K3 * 4);
     const size_t o_bka = off;  off = al256(off + (size_t)d.ntiles * cap * 16);
@@ -267,7 +284,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     d.tw2 = A.tw + K1;
     d.tw3h = A.tw + K1 + K2;
     d.tw3 = A.tw + K1 + K2 + Nh;
-    A.bc = (float2 *)(b + o_bc);
+    A.bc = (float4 *)(b + o_bc);
     d.bc = A.bc;
     d.spec = (float2 *)(b + o_spec);
     d.phi = (float *)(b + o_phi);

@@ -69,7 +69,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static pme_status upload_tables(pme_plan *pl) {
     const int *K = pl->K;
     const int H3 = K[2] / 2 + 1, Nh = K[2] / 2;
-    std::vector<float2> bc((size_t)K[0] * K[1] * H3);
+    std::vector<float4> bc((size_t)K[0] * K[1] * H3);
     make_influence(K, pl->p, pl->beta, pl->recip, pl->vol, bc.data());
     std::vector<float2> tw((size_t)K[0] + K[1] + Nh + Nh + 1);
     make_twiddles(K[0], K[0], tw.data());
@@ -78,7 +78,7 @@ static pme_status upload_tables(pme_plan *pl) {
     make_twiddles(K[2], Nh + 1, tw.data() + K[0] + K[1] + Nh);
     cudaError_t e;
     if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    if ((e = cudaMemcpy((void *)pl->d.bc, bc.data(), bc.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy((void *)pl->d.bc, bc.data(), bc.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(influence table)");
     if ((e = cudaMemcpy((void *)pl->d.tw1, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy(twiddles)");
@@ -92,7 +92,7 @@ static pme_status alloc_mesh(pme_plan *pl) {
     const size_t o_grid = off; off = align256(off + K1 * K2 * K3 * 8);
     const size_t o_spec = off; off = align256(off + K1 * K2 * H3 * 8);
     const size_t o_phi = off;  off = align256(off + K1 * K2 * K3 * 4);
-    const size_t o_bc = off;   off = align256(off + K1 * K2 * H3 * 8);
+    const size_t o_bc = off;   off = align256(off + K1 * K2 * H3 * sizeof(float4));
     const size_t o_tw = off;   off = align256(off + (K1 + K2 + Nh + Nh + 1) * 8);
     const size_t o_cnt = off;  off = align256(off + bcount_bytes_max(pl->K));
     const size_t o_par = off;  off = align256(off + partials_bytes(d));
@@ -107,7 +107,7 @@ static pme_status alloc_mesh(pme_plan *pl) {
     d.grid = (unsigned long long *)(b + o_grid);
     d.spec = (float2 *)(b + o_spec);
     d.phi = (float *)(b + o_phi);
-    d.bc = (const float2 *)(b + o_bc);
+    d.bc = (const float4 *)(b + o_bc);
     float2 *tw = (float2 *)(b + o_tw);
     d.tw1 = tw;
     d.tw2 = tw + K1;

@@ -16,6 +16,12 @@
 #include "common.cuh"
 #include "fft.cuh"
 
+// The register transforms (lane plans) need warps; the CPU emulation and builds that define
+// PME_NO_LANE_FFT keep only the shared-memory transforms.
+#if !defined(PME_HOST_EMULATION) && !defined(PME_NO_LANE_FFT)
+#define PME_LANE_FFT 1
+#endif
+
 namespace pme {
 
 // Tile region edge (mesh points) for spline order P and tile edge T: the tile plus the p - 1 points below.
@@ -35,9 +41,10 @@ inline size_t smem_tile_region(int p, int tlog) {
 }
 inline size_t smem_spread(int p, int tlog) { return smem_tile_region(p, tlog) * 2 * sizeof(int); }
 inline size_t smem_gather(int p, int tlog) { return smem_tile_region(p, tlog) * sizeof(float); }
+// Two K2 x H3 buffers (the register path uses one, with rows padded by up to 15), then the twiddles.
 inline size_t smem_slab(int K2, int K3) {
     const int H3 = K3 / 2 + 1;
-    return (2 * (size_t)K2 * H3 + (K3 / 2) + (K3 / 2 + 1) + K2) * sizeof(float2);
+    return (2 * (size_t)K2 * H3 + 16 * (size_t)K2 + (K3 / 2) + (K3 / 2 + 1) + K2) * sizeof(float2);
 }
 inline size_t smem_conv(int K1, int nth) {
     size_t fft = (2 * (size_t)K1 * CONV_COLS + K1) * sizeof(float2);
@@ -71,9 +78,16 @@ PME_DEV void copy_batched(T *dst, const T *src, int n) {
 // deterministic function of the float v, used identically by the shared-memory and the global paths, so
 // the mesh does not depend on which path an atom takes.
 
-PME_DEV void fix_split(float v, int &h, unsigned &l) {
-    h = f2i_rd(v * 9.5367431640625e-07f);  // floor(v / 2^20)
-    l = (unsigned)f2i_rn(fmaf(-(float)h, 1048576.0f, v));
+PME_DEV void fix_split(float v, int &h, int &l) {
+    // Round-to-nearest by the float magic number M = 1.5 * 2^23: for |x| < 2^22, x + M carries
+    // rn(x) in its low mantissa bits, so no float-to-integer conversion instruction is needed.
+    // h = rn(v / 2^20) (v / 2^20 is exact), l = rn(v - h 2^20) with v - h 2^20 in [-2^19, 2^19] exact;
+    // h 2^20 + l = rn(v), the same integer whatever the split.
+    const float M = 12582912.0f;
+    const float t = fmaf(v, 9.5367431640625e-07f, M);
+    h = float_bits(t) - 0x4B400000;
+    const float r = fmaf(-(t - M), 1048576.0f, v);
+    l = float_bits(r + M) - 0x4B400000;
 }
 PME_DEV unsigned long long fix_join(long long h, long long l) { return (unsigned long long)(h * 1048576ll + l); }
 
@@ -195,10 +209,8 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
             unsigned long long *row = d.grid + ((size_t)k1 * d.K2 + k2) * d.K3;
 #pragma unroll
             for (int j3 = 0; j3 < P; ++j3) {
-                int h;
-                unsigned l;
-                fix_split(c * th3[j3] * FIX_SCALE, h, l);
-                red_add_u64(row + wrapk(b3 - j3, d.K3), fix_join(h, l));
+                // rn(v) directly in 64 bits: the same integer as the tile path's split, for any |q| < 2^22
+                red_add_u64(row + wrapk(b3 - j3, d.K3), (unsigned long long)f2ll_rn(c * th3[j3] * FIX_SCALE));
             }
         }
     }
@@ -217,12 +229,12 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
     }
     constexpr int R = Region<P, T>::R, VOL = Region<P, T>::VOL, H = P - 1;
     int *hi = (int *)smem;
-    unsigned *lo = (unsigned *)(hi + VOL);
+    int *lo = hi + VOL;
     int o1, o2, o3;
     tile_origin(d, item, o1, o2, o3);
     for (int i = tid; i < VOL; i += nth) {
         hi[i] = 0;
-        lo[i] = 0u;
+        lo[i] = 0;
     }
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
     PME_SYNC();
@@ -251,20 +263,18 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
                 const int row = ((l1 - j1) * R + (l2 - j2)) * R + l3;
 #pragma unroll
                 for (int j3 = 0; j3 < P; ++j3) {
-                    int h;
-                    unsigned l;
+                    int h, l;
                     fix_split(c * th3[j3] * FIX_SCALE, h, l);
                     atomic_add_i32(hi + row - j3, h);
-                    atomic_add_u32_nr(lo + row - j3, l);
+                    atomic_add_i32(lo + row - j3, l);
                 }
             }
         }
     }
     PME_SYNC();
     for (int i = tid; i < VOL; i += nth) {
-        const int h = hi[i];
-        const unsigned l = lo[i];
-        if ((h | (int)l) == 0) continue;
+        const int h = hi[i], l = lo[i];
+        if ((h | l) == 0) continue;
         const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
         const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
         red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
@@ -273,10 +283,10 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
 
 // ---------------------------------------------------------------------------------------------------------
 // a3: forward slab k1 — mesh int64 -> float, real-to-complex FFT along k3 (a length K3/2 complex FFT of
-// even/odd pairs plus the split step), then the complex FFT along k2 for every m3 column. The slab of
-// the int64 mesh is zeroed after it is read, ready for the next evaluation's spreading.
+// even/odd pairs plus the split step), then the complex FFT along k2 for every m3 column. (The inverse
+// stage zeroes the slab of the int64 mesh for the next evaluation's spreading.)
 
-PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
+PME_DEV void stage_fwd_smem(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     const int K2 = d.K2, K3 = d.K3, H3 = d.H3, Nh = K3 / 2;
     const float inv_h3 = 1.0f / (float)H3;
@@ -285,7 +295,7 @@ PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
     float2 *twh = B + K2 * H3;   // Nh
     float2 *tw3 = twh + Nh;      // Nh + 1
     float2 *tw2 = tw3 + Nh + 1;  // K2
-    ulonglong2 *g = (ulonglong2 *)(d.grid + (size_t)k1 * K2 * K3);
+    const ulonglong2 *g = (const ulonglong2 *)(d.grid + (size_t)k1 * K2 * K3);
     const int tot = K2 * Nh;
     for (int base = tid; base < tot; base += LOAD_BATCH * nth) {  // row k2 pairs (2n, 2n+1) -> complex z[n]
         ulonglong2 v[LOAD_BATCH];
@@ -297,14 +307,12 @@ PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
             const int i = base + u * nth;
             if (i < tot) {
                 A[i] = make_float2(fix_to_float((long long)v[u].x), fix_to_float((long long)v[u].y));
-                g[i] = make_ulonglong2(0ull, 0ull);
             }
         }
     }
     for (int i = tid; i < Nh; i += nth) twh[i] = d.tw3h[i];
     for (int i = tid; i <= Nh; i += nth) tw3[i] = d.tw3[i];
     for (int i = tid; i < K2; i += nth) tw2[i] = d.tw2[i];
-    if (k1 == 0 && tid == 0) d.ctl->novf = 0u;  // spreading (its last reader) has finished
     PME_SYNC();
     float2 *Z = fft_batch<false>(A, B, Nh, K2, 1, Nh, twh);  // rows, stride Nh
     float2 *X = (Z == A) ? B : A;
@@ -333,20 +341,10 @@ PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
 // partner (weight 2), m3 = 0 and K3/2 have weight 1. Per-thread sums are double-float (about 44 bits);
 // per-item partials are FP64, and the last item reduces all partials in a fixed order.
 
-// Virial weight W_ab = delta_ab - 2 (1 + pi^2 |m'|^2 / beta^2) m'_a m'_b / |m'|^2 for the signed
-// frequency (mt1, mt2, mt3), m' = sum_alpha mt_alpha a*_alpha. Order xx yy zz xy xz yz.
-PME_DEV void virial_weights(const SysDev &d, float mt1, float mt2, float mt3, float W[6]) {
-    float mv[3];
+// m' = sum_alpha mt_alpha a*_alpha for the signed frequency (mt1, mt2, mt3).
+PME_DEV void recip_vec(const SysDev &d, float mt1, float mt2, float mt3, float mv[3]) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) mv[j] = mt1 * d.rec[3 * j] + mt2 * d.rec[3 * j + 1] + mt3 * d.rec[3 * j + 2];
-    const float m2n = mv[0] * mv[0] + mv[1] * mv[1] + mv[2] * mv[2];
-    const float f = 2.0f * (1.0f / m2n + d.pi2b2);
-    W[0] = 1.0f - f * mv[0] * mv[0];
-    W[1] = 1.0f - f * mv[1] * mv[1];
-    W[2] = 1.0f - f * mv[2] * mv[2];
-    W[3] = -f * mv[0] * mv[1];
-    W[4] = -f * mv[0] * mv[2];
-    W[5] = -f * mv[1] * mv[2];
 }
 
 // signed frequency of index m on a K-point axis: m for m <= K/2, else m - K (K/2 maps to +K/2)
@@ -367,7 +365,54 @@ __device__ __forceinline__ DF warp_sum_df(DF v) {
 }
 #endif
 
-PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
+// One point m of the half spectrum: energy and virial terms of B*C |Q^(m)|^2 added to acc (E, then
+// Pi xx yy zz xy xz yz), and the point multiplied by B*C. t is the point's influence-table entry (see
+// SysDev::bc). With e = w B C |Q^|^2 (w = 1/2 on the self-conjugate planes m3 = 0, K3/2, else 1, the point
+// standing for itself and its partner) the virial term is e (delta_ab - f m'_a m'_b), f = 2 (1 / |m'|^2 +
+// pi^2 / beta^2), the table holding B*C f; on Nyquist planes the partner's m'_p differs from -m' and the
+// term averages the two. m = 0 gives zero.
+PME_DEV float2 influence_point(const SysDev &d, int m1, int m2, int m3, int mt2, float2 x, float4 t, float acc[7]) {
+    if ((m1 | m2 | m3) == 0) return make_float2(0.f, 0.f);
+    const bool self = (m3 == 0 || 2 * m3 == d.K3);
+    const float wgt = self ? 0.5f : 1.0f;
+    const float s2 = x.x * x.x + x.y * x.y;
+    const float e = wgt * fmaf(t.x, s2, t.y * s2);
+    const int mt1 = signed_freq(m1, d.K1);
+    float mv[3];
+    recip_vec(d, (float)mt1, (float)mt2, (float)m3, mv);
+    const bool pair = t.w != 0.f;  // Nyquist plane: average with the partner
+    const float G = (pair ? 0.5f : 1.0f) * wgt * s2 * t.z;
+    float V[6];
+    V[0] = G * mv[0] * mv[0];
+    V[1] = G * mv[1] * mv[1];
+    V[2] = G * mv[2] * mv[2];
+    V[3] = G * mv[0] * mv[1];
+    V[4] = G * mv[0] * mv[2];
+    V[5] = G * mv[1] * mv[2];
+    if (pair) {
+        float mp[3];
+        recip_vec(d, (float)(2 * m1 == d.K1 ? mt1 : -mt1), (float)(2 * m2 == d.K2 ? mt2 : -mt2), (float)(-m3), mp);
+        const float Gp = 0.5f * wgt * s2 * t.w;
+        V[0] = fmaf(Gp * mp[0], mp[0], V[0]);
+        V[1] = fmaf(Gp * mp[1], mp[1], V[1]);
+        V[2] = fmaf(Gp * mp[2], mp[2], V[2]);
+        V[3] = fmaf(Gp * mp[0], mp[1], V[3]);
+        V[4] = fmaf(Gp * mp[0], mp[2], V[4]);
+        V[5] = fmaf(Gp * mp[1], mp[2], V[5]);
+    }
+    acc[0] += e;
+    acc[1] += e - V[0];
+    acc[2] += e - V[1];
+    acc[3] += e - V[2];
+    acc[4] -= V[3];
+    acc[5] -= V[4];
+    acc[6] -= V[5];
+    x.x *= t.x;
+    x.y *= t.x;
+    return x;
+}
+
+PME_DEV void stage_conv_smem(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
     const int K1 = d.K1, K2 = d.K2, K3 = d.K3, H3 = d.H3;
     const int m2 = item / d.nchunk3;
@@ -397,36 +442,11 @@ PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
     float acc[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) acc[c] = 0.f;
-    const float2 *bc = d.bc + (size_t)m2 * K1 * H3 + c0;
+    const float4 *bc = d.bc + (size_t)m2 * K1 * H3 + c0;
     const int mt2 = signed_freq(m2, K2);
     for (int i = tid; i < K1 * C; i += nth) {
         const int m1 = fdiv(i, inv_c), mc = i - m1 * C, m3 = c0 + mc;
-        const float2 t = bc[(size_t)m1 * H3 + mc];  // B*C as hi + lo
-        float2 x = X[i];
-        if ((m1 | m2 | m3) != 0) {
-            const bool self = (m3 == 0 || 2 * m3 == K3);  // conjugate partner is another point of this plane
-            const float s2 = x.x * x.x + x.y * x.y;
-            const float e = (self ? 0.5f : 1.0f) * fmaf(t.x, s2, t.y * s2);
-            const int mt1 = signed_freq(m1, K1);
-            float W[6];
-            virial_weights(d, (float)mt1, (float)mt2, (float)m3, W);
-            if (!self && (2 * m1 == K1 || 2 * m2 == K2)) {
-                // the partner -m keeps +K/2 on a Nyquist axis, so its m' is not -m': average the two
-                float Wp[6];
-                virial_weights(d, (float)(2 * m1 == K1 ? mt1 : -mt1), (float)(2 * m2 == K2 ? mt2 : -mt2),
-                               (float)(-m3), Wp);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) W[c] = 0.5f * (W[c] + Wp[c]);
-            }
-            acc[0] += e;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc[1 + c] = fmaf(e, W[c], acc[1 + c]);
-            x.x *= t.x;
-            x.y *= t.x;
-        } else {
-            x = make_float2(0.f, 0.f);
-        }
-        X[i] = x;
+        X[i] = influence_point(d, m1, m2, m3, mt2, X[i], bc[(size_t)m1 * H3 + mc], acc);
     }
     PME_SYNC();
     float2 *Y = fft_batch<true>(X, (X == A) ? B : A, K1, C, C, 1, tw1);
@@ -532,9 +552,8 @@ PME_DEV void reduce_level2(const SysDev &d, void *smem) {
 // a5: inverse slab k1 — inverse FFT along k2 per m3 column, then the complex-to-real inverse along k3
 // (merge step + a length K3/2 complex FFT whose real / imaginary parts are the even / odd samples).
 
-PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
+PME_DEV void stage_inv_smem(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
-    reduce_level1(d, k1);  // every influence item has finished
     const int K2 = d.K2, K3 = d.K3, H3 = d.H3, Nh = K3 / 2;
     const float inv_nh = 1.0f / (float)Nh;
     float2 *A = (float2 *)smem;
@@ -563,6 +582,324 @@ PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
     float2 *R = fft_batch<true>(Z, Y, Nh, K2, 1, Nh, twh);
     float2 *out = (float2 *)(d.phi + (size_t)k1 * K2 * K3);  // (phi[2n], phi[2n+1]) = (Re, Im) of R[n]
     for (int i = tid; i < K2 * Nh; i += nth) out[i] = R[i];
+}
+
+#if defined(PME_LANE_FFT)
+// ---------------------------------------------------------------------------------------------------------
+// Register path of a3 - a5 (lane plans, fft.cuh): each transform runs in the registers of L lanes of one
+// warp, reading its points straight from global memory (or from the slab buffer in shared memory) and
+// writing its results straight to their destination. A slab stage has one CTA barrier (between its two
+// transform directions), the influence stage none before its energy reduction. Thread counts must be
+// multiples of 32; every warp runs whole loop iterations, and lanes past the end work on a valid dummy
+// transform without storing, so the shuffles always see full warps.
+
+// Unit u -> (transform t, lane j): warp u / 32 holds T = 32 / L transforms at lane ids t mod T + T j.
+template <int L>
+PME_DEV void lane_unit(int u, int &t, int &j) {
+    constexpr int T = 32 / L;
+    const int lid = u & 31;
+    t = (u >> 5) * T + (lid & (T - 1));
+    j = lid / T;
+}
+
+// Units covering ntr transforms of L lanes: whole warps.
+template <int L>
+PME_DEV int lane_units(int ntr) {
+    constexpr int T = 32 / L;
+    return ((ntr + T - 1) / T) * 32;
+}
+
+// a3 rows: the packed real row k2 (z[n] = Q[2n] + i Q[2n+1], K3/2 = L E points) from the int64 mesh; the
+// K3/2-point transform goes to row k2 of Z (row stride zs).
+template <int L, int E>
+PME_DEV void fwd_rows_lane(const SysDev &d, int k1, float2 *Z, int zs) {
+    const int K2 = d.K2, total = lane_units<L>(K2);
+    for (int u = PME_TID; u < total; u += PME_NTH) {
+        int t, j;
+        lane_unit<L>(u, t, j);
+        const bool ok = t < K2;
+        const ulonglong2 *g = (const ulonglong2 *)(d.grid + ((size_t)k1 * K2 + (ok ? t : 0)) * d.K3);
+        ulonglong2 w[E];
+#pragma unroll
+        for (int n = 0; n < E; ++n) w[n] = ldcg(g + j + L * n);
+        const LaneTw<L, E> tw = lane_tw<L, E, true>(d.tw3h, j);
+        float2 v[E];
+#pragma unroll
+        for (int n = 0; n < E; ++n) v[n] = make_float2(fix_to_float((long long)w[n].x), fix_to_float((long long)w[n].y));
+        lane_fft<L, E, false>(v, j, tw);
+        if (ok) {
+            const int r = lane_rev<L>(j);
+#pragma unroll
+            for (int k = 0; k < E; ++k) Z[t * zs + k + E * r] = v[k];
+        }
+    }
+}
+
+// a3 columns: the split X[m] = E[m] + W_K3^m O[m] of row transforms Z (E, O as in the shared-memory path)
+// fused into the loads of column m3, then the K2-point transform along k2 into the half spectrum. tw3
+// (K3/2 + 1 entries) and tw2 (K2 entries) are shared-memory copies.
+template <int L, int E>
+PME_DEV void fwd_cols_lane(const SysDev &d, int k1, const float2 *Z, int zs, const float2 *tw3, const float2 *tw2) {
+    const int K2 = d.K2, H3 = d.H3, Nh = d.K3 / 2, total = lane_units<L>(H3);
+    float2 *out = d.spec + (size_t)k1 * K2 * H3;
+    for (int u = PME_TID; u < total; u += PME_NTH) {
+        int m, j;
+        lane_unit<L>(u, m, j);
+        const bool ok = m < H3;
+        const int mm = ok ? m : 0;
+        const LaneTw<L, E> tw = lane_tw<L, E, false>(tw2, j);
+        const float2 w3 = tw3[mm];
+        const int ia = mm == Nh ? 0 : mm, ib = mm == 0 ? 0 : Nh - mm;
+        float2 v[E];
+#pragma unroll
+        for (int n = 0; n < E; ++n) {
+            const float2 *z = Z + (j + L * n) * zs;
+            const float2 zm = z[ia], zc = cconj(z[ib]);
+            const float2 Ev = cscale(cadd(zm, zc), 0.5f);
+            const float2 Ov = cscale(cmul_mi<false>(csub(zm, zc)), 0.5f);
+            v[n] = cadd(Ev, cmul(w3, Ov));
+        }
+        lane_fft<L, E, false>(v, j, tw);
+        if (ok) {
+            const int r = lane_rev<L>(j);
+#pragma unroll
+            for (int k = 0; k < E; ++k) out[(size_t)(k + E * r) * H3 + m] = v[k];
+        }
+    }
+}
+
+// a5 columns: inverse K2-point transforms of column m3 of the half spectrum into Y (row stride ys).
+template <int L, int E>
+PME_DEV void inv_cols_lane(const SysDev &d, int k1, float2 *Y, int ys) {
+    const int K2 = d.K2, H3 = d.H3, total = lane_units<L>(H3);
+    const float2 *in = d.spec + (size_t)k1 * K2 * H3;
+    for (int u = PME_TID; u < total; u += PME_NTH) {
+        int m, j;
+        lane_unit<L>(u, m, j);
+        const bool ok = m < H3;
+        const int mm = ok ? m : 0;
+        float2 v[E];
+#pragma unroll
+        for (int n = 0; n < E; ++n) v[n] = ldcg(in + (size_t)(j + L * n) * H3 + mm);
+        const LaneTw<L, E> tw = lane_tw<L, E, true>(d.tw2, j);
+        lane_fft<L, E, true>(v, j, tw);
+        if (ok) {
+            const int r = lane_rev<L>(j);
+#pragma unroll
+            for (int k = 0; k < E; ++k) Y[(k + E * r) * ys + m] = v[k];
+        }
+    }
+}
+
+// a5 rows: the merge Z[m] = (X[m] + conj X[Nh-m]) + i (X[m] - conj X[Nh-m]) exp(+2 pi i m / K3) fused into
+// the loads, then the inverse K3/2-point transform, whose real / imaginary parts are phi at even / odd k3.
+// twh (K3/2 entries) and tw3 (K3/2 + 1) are shared-memory copies.
+template <int L, int E>
+PME_DEV void inv_rows_lane(const SysDev &d, int k1, const float2 *Y, int ys, const float2 *twh, const float2 *tw3) {
+    const int K2 = d.K2, Nh = d.K3 / 2, total = lane_units<L>(K2);
+    float2 *out = (float2 *)(d.phi + (size_t)k1 * K2 * d.K3);
+    for (int u = PME_TID; u < total; u += PME_NTH) {
+        int t, j;
+        lane_unit<L>(u, t, j);
+        const bool ok = t < K2;
+        const float2 *x = Y + (ok ? t : 0) * ys;
+        const LaneTw<L, E> tw = lane_tw<L, E, false>(twh, j);
+        float2 v[E];
+#pragma unroll
+        for (int n = 0; n < E; ++n) {
+            const int m = j + L * n;
+            const float2 xm = x[m], xc = cconj(x[Nh - m]);
+            const float2 a = cadd(xm, xc);
+            const float2 b = cmul(csub(xm, xc), cconj(tw3[m]));
+            v[n] = make_float2(a.x - b.y, a.y + b.x);
+        }
+        lane_fft<L, E, true>(v, j, tw);
+        if (ok) {
+            const int r = lane_rev<L>(j);
+            float2 *o = out + (size_t)t * Nh;
+#pragma unroll
+            for (int k = 0; k < E; ++k) o[k + E * r] = v[k];
+        }
+    }
+}
+
+// a4 / a7 register path: work item = CONV_UNITS / L consecutive columns (m2, m3) of the half spectrum
+// (flattened m2 H3 + m3). Each column: forward K1-point transform, B*C product with the energy and virial
+// terms (influence_point), adjoint transform back in place. The item's energy / virial partial is a
+// fixed-order double-float tree over its CONV_UNITS lanes, one component per warp, independent of the block
+// size.
+template <int L, int E>
+PME_DEV void conv_lane(const SysDev &d, int item, void *smem) {
+    constexpr int COLS = CONV_UNITS / L;
+    const int tid = PME_TID, nth = PME_NTH;
+    const int K1 = d.K1, K2 = d.K2, H3 = d.H3, ncol = K2 * H3;
+    const float inv_h3 = 1.0f / (float)H3;
+    float *red = (float *)smem;  // 7 x CONV_UNITS
+    for (int u = tid; u < CONV_UNITS; u += nth) {
+        int t, j;
+        lane_unit<L>(u, t, j);
+        const int col = item * COLS + t;
+        const bool ok = col < ncol;
+        const int cc = ok ? col : 0;
+        const int m2 = fdiv(cc, inv_h3), m3 = cc - m2 * H3;
+        const int r = lane_rev<L>(j);
+        float2 v[E];
+        float4 bcv[E];
+#pragma unroll
+        for (int n = 0; n < E; ++n) v[n] = ldcg(d.spec + ((size_t)(j + L * n) * K2 + m2) * H3 + m3);
+#pragma unroll
+        for (int k = 0; k < E; ++k) bcv[k] = ldcg(d.bc + ((size_t)m2 * K1 + k + E * r) * H3 + m3);
+        const LaneTw<L, E> tw = lane_tw<L, E, true>(d.tw1, j);
+        lane_fft<L, E, false>(v, j, tw);
+        float acc[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[c] = 0.f;
+        const int mt2 = signed_freq(m2, K2);
+#pragma unroll
+        for (int k = 0; k < E; ++k) v[k] = influence_point(d, k + E * r, m2, m3, mt2, v[k], bcv[k], acc);
+        lane_fft_adjoint<L, E>(v, j, tw);
+        if (ok) {
+#pragma unroll
+            for (int n = 0; n < E; ++n) d.spec[((size_t)(j + L * n) * K2 + m2) * H3 + m3] = v[n];
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) red[c * CONV_UNITS + u] = ok ? acc[c] : 0.f;
+    }
+    PME_SYNC();
+    // component c by warp c mod 4: each lane adds units lane, lane + 32, ... in double-float, then a
+    // shuffle tree over the warp (lane 0 holds the fixed-order result)
+    DF *part = (DF *)d.partials;
+    const int nw = nth >> 5, w = tid >> 5, lane = tid & 31;
+    for (int c = w; c < 7; c += nw) {
+        DF sum;
+        sum.hi = red[c * CONV_UNITS + lane];
+        sum.lo = 0.f;
+        for (int t = lane + 32; t < CONV_UNITS; t += 32) sum = df_add(sum, red[c * CONV_UNITS + t]);
+        sum = warp_sum_df(sum);
+        if (lane == 0) part[(size_t)item * 8 + c] = sum;
+    }
+}
+
+// Lanes of plan c (PME_LANE_CASES).
+PME_DEV int plan_lanes(int c) {
+    switch (c) {
+#define PME_PL(c, L, E) \
+    case c: return L;
+        PME_LANE_CASES(PME_PL)
+#undef PME_PL
+    }
+    return 1;
+}
+
+// Row strides (>= w) of the slab buffers, chosen so that the 16 lanes of a half-warp of the reading pass
+// (T = 32 / L transforms x 16 / T lanes, float2 = two banks) fall on distinct shared-memory banks.
+// Column reader (transform = column, lane j steps rows): stride = min(T, 16) mod 16.
+PME_DEV int stride_col_reader(int w, int c) {
+    const int L = plan_lanes(c);
+    if (L <= 2) return w;  // a half-warp reads 16 consecutive columns of one row
+    return w + ((32 / L - w) & 15);
+}
+// Row reader (transform = row, lane j steps along the row): stride = max(L / 2, 1) mod 16.
+PME_DEV int stride_row_reader(int w, int c) {
+    const int L = plan_lanes(c);
+    if (L >= 32) return w;  // a half-warp reads 16 consecutive points of one row
+    return w + (((L >= 2 ? L / 2 : 1) - w) & 15);
+}
+
+PME_DEV void stage_fwd_lane(const SysDev &d, int k1, void *smem) {
+    const int Nh = d.K3 / 2, zs = stride_col_reader(Nh, d.lp_cols);
+    float2 *Z = (float2 *)smem;
+    float2 *tw3 = Z + d.K2 * zs;  // Nh + 1
+    float2 *tw2 = tw3 + Nh + 1;   // K2
+    for (int i = PME_TID; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
+    for (int i = PME_TID; i < d.K2; i += PME_NTH) tw2[i] = d.tw2[i];
+    switch (d.lp_rows) {
+#define PME_ROWS(c, L, E) \
+    case c: fwd_rows_lane<L, E>(d, k1, Z, zs); break;
+        PME_LANE_CASES(PME_ROWS)
+#undef PME_ROWS
+    }
+    PME_SYNC();
+    switch (d.lp_cols) {
+#define PME_COLS(c, L, E) \
+    case c: fwd_cols_lane<L, E>(d, k1, Z, zs, tw3, tw2); break;
+        PME_LANE_CASES(PME_COLS)
+#undef PME_COLS
+    }
+}
+
+PME_DEV void stage_inv_lane(const SysDev &d, int k1, void *smem) {
+    const int Nh = d.K3 / 2, ys = stride_row_reader(d.H3, d.lp_rows);
+    float2 *Y = (float2 *)smem;
+    float2 *twh = Y + d.K2 * ys;  // Nh
+    float2 *tw3 = twh + Nh;       // Nh + 1
+    for (int i = PME_TID; i < Nh; i += PME_NTH) twh[i] = d.tw3h[i];
+    for (int i = PME_TID; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
+    switch (d.lp_cols) {
+#define PME_COLS(c, L, E) \
+    case c: inv_cols_lane<L, E>(d, k1, Y, ys); break;
+        PME_LANE_CASES(PME_COLS)
+#undef PME_COLS
+    }
+    PME_SYNC();
+    switch (d.lp_rows) {
+#define PME_ROWS(c, L, E) \
+    case c: inv_rows_lane<L, E>(d, k1, Y, ys, twh, tw3); break;
+        PME_LANE_CASES(PME_ROWS)
+#undef PME_ROWS
+    }
+}
+
+PME_DEV void stage_conv_lane(const SysDev &d, int item, void *smem) {
+    switch (d.lp_k1) {
+#define PME_K1(c, L, E) \
+    case c: conv_lane<L, E>(d, item, smem); break;
+        PME_LANE_CASES(PME_K1)
+#undef PME_K1
+    }
+}
+#endif  // PME_LANE_FFT
+
+// Stage entry points: the register path where the plan has lane plans, else the shared-memory path.
+PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
+    if (k1 == 0 && PME_TID == 0) d.ctl->novf = 0u;  // spreading (its last reader) has finished
+#if defined(PME_LANE_FFT)
+    if (d.lane_slab) {
+        stage_fwd_lane(d, k1, smem);
+        return;
+    }
+#endif
+    stage_fwd_smem(d, k1, smem);
+}
+
+PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
+#if defined(PME_LANE_FFT)
+    if (d.lane_conv) {
+        stage_conv_lane(d, item, smem);
+        return;
+    }
+#endif
+    stage_conv_smem(d, item, smem);
+}
+
+// Plane k1 of the int64 charge mesh back to zero for the next spreading (its reader, the forward stage,
+// finished before the influence stage started); the stores overlap the inverse stage's own work.
+PME_DEV void zero_mesh_plane(const SysDev &d, int k1) {
+    ulonglong2 *g = (ulonglong2 *)(d.grid + (size_t)k1 * d.K2 * d.K3);
+    const int tot = d.K2 * d.K3 / 2;
+    for (int i = PME_TID; i < tot; i += PME_NTH) g[i] = make_ulonglong2(0ull, 0ull);
+}
+
+PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
+    zero_mesh_plane(d, k1);
+    reduce_level1(d, k1);  // every influence item has finished
+#if defined(PME_LANE_FFT)
+    if (d.lane_slab) {
+        stage_inv_lane(d, k1, smem);
+        return;
+    }
+#endif
+    stage_inv_smem(d, k1, smem);
 }
 
 // ---------------------------------------------------------------------------------------------------------

@@ -20,7 +20,8 @@ using namespace pme;
 struct EmuState {
     SysDev d;
     std::vector<unsigned long long> grid;
-    std::vector<float2> spec, bc, tw;
+    std::vector<float2> spec, tw;
+    std::vector<float4> bc;
     std::vector<float> phi;
     std::vector<unsigned> bcount;
     std::vector<double> partials;
