@@ -43,7 +43,7 @@ constexpr float FIX_INV = 9.094947017729282379150390625e-13f;  // 2^-40
 // bounds every mesh value and every partial sum, so larger totals are refused.
 constexpr float QABS_SCALE = 16777216.0f;                // 2^24
 constexpr unsigned long long QABS_LIMIT = 1ull << 46;    // 2^22 e in 2^24 units
-constexpr int BIN_PER_THREAD = 4;           // atoms per thread in the binning stage (for memory-level parallelism)
+constexpr int BIN_PER_THREAD = 1;           // atoms per thread per pass of the binning stage
 constexpr int BIN_CHUNK = 128 * BIN_PER_THREAD;  // atoms per binning work item
 constexpr int OVF_ITEMS = 8;     // extra spread / gather work items that handle bucket-overflow atoms
 constexpr int MAX_K = 128;

@@ -167,13 +167,17 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
         }
     }
     if (bad) atomic_or_u32(&d.ctl->status, bad);
-    // warp sums of |q| in fixed point (exact, so the order of the atomics does not matter)
+    // sum of |q| in fixed point (exact, so the order of the additions does not matter): warp sums, then
+    // one atomic per CTA
     qacc = warp_sum_u64(qacc);
-    if ((tid & 31) == 0 && qacc) {
-        if (qacc >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
-        else atomic_add_u64(&d.ctl->qabs, qacc);
+    if ((tid & 31) == 0) red[tid >> 5] = qacc;
+    PME_SYNC();
+    if (tid == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < (nth + 31) / 32; ++w) tot += red[w];
+        if (tot >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+        else if (tot) atomic_add_u64(&d.ctl->qabs, tot);
     }
-    (void)red;
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -414,7 +418,7 @@ PME_DEV float2 influence_point(const SysDev &d, int m1, int m2, int m3, int mt2,
 
 PME_DEV void stage_conv_smem(const SysDev &d, int item, void *smem) {
     const int tid = PME_TID, nth = PME_NTH;
-    const int K1 = d.K1, K2 = d.K2, K3 = d.K3, H3 = d.H3;
+    const int K1 = d.K1, K2 = d.K2, H3 = d.H3;
     const int m2 = item / d.nchunk3;
     const int c0 = (item - m2 * d.nchunk3) * CONV_COLS;
     const int C = imin(CONV_COLS, H3 - c0);
@@ -483,8 +487,7 @@ PME_DEV void stage_conv_smem(const SysDev &d, int item, void *smem) {
 // slab item k1): the influence-stage item partials k1, k1 + K1, k1 + 2 K1, ... in order -> slot k1. Level 2
 // (the first overflow item of the force stage, otherwise idle when no bucket overflowed): the K1 slots in a
 // fixed binary tree -> FP64 energy and virial. Neither order depends on the block size.
-PME_DEV void reduce_level1(const SysDev &d, int k1) {
-    const int tid = PME_TID, nth = PME_NTH;
+PME_DEV void reduce_level1(const SysDev &d, int k1, int tid, int nth) {
     const DF *part = (const DF *)d.partials;
     DF *slot = (DF *)d.partials + (size_t)d.nconv * 8;  // K1 level-1 slots of 8 after the item partials
     for (int c = tid; c < 7; c += nth) {
@@ -508,6 +511,23 @@ PME_DEV void reduce_level1(const SysDev &d, int k1) {
         }
         slot[(size_t)k1 * 8 + c] = s;
     }
+}
+
+// Plane k1 of the int64 charge mesh back to zero for the next spreading (its reader, the forward stage,
+// finished before the influence stage started); the stores overlap the inverse stage's own work.
+PME_DEV void zero_mesh_plane(const SysDev &d, int k1, int tid, int nth) {
+    ulonglong2 *g = (ulonglong2 *)(d.grid + (size_t)k1 * d.K2 * d.K3);
+    const int tot = d.K2 * d.K3 / 2;
+    for (int i = tid; i < tot; i += nth) g[i] = make_ulonglong2(0ull, 0ull);
+}
+
+// Side work of inverse slab k1, off the transforms' critical path: zero the mesh plane and run the level-1
+// energy / virial reduction (every influence item has finished), on threads [t0, t0 + nt).
+PME_DEV void inv_side_work(const SysDev &d, int k1, int t0, int nt) {
+    const int t = PME_TID - t0;
+    if (t < 0 || t >= nt) return;
+    reduce_level1(d, k1, t, nt);
+    zero_mesh_plane(d, k1, t, nt);
 }
 
 PME_DEV void reduce_level2(const SysDev &d, void *smem) {
@@ -770,15 +790,27 @@ PME_DEV void conv_lane(const SysDev &d, int item, void *smem) {
     // shuffle tree over the warp (lane 0 holds the fixed-order result)
     DF *part = (DF *)d.partials;
     const int nw = nth >> 5, w = tid >> 5, lane = tid & 31;
-    for (int c = w; c < 7; c += nw) {
-        DF sum;
-        sum.hi = red[c * CONV_UNITS + lane];
-        sum.lo = 0.f;
-        for (int t = lane + 32; t < CONV_UNITS; t += 32) sum = df_add(sum, red[c * CONV_UNITS + t]);
-        sum = warp_sum_df(sum);
-        if (lane == 0) part[(size_t)item * 8 + c] = sum;
+    for (int c0 = w; c0 < 7; c0 += 2 * nw) {  // components c0 and c0 + nw side by side
+        const int c1 = c0 + nw < 7 ? c0 + nw : c0;
+        DF s0, s1;
+        s0.hi = red[c0 * CONV_UNITS + lane];
+        s1.hi = red[c1 * CONV_UNITS + lane];
+        s0.lo = s1.lo = 0.f;
+        for (int t = lane + 32; t < CONV_UNITS; t += 32) {
+            s0 = df_add(s0, red[c0 * CONV_UNITS + t]);
+            s1 = df_add(s1, red[c1 * CONV_UNITS + t]);
+        }
+        s0 = warp_sum_df(s0);
+        s1 = warp_sum_df(s1);
+        if (lane == 0) {
+            part[(size_t)item * 8 + c0] = s0;
+            if (c1 != c0) part[(size_t)item * 8 + c1] = s1;
+        }
     }
 }
+
+// Threads (whole warps) a lane pass of plan c over ntr transforms occupies in its first iteration.
+PME_DEV int plan_col_units(int c, int ntr);
 
 // Lanes of plan c (PME_LANE_CASES).
 PME_DEV int plan_lanes(int c) {
@@ -789,6 +821,11 @@ PME_DEV int plan_lanes(int c) {
 #undef PME_PL
     }
     return 1;
+}
+
+PME_DEV int plan_col_units(int c, int ntr) {
+    const int T = 32 / plan_lanes(c);
+    return ((ntr + T - 1) / T) * 32;
 }
 
 // Row strides (>= w) of the slab buffers, chosen so that the 16 lanes of a half-warp of the reading pass
@@ -811,14 +848,21 @@ PME_DEV void stage_fwd_lane(const SysDev &d, int k1, void *smem) {
     float2 *Z = (float2 *)smem;
     float2 *tw3 = Z + d.K2 * zs;  // Nh + 1
     float2 *tw2 = tw3 + Nh + 1;   // K2
-    for (int i = PME_TID; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
-    for (int i = PME_TID; i < d.K2; i += PME_NTH) tw2[i] = d.tw2[i];
+    // the column pass's tables: loads issued before the row pass, stores after it, so their latency hides
+    // behind the row pass
+    const int tid = PME_TID;
+    const float2 a = tid <= Nh ? __ldg(d.tw3 + tid) : make_float2(0.f, 0.f);
+    const float2 b = tid < d.K2 ? __ldg(d.tw2 + tid) : make_float2(0.f, 0.f);
     switch (d.lp_rows) {
 #define PME_ROWS(c, L, E) \
     case c: fwd_rows_lane<L, E>(d, k1, Z, zs); break;
         PME_LANE_CASES(PME_ROWS)
 #undef PME_ROWS
     }
+    if (tid <= Nh) tw3[tid] = a;
+    if (tid < d.K2) tw2[tid] = b;
+    for (int i = tid + PME_NTH; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
+    for (int i = tid + PME_NTH; i < d.K2; i += PME_NTH) tw2[i] = d.tw2[i];
     PME_SYNC();
     switch (d.lp_cols) {
 #define PME_COLS(c, L, E) \
@@ -833,14 +877,24 @@ PME_DEV void stage_inv_lane(const SysDev &d, int k1, void *smem) {
     float2 *Y = (float2 *)smem;
     float2 *twh = Y + d.K2 * ys;  // Nh
     float2 *tw3 = twh + Nh;       // Nh + 1
-    for (int i = PME_TID; i < Nh; i += PME_NTH) twh[i] = d.tw3h[i];
-    for (int i = PME_TID; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
+    // the row pass's tables: loads issued first, stores after the column pass (latency hidden behind it)
+    const int tid = PME_TID;
+    const float2 a = tid < Nh ? __ldg(d.tw3h + tid) : make_float2(0.f, 0.f);
+    const float2 b = tid <= Nh ? __ldg(d.tw3 + tid) : make_float2(0.f, 0.f);
+    // the column pass needs cu threads; warps beyond them (if any) take the side work, else everyone first
+    const int cu = plan_col_units(d.lp_cols, d.H3);
+    if (PME_NTH - cu >= 32) inv_side_work(d, k1, cu, PME_NTH - cu);
+    else inv_side_work(d, k1, 0, PME_NTH);
     switch (d.lp_cols) {
 #define PME_COLS(c, L, E) \
     case c: inv_cols_lane<L, E>(d, k1, Y, ys); break;
         PME_LANE_CASES(PME_COLS)
 #undef PME_COLS
     }
+    if (tid < Nh) twh[tid] = a;
+    if (tid <= Nh) tw3[tid] = b;
+    for (int i = tid + PME_NTH; i < Nh; i += PME_NTH) twh[i] = d.tw3h[i];
+    for (int i = tid + PME_NTH; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
     PME_SYNC();
     switch (d.lp_rows) {
 #define PME_ROWS(c, L, E) \
@@ -882,23 +936,14 @@ PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
     stage_conv_smem(d, item, smem);
 }
 
-// Plane k1 of the int64 charge mesh back to zero for the next spreading (its reader, the forward stage,
-// finished before the influence stage started); the stores overlap the inverse stage's own work.
-PME_DEV void zero_mesh_plane(const SysDev &d, int k1) {
-    ulonglong2 *g = (ulonglong2 *)(d.grid + (size_t)k1 * d.K2 * d.K3);
-    const int tot = d.K2 * d.K3 / 2;
-    for (int i = PME_TID; i < tot; i += PME_NTH) g[i] = make_ulonglong2(0ull, 0ull);
-}
-
 PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
-    zero_mesh_plane(d, k1);
-    reduce_level1(d, k1);  // every influence item has finished
 #if defined(PME_LANE_FFT)
     if (d.lane_slab) {
         stage_inv_lane(d, k1, smem);
         return;
     }
 #endif
+    inv_side_work(d, k1, 0, PME_NTH);
     stage_inv_smem(d, k1, smem);
 }
 
