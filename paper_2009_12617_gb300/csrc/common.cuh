@@ -68,6 +68,44 @@ constexpr int LANE_PLANS = 21;
 constexpr int CONV_UNITS = 128;
 // Threads of a slab-stage CTA (the register path picks its lane plans to fill about this many).
 constexpr int SLAB_THREADS = 512;
+
+#if defined(PME_HOST_EMULATION)
+#define PME_HD constexpr inline
+#else
+#define PME_HD __host__ __device__ constexpr inline
+#endif
+
+// Lanes L and points per lane E of lane plan c.
+#define PME_PLAN_L(c_, L_, E_) c == c_ ? L_:
+#define PME_PLAN_E(c_, L_, E_) c == c_ ? E_:
+PME_HD int plan_L(int c) { return PME_LANE_CASES(PME_PLAN_L) 1; }
+PME_HD int plan_E(int c) { return PME_LANE_CASES(PME_PLAN_E) 1; }
+#undef PME_PLAN_L
+#undef PME_PLAN_E
+
+// Plan for ntr transforms of length N in one slab CTA: the fewest points per lane (the shortest serial
+// chain per thread) whose lanes still fit in SLAB_THREADS, else the plan with the fewest lanes; -1 when N
+// has no plan.
+PME_HD int slab_lane_plan(int N, int ntr) {
+    int best = -1, fewest = -1;
+    for (int c = 0; c < LANE_PLANS; ++c) {
+        const int L = plan_L(c), E = plan_E(c);
+        if (L * E != N) continue;
+        const int T = 32 / L, units = ((ntr + T - 1) / T) * 32;
+        if (units <= SLAB_THREADS && (best < 0 || E < plan_E(best))) best = c;
+        if (fewest < 0 || L < plan_L(fewest)) fewest = c;
+    }
+    return best >= 0 ? best : fewest;
+}
+
+// Plan of the influence stage's K1-point transforms: the fewest points per lane, so that the work spreads
+// over as many threads as possible.
+PME_HD int conv_lane_plan(int N) {
+    int best = -1;
+    for (int c = 0; c < LANE_PLANS; ++c)
+        if (plan_L(c) * plan_E(c) == N && (best < 0 || plan_E(c) < plan_E(best))) best = c;
+    return best;
+}
 // Independent global loads each thread keeps in flight when staging data into shared memory.
 constexpr int LOAD_BATCH = 8;
 // Slots of the fixed-order final energy / virial reduction (a power of two, >= MAX_K / 2).

@@ -89,49 +89,6 @@ inline int choose_tile_log(int64_t n, const int K[3]) {
     return TILE_MIN_LOG;
 }
 
-// Lane plans (PME_LANE_CASES): lanes L and points per lane E of plan c.
-inline int lane_plan_lanes(int c) {
-    static const int Ls[LANE_PLANS] = {
-#define PME_LANE_L(c, L, E) L,
-        PME_LANE_CASES(PME_LANE_L)
-#undef PME_LANE_L
-    };
-    return Ls[c];
-}
-inline int lane_plan_points(int c) {
-    static const int Es[LANE_PLANS] = {
-#define PME_LANE_E(c, L, E) E,
-        PME_LANE_CASES(PME_LANE_E)
-#undef PME_LANE_E
-    };
-    return Es[c];
-}
-
-// Plan for ntr transforms of length N in one slab CTA: the fewest points per lane (the shortest serial
-// chain per thread) whose lanes still fit in SLAB_THREADS, else the plan with the fewest lanes; -1 when N
-// has no plan.
-inline int slab_lane_plan(int N, int ntr) {
-    int best = -1, fewest = -1;
-    for (int c = 0; c < LANE_PLANS; ++c) {
-        const int L = lane_plan_lanes(c), E = lane_plan_points(c);
-        if (L * E != N) continue;
-        const int T = 32 / L, units = ((ntr + T - 1) / T) * 32;
-        if (units <= SLAB_THREADS && (best < 0 || E < lane_plan_points(best))) best = c;
-        if (fewest < 0 || L < lane_plan_lanes(fewest)) fewest = c;
-    }
-    return best >= 0 ? best : fewest;
-}
-
-// Plan of the influence stage's K1-point transforms: the fewest points per lane, so that the work spreads
-// over as many threads as possible.
-inline int conv_lane_plan(int N) {
-    int best = -1;
-    for (int c = 0; c < LANE_PLANS; ++c)
-        if (lane_plan_lanes(c) * lane_plan_points(c) == N && (best < 0 || lane_plan_points(c) < lane_plan_points(best)))
-            best = c;
-    return best;
-}
-
 // Transform paths: the register path (lane plans) wherever both transforms of a slab stage, or the K1
 // transform of the influence stage, have a plan; the shared-memory Stockham path otherwise. The CPU
 // emulation of the stage bodies (one thread per CTA) has no lanes and always takes the shared-memory path.
@@ -143,7 +100,7 @@ inline void choose_fft_paths(SysDev &d, bool lanes) {
     d.lane_conv = d.lp_k1 >= 0 ? 1 : 0;
     d.nchunk3 = (d.H3 + CONV_COLS - 1) / CONV_COLS;
     if (d.lane_conv) {
-        const int cols = CONV_UNITS / lane_plan_lanes(d.lp_k1);  // columns per work item
+        const int cols = CONV_UNITS / plan_L(d.lp_k1);  // columns per work item
         d.nconv = (d.K2 * d.H3 + cols - 1) / cols;
     } else {
         d.nconv = d.K2 * d.nchunk3;

@@ -60,6 +60,37 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
     stage_inv(d, blockIdx.x, smem);
 }
 
+// Slab and influence kernels specialised for the lane plans of cubic meshes K^3, K in PME_CUBIC_KS (the
+// shapes most systems use); each holds only its plans' code. Other meshes run the kernels above, which
+// choose among all plans at run time.
+#define PME_CUBIC_KS(X) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(128)
+template <int K>
+struct Cubic {
+    static constexpr int PR = slab_lane_plan(K / 2, K), PC = slab_lane_plan(K, K / 2 + 1), P1 = conv_lane_plan(K);
+    static_assert(PR >= 0 && PC >= 0 && P1 >= 0, "every listed cubic mesh has lane plans");
+};
+
+template <int PR, int PC>
+__global__ void __launch_bounds__(NT_SLAB) k_fwd_p(SysDev d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
+    stage_fwd<PR, PC>(d, blockIdx.x, smem);
+}
+
+template <int P1>
+__global__ void __launch_bounds__(NT_CONV) k_conv_p(SysDev d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
+    stage_conv<P1>(d, blockIdx.x, smem);
+}
+
+template <int PR, int PC>
+__global__ void __launch_bounds__(NT_SLAB) k_inv_p(SysDev d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late != 0);
+    stage_inv<PR, PC>(d, blockIdx.x, smem);
+}
+
 template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -99,7 +130,44 @@ cudaError_t configure_kernels() {
         cudaError_t e = set_smem_limit(f, big);
         if (e != cudaSuccess) return e;
     }
+#define PME_CFG_K(K)                                                                                        \
+    for (const void *f : {(const void *)k_fwd_p<Cubic<K>::PR, Cubic<K>::PC>, (const void *)k_conv_p<Cubic<K>::P1>, \
+                          (const void *)k_inv_p<Cubic<K>::PR, Cubic<K>::PC>}) {                               \
+        cudaError_t e = set_smem_limit(f, big);                                                             \
+        if (e != cudaSuccess) return e;                                                                     \
+    }
+    PME_CUBIC_KS(PME_CFG_K)
+#undef PME_CFG_K
     return cudaSuccess;
+}
+
+// The specialised kernel for the system's plans, or the general one.
+static void (*fwd_kernel(const SysDev &d))(SysDev) {
+    if (d.lane_slab) {
+#define PME_PICK(K) \
+    if (d.lp_rows == Cubic<K>::PR && d.lp_cols == Cubic<K>::PC) return k_fwd_p<Cubic<K>::PR, Cubic<K>::PC>;
+        PME_CUBIC_KS(PME_PICK)
+#undef PME_PICK
+    }
+    return k_fwd;
+}
+static void (*inv_kernel(const SysDev &d))(SysDev) {
+    if (d.lane_slab) {
+#define PME_PICK(K) \
+    if (d.lp_rows == Cubic<K>::PR && d.lp_cols == Cubic<K>::PC) return k_inv_p<Cubic<K>::PR, Cubic<K>::PC>;
+        PME_CUBIC_KS(PME_PICK)
+#undef PME_PICK
+    }
+    return k_inv;
+}
+static void (*conv_kernel(const SysDev &d))(SysDev) {
+    if (d.lane_conv) {
+#define PME_PICK(K) \
+    if (d.lp_k1 == Cubic<K>::P1) return k_conv_p<Cubic<K>::P1>;
+        PME_CUBIC_KS(PME_PICK)
+#undef PME_PICK
+    }
+    return k_conv;
 }
 
 template <int P>
@@ -124,13 +192,13 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             else launch_tiles_spread<8>(d, s);
             break;
         case STAGE_FWD:
-            launch_pdl(k_fwd, d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d);
+            launch_pdl(fwd_kernel(d), d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d);
             break;
         case STAGE_CONV:
-            launch_pdl(k_conv, d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d);
+            launch_pdl(conv_kernel(d), d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d);
             break;
         case STAGE_INV:
-            launch_pdl(k_inv, d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d);
+            launch_pdl(inv_kernel(d), d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d);
             break;
         default:
             if (d.p == 4) launch_tiles_gather<4>(d, s);

@@ -809,22 +809,9 @@ PME_DEV void conv_lane(const SysDev &d, int item, void *smem) {
     }
 }
 
-// Threads (whole warps) a lane pass of plan c over ntr transforms occupies in its first iteration.
-PME_DEV int plan_col_units(int c, int ntr);
-
-// Lanes of plan c (PME_LANE_CASES).
-PME_DEV int plan_lanes(int c) {
-    switch (c) {
-#define PME_PL(c, L, E) \
-    case c: return L;
-        PME_LANE_CASES(PME_PL)
-#undef PME_PL
-    }
-    return 1;
-}
 
 PME_DEV int plan_col_units(int c, int ntr) {
-    const int T = 32 / plan_lanes(c);
+    const int T = 32 / plan_L(c);
     return ((ntr + T - 1) / T) * 32;
 }
 
@@ -832,17 +819,27 @@ PME_DEV int plan_col_units(int c, int ntr) {
 // (T = 32 / L transforms x 16 / T lanes, float2 = two banks) fall on distinct shared-memory banks.
 // Column reader (transform = column, lane j steps rows): stride = min(T, 16) mod 16.
 PME_DEV int stride_col_reader(int w, int c) {
-    const int L = plan_lanes(c);
+    const int L = plan_L(c);
     if (L <= 2) return w;  // a half-warp reads 16 consecutive columns of one row
     return w + ((32 / L - w) & 15);
 }
 // Row reader (transform = row, lane j steps along the row): stride = max(L / 2, 1) mod 16.
 PME_DEV int stride_row_reader(int w, int c) {
-    const int L = plan_lanes(c);
+    const int L = plan_L(c);
     if (L >= 32) return w;  // a half-warp reads 16 consecutive points of one row
     return w + (((L >= 2 ? L / 2 : 1) - w) & 15);
 }
 
+// Compile-time lanes and points of plan C.
+template <int C>
+struct PlanLE {
+    static constexpr int L = plan_L(C), E = plan_E(C);
+};
+
+// Lane slab / influence stages with the plans fixed at compile time (PR, PC, P1 >= 0: only that plan's code
+// is built into the kernel, which keeps it small enough for the instruction caches) or chosen at run time
+// from the system's plans (-1).
+template <int PR, int PC>
 PME_DEV void stage_fwd_lane(const SysDev &d, int k1, void *smem) {
     const int Nh = d.K3 / 2, zs = stride_col_reader(Nh, d.lp_cols);
     float2 *Z = (float2 *)smem;
@@ -853,25 +850,34 @@ PME_DEV void stage_fwd_lane(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID;
     const float2 a = tid <= Nh ? __ldg(d.tw3 + tid) : make_float2(0.f, 0.f);
     const float2 b = tid < d.K2 ? __ldg(d.tw2 + tid) : make_float2(0.f, 0.f);
-    switch (d.lp_rows) {
+    if constexpr (PR >= 0) {
+        fwd_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Z, zs);
+    } else {
+        switch (d.lp_rows) {
 #define PME_ROWS(c, L, E) \
     case c: fwd_rows_lane<L, E>(d, k1, Z, zs); break;
-        PME_LANE_CASES(PME_ROWS)
+            PME_LANE_CASES(PME_ROWS)
 #undef PME_ROWS
+        }
     }
     if (tid <= Nh) tw3[tid] = a;
     if (tid < d.K2) tw2[tid] = b;
     for (int i = tid + PME_NTH; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
     for (int i = tid + PME_NTH; i < d.K2; i += PME_NTH) tw2[i] = d.tw2[i];
     PME_SYNC();
-    switch (d.lp_cols) {
+    if constexpr (PC >= 0) {
+        fwd_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Z, zs, tw3, tw2);
+    } else {
+        switch (d.lp_cols) {
 #define PME_COLS(c, L, E) \
     case c: fwd_cols_lane<L, E>(d, k1, Z, zs, tw3, tw2); break;
-        PME_LANE_CASES(PME_COLS)
+            PME_LANE_CASES(PME_COLS)
 #undef PME_COLS
+        }
     }
 }
 
+template <int PR, int PC>
 PME_DEV void stage_inv_lane(const SysDev &d, int k1, void *smem) {
     const int Nh = d.K3 / 2, ys = stride_row_reader(d.H3, d.lp_rows);
     float2 *Y = (float2 *)smem;
@@ -885,66 +891,97 @@ PME_DEV void stage_inv_lane(const SysDev &d, int k1, void *smem) {
     const int cu = plan_col_units(d.lp_cols, d.H3);
     if (PME_NTH - cu >= 32) inv_side_work(d, k1, cu, PME_NTH - cu);
     else inv_side_work(d, k1, 0, PME_NTH);
-    switch (d.lp_cols) {
+    if constexpr (PC >= 0) {
+        inv_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Y, ys);
+    } else {
+        switch (d.lp_cols) {
 #define PME_COLS(c, L, E) \
     case c: inv_cols_lane<L, E>(d, k1, Y, ys); break;
-        PME_LANE_CASES(PME_COLS)
+            PME_LANE_CASES(PME_COLS)
 #undef PME_COLS
+        }
     }
     if (tid < Nh) twh[tid] = a;
     if (tid <= Nh) tw3[tid] = b;
     for (int i = tid + PME_NTH; i < Nh; i += PME_NTH) twh[i] = d.tw3h[i];
     for (int i = tid + PME_NTH; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
     PME_SYNC();
-    switch (d.lp_rows) {
+    if constexpr (PR >= 0) {
+        inv_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Y, ys, twh, tw3);
+    } else {
+        switch (d.lp_rows) {
 #define PME_ROWS(c, L, E) \
     case c: inv_rows_lane<L, E>(d, k1, Y, ys, twh, tw3); break;
-        PME_LANE_CASES(PME_ROWS)
+            PME_LANE_CASES(PME_ROWS)
 #undef PME_ROWS
+        }
     }
 }
 
+template <int P1>
 PME_DEV void stage_conv_lane(const SysDev &d, int item, void *smem) {
-    switch (d.lp_k1) {
+    if constexpr (P1 >= 0) {
+        conv_lane<PlanLE<P1>::L, PlanLE<P1>::E>(d, item, smem);
+    } else {
+        switch (d.lp_k1) {
 #define PME_K1(c, L, E) \
     case c: conv_lane<L, E>(d, item, smem); break;
-        PME_LANE_CASES(PME_K1)
+            PME_LANE_CASES(PME_K1)
 #undef PME_K1
+        }
     }
 }
 #endif  // PME_LANE_FFT
 
-// Stage entry points: the register path where the plan has lane plans, else the shared-memory path.
+// Stage entry points: the register path where the plan has lane plans, else the shared-memory path. With
+// plans given at compile time (a kernel specialised for one mesh), only the register path is built in; such
+// a kernel runs only for systems with exactly those plans.
+template <int PR = -1, int PC = -1>
 PME_DEV void stage_fwd(const SysDev &d, int k1, void *smem) {
     if (k1 == 0 && PME_TID == 0) d.ctl->novf = 0u;  // spreading (its last reader) has finished
 #if defined(PME_LANE_FFT)
-    if (d.lane_slab) {
-        stage_fwd_lane(d, k1, smem);
-        return;
+    if constexpr (PR >= 0) {
+        stage_fwd_lane<PR, PC>(d, k1, smem);
+    } else {
+        if (d.lane_slab) stage_fwd_lane<-1, -1>(d, k1, smem);
+        else stage_fwd_smem(d, k1, smem);
     }
-#endif
+#else
     stage_fwd_smem(d, k1, smem);
+#endif
 }
 
+template <int P1 = -1>
 PME_DEV void stage_conv(const SysDev &d, int item, void *smem) {
 #if defined(PME_LANE_FFT)
-    if (d.lane_conv) {
-        stage_conv_lane(d, item, smem);
-        return;
+    if constexpr (P1 >= 0) {
+        stage_conv_lane<P1>(d, item, smem);
+    } else {
+        if (d.lane_conv) stage_conv_lane<-1>(d, item, smem);
+        else stage_conv_smem(d, item, smem);
     }
-#endif
+#else
     stage_conv_smem(d, item, smem);
+#endif
 }
 
+template <int PR = -1, int PC = -1>
 PME_DEV void stage_inv(const SysDev &d, int k1, void *smem) {
 #if defined(PME_LANE_FFT)
-    if (d.lane_slab) {
-        stage_inv_lane(d, k1, smem);
-        return;
+    if constexpr (PR >= 0) {
+        stage_inv_lane<PR, PC>(d, k1, smem);
+    } else {
+        if (d.lane_slab) {
+            stage_inv_lane<-1, -1>(d, k1, smem);
+        } else {
+            inv_side_work(d, k1, 0, PME_NTH);
+            stage_inv_smem(d, k1, smem);
+        }
     }
-#endif
+#else
     inv_side_work(d, k1, 0, PME_NTH);
     stage_inv_smem(d, k1, smem);
+#endif
 }
 
 // ---------------------------------------------------------------------------------------------------------
