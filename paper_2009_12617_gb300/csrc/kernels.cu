@@ -60,15 +60,9 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
     stage_inv(d, blockIdx.x, smem);
 }
 
-// Slab and influence kernels specialised for the lane plans of cubic meshes K^3, K in PME_CUBIC_KS (the
-// shapes most systems use); each holds only its plans' code. Other meshes run the kernels above, which
-// choose among all plans at run time.
-#define PME_CUBIC_KS(X) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(128)
-template <int K>
-struct Cubic {
-    static constexpr int PR = slab_lane_plan(K / 2, K), PC = slab_lane_plan(K, K / 2 + 1), P1 = conv_lane_plan(K);
-    static_assert(PR >= 0 && PC >= 0 && P1 >= 0, "every listed cubic mesh has lane plans");
-};
+// Slab and influence kernels specialised for the lane plans of the cubic meshes of PME_CUBIC_KS (kernels.h);
+// each holds only its plans' code. Other meshes run the kernels above, which choose among all plans at run
+// time.
 
 template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_fwd_p(SysDev d) {

@@ -13,6 +13,14 @@ constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interp
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
 constexpr size_t MAX_SMEM_BYTES = 226 * 1024;  // opt-in limit is 227 KB including static shared memory
 
+// Cubic meshes K^3 whose lane plans get kernels (and batch stage calls) specialised at compile time.
+#define PME_CUBIC_KS(X) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(128)
+template <int K>
+struct Cubic {
+    static constexpr int PR = slab_lane_plan(K / 2, K), PC = slab_lane_plan(K, K / 2 + 1), P1 = conv_lane_plan(K);
+    static_assert(PR >= 0 && PC >= 0 && P1 >= 0, "every listed cubic mesh has lane plans");
+};
+
 // Launch mode of the per-stage kernels: 0 plain, 1 programmatic dependent launch triggered at kernel entry,
 // 2 triggered at CTA exit. Process-wide; affects launches recorded afterwards.
 void set_launch_mode(int mode);

@@ -236,19 +236,25 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
     int *lo = hi + VOL;
     int o1, o2, o3;
     tile_origin(d, item, o1, o2, o3);
+    const float4 *A = d.bka + (size_t)item * d.cap;
+    const int2 *B = d.bkb + (size_t)item * d.cap;
+    // the count and this thread's first record are loaded together (the record slot is always inside the
+    // bucket; it is used only if it holds an atom)
+    const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
+    const int a0 = imin(tid >> 1, d.cap - 1);
+    const float4 ra0 = ldcg(A + a0);
+    const int2 rb0 = ldcg(B + a0);
     for (int i = tid; i < VOL; i += nth) {
         hi[i] = 0;
         lo[i] = 0;
     }
-    const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
     PME_SYNC();
-    const float4 *A = d.bka + (size_t)item * d.cap;
-    const int2 *B = d.bkb + (size_t)item * d.cap;
     // two threads per atom: half h takes the planes j1 in [h P/2, (h + 1) P/2)
     for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
         const int a = a2 >> 1, half = a2 & 1;
-        const float4 ra = ldcg(A + a);
-        const int2 rb = ldcg(B + a);
+        const bool first = a2 == tid;
+        const float4 ra = first ? ra0 : ldcg(A + a);
+        const int2 rb = first ? rb0 : ldcg(B + a);
         float th1[P], th2[P], th3[P];
         bspline_w<P>(ra.x, th1);
         bspline_w<P>(ra.y, th2);
@@ -1050,6 +1056,14 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         float *reg = (float *)smem;
         int o1, o2, o3;
         tile_origin(d, item, o1, o2, o3);
+        const float4 *A = d.bka + (size_t)item * d.cap;
+        const int2 *B = d.bkb + (size_t)item * d.cap;
+        // the count and this thread's first record in flight with the region loads (the record slot is
+        // always inside the bucket; it is used only if it holds an atom)
+        const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
+        const int a0 = imin(tid >> 1, d.cap - 1);
+        const float4 ra0 = ldcg(A + a0);
+        const int2 rb0 = ldcg(B + a0);
         for (int base = tid; base < VOL; base += LOAD_BATCH * nth) {
             float v[LOAD_BATCH];
 #pragma unroll
@@ -1065,11 +1079,8 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
             for (int u = 0; u < LOAD_BATCH; ++u)
                 if (base + u * nth < VOL) reg[base + u * nth] = v[u];
         }
-        const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
         PME_SYNC();
         if (tid == 0) d.bcount[(size_t)item * BCOUNT_STRIDE] = 0u;  // consumed: ready for the next binning
-        const float4 *A = d.bka + (size_t)item * d.cap;
-        const int2 *B = d.bkb + (size_t)item * d.cap;
 #if defined(PME_HOST_EMULATION)
         float e1 = 0.f, e2 = 0.f, e3 = 0.f;  // the even half's partial sums, combined on the odd half
 #endif
@@ -1077,8 +1088,9 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         // halves are added in a fixed order, so both lanes hold the same total
         for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
             const int a = a2 >> 1, half = a2 & 1;
-            const float4 ra = ldcg(A + a);
-            const int2 rb = ldcg(B + a);
+            const bool first = a2 == tid;
+            const float4 ra = first ? ra0 : ldcg(A + a);
+            const int2 rb = first ? rb0 : ldcg(B + a);
             float th1[P], th2[P], th3[P], dth1[P], dth2[P], dth3[P];
             bspline_wd<P>(ra.x, th1, dth1);
             bspline_wd<P>(ra.y, th2, dth2);
