@@ -106,7 +106,11 @@ pme_status pme_sync(pme_plan *plan);
 
 /* pme_compute with HOST arrays (pos, q, forces in pageable or pinned host memory): the library copies
  * inputs to its own device staging, evaluates, and copies forces back, all on the plan stream, and
- * returns when forces, energy and virial are in host memory. */
+ * returns when forces, energy and virial are in host memory. When all three arrays are page-locked
+ * (cudaHostAlloc / cudaHostRegister), nothing is copied: the kernels read positions and charges and write
+ * forces in host memory directly over the CPU-GPU link, and the first call records the six stages as one
+ * CUDA graph that later calls with the same arrays and n replay (one launch per call); the arrays must then
+ * stay page-locked and allocated while the plan uses them. */
 pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                             double *energy, double *virial);
 

@@ -202,6 +202,38 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
     }
 }
 
+// Forces from device memory to page-locked host memory (coalesced 16-byte stores where both addresses
+// allow) and the control block to its host copy: the last step of an evaluation on host arrays.
+__global__ void __launch_bounds__(256) k_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl) {
+    pdl_wait();
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
+    if (((((size_t)src) | ((size_t)dst)) & 15) == 0) {
+        const long long n4 = nf >> 2;
+        for (long long i = tid; i < n4; i += nth) ((float4 *)dst)[i] = __ldcg((const float4 *)src + i);
+        for (long long i = (n4 << 2) + tid; i < nf; i += nth) dst[i] = __ldcg(src + i);
+    } else {
+        for (long long i = tid; i < nf; i += nth) dst[i] = __ldcg(src + i);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(Ctl) / 4)
+        ((unsigned *)hctl)[threadIdx.x] = __ldcg((const unsigned *)ctl + threadIdx.x);
+}
+
+cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl, cudaStream_t s) {
+    long long blocks = (nf / 4 + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1216) blocks = 1216;  // 152 SMs x 8
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_launch_mode ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_copy_out, src, dst, nf, ctl, hctl);
+}
+
 cudaError_t launch_pipeline(const SysDev &d, cudaStream_t s, const DebugTaps *taps) {
     const size_t mesh = (size_t)d.K1 * d.K2 * d.K3;
     cudaError_t e;

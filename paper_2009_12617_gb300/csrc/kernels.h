@@ -37,6 +37,11 @@ struct DebugTaps {
 
 enum Stage { STAGE_BIN = 0, STAGE_SPREAD, STAGE_FWD, STAGE_CONV, STAGE_INV, STAGE_GATHER, NUM_STAGES };
 
+// Enqueue the copy of nf floats from device memory to page-locked host memory (dst: its device-side
+// address) and of the control block ctl to its host copy hctl (device-side address), after the work before
+// it on s.
+cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl, cudaStream_t s);
+
 // Enqueue one stage kernel of system d.
 void launch_stage(const SysDev &d, int stage, cudaStream_t s);
 

@@ -195,6 +195,49 @@ pme_status collect_status(pme_plan *pl, bool copy_ctl) {
     return status_from_bits(bits);
 }
 
+// Device-accessible address of host memory that is page-locked (cudaHostAlloc / cudaHostRegister), or null.
+static void *device_view(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Enqueue the call described by key through graph g: replay it if it was recorded for these arguments,
+// record it now if the previous call (seen) had the same arguments, else enqueue directly. enqueue(stream)
+// issues the call's work on a stream.
+template <class F>
+static cudaError_t run_call(pme_plan *pl, pme_plan::EvalGraph &g, pme_plan::EvalGraph &seen,
+                            const pme_plan::EvalGraph &key, F enqueue) {
+    if (g.exec && g.same(key)) return cudaGraphLaunch(g.exec, pl->stream);
+    const bool repeat = seen.same(key);
+    seen = key;
+    if (repeat) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = pme_plan::EvalGraph();
+        bool ok = pl->rec_stream || cudaStreamCreateWithFlags(&pl->rec_stream, cudaStreamNonBlocking) == cudaSuccess;
+        cudaGraph_t graph = nullptr;
+        if (ok) ok = cudaStreamBeginCapture(pl->rec_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const cudaError_t r = enqueue(pl->rec_stream);
+            const cudaError_t e = cudaStreamEndCapture(pl->rec_stream, &graph);
+            ok = r == cudaSuccess && e == cudaSuccess;
+            cudaGraphExec_t exec = nullptr;
+            if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            if (ok) {
+                g = key;
+                g.exec = exec;
+                return cudaGraphLaunch(g.exec, pl->stream);
+            }
+        }
+        cudaGetLastError();  // not recordable here: enqueue directly
+    }
+    return enqueue(pl->stream);
+}
+
 }  // namespace pme
 
 using namespace pme;
@@ -281,6 +324,7 @@ pme_status pme_set_box(pme_plan *pl, const double box[9]) {
     memcpy(pl->recip, recip, sizeof(recip));
     pl->vol = vol;
     fill_geometry(pl->d, pl->K, pl->p, pl->beta, recip);
+    ++pl->gen;
     return upload_tables(pl);
 }
 
@@ -321,10 +365,27 @@ pme_status pme_compute_debug(pme_plan *pl, const float *pos, const float *q, int
     if ((st = plan_reserve(pl, n)) != PME_OK) return st;
     const SysDev d = plan_descriptor(pl, pos, q, n, forces, nullptr);
     DebugTaps taps = {(unsigned long long *)mesh_dev, phi_dev};
-    cudaError_t e = launch_pipeline(d, pl->stream, (mesh_dev || phi_dev) ? &taps : nullptr);
+    const bool tapped = mesh_dev || phi_dev;
+    auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t r = launch_pipeline(d, s, tapped ? &taps : nullptr);
+        if (r != cudaSuccess) return r;
+        return cudaMemcpyAsync(pl->h_ctl, pl->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    };
+    cudaError_t e;
+    if (tapped) {
+        e = enqueue(pl->stream);
+    } else {
+        pme_plan::EvalGraph key;
+        key.pos = pos;
+        key.q = q;
+        key.forces = forces;
+        key.atoms = pl->atom_mem;
+        key.n = n;
+        key.mode = launch_mode();
+        key.gen = pl->gen;
+        e = run_call(pl, pl->g_dev, pl->seen_dev, key, enqueue);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-    if ((e = cudaMemcpyAsync(pl->h_ctl, pl->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(result)");
     if ((st = collect_status(pl, true)) != PME_OK) return st;
     if (energy) *energy = pl->h_ctl->ev[0];
     if (virial)
@@ -338,6 +399,7 @@ pme_status pme_compute_host(pme_plan *pl, const float *pos, const float *q, int6
     if (st) return st;
     DeviceGuard g(pl->dev);
     cudaError_t e;
+    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
     if (n > pl->host_cap) {
         if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
         if (pl->host_mem) cudaFree(pl->host_mem);
@@ -353,19 +415,45 @@ pme_status pme_compute_host(pme_plan *pl, const float *pos, const float *q, int6
     char *b = (char *)pl->host_mem;
     float *dpos = (float *)b, *dfor = (float *)(b + align256((size_t)pl->host_cap * 12));
     float *dq = (float *)(b + 2 * align256((size_t)pl->host_cap * 12));
-    if (n > 0) {
-        if ((e = cudaMemcpyAsync(dpos, pos, (size_t)n * 12, cudaMemcpyHostToDevice, pl->stream)) != cudaSuccess)
-            return cuda_fail(e, "cudaMemcpyAsync(pos)");
-        if ((e = cudaMemcpyAsync(dq, q, (size_t)n * 4, cudaMemcpyHostToDevice, pl->stream)) != cudaSuccess)
-            return cuda_fail(e, "cudaMemcpyAsync(q)");
+    const float *mpos = n > 0 ? (const float *)device_view(pos) : nullptr;
+    const float *mq = n > 0 ? (const float *)device_view(q) : nullptr;
+    float *mfor = n > 0 ? (float *)device_view(forces) : nullptr;
+    Ctl *mctl = (Ctl *)device_view(pl->h_ctl);
+    if (mpos && mq && mfor && mctl) {
+        // Page-locked arrays: binning reads positions and charges in host memory directly (coalesced, over
+        // the CPU-GPU link), the forces are gathered into device staging and written back with the control
+        // block by one copy kernel; as a graph, the call is one launch and one wait.
+        const SysDev d = plan_descriptor(pl, mpos, mq, n, dfor, nullptr);
+        auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+            cudaError_t r = launch_pipeline(d, s);
+            if (r != cudaSuccess) return r;
+            return launch_copy_out(dfor, mfor, (long long)n * 3, pl->d.ctl, mctl, s);
+        };
+        pme_plan::EvalGraph key;
+        key.pos = pos;
+        key.q = q;
+        key.forces = forces;
+        key.atoms = pl->atom_mem;
+        key.staging = pl->host_mem;
+        key.n = n;
+        key.mode = launch_mode();
+        key.gen = pl->gen;
+        if ((e = run_call(pl, pl->g_host, pl->seen_host, key, enqueue)) != cudaSuccess)
+            return cuda_fail(e, "enqueueing the evaluation");
+    } else {  // pageable arrays: copies to and from device staging around the six stages
+        if (n > 0) {
+            if ((e = cudaMemcpyAsync(dpos, pos, (size_t)n * 12, cudaMemcpyHostToDevice, pl->stream)) != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpyAsync(pos)");
+            if ((e = cudaMemcpyAsync(dq, q, (size_t)n * 4, cudaMemcpyHostToDevice, pl->stream)) != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpyAsync(q)");
+        }
+        const SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, nullptr);
+        if ((e = launch_pipeline(d, pl->stream)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (n > 0 && (e = cudaMemcpyAsync(forces, dfor, (size_t)n * 12, cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(forces)");
+        if ((e = cudaMemcpyAsync(pl->h_ctl, pl->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(result)");
     }
-    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
-    const SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, nullptr);
-    if ((e = launch_pipeline(d, pl->stream)) != cudaSuccess) return cuda_fail(e, "kernel launch");
-    if (n > 0 && (e = cudaMemcpyAsync(forces, dfor, (size_t)n * 12, cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(forces)");
-    if ((e = cudaMemcpyAsync(pl->h_ctl, pl->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, pl->stream)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(result)");
     if ((st = collect_status(pl, true)) != PME_OK) return st;
     if (energy) *energy = pl->h_ctl->ev[0];
     if (virial)
@@ -421,6 +509,9 @@ void pme_destroy(pme_plan *pl) {
     if (!pl) return;
     DeviceGuard g(pl->dev);
     cudaStreamSynchronize(pl->stream);
+    if (pl->g_dev.exec) cudaGraphExecDestroy(pl->g_dev.exec);
+    if (pl->g_host.exec) cudaGraphExecDestroy(pl->g_host.exec);
+    if (pl->rec_stream) cudaStreamDestroy(pl->rec_stream);
     if (pl->mesh_mem) cudaFree(pl->mesh_mem);
     if (pl->atom_mem) cudaFree(pl->atom_mem);
     if (pl->host_mem) cudaFree(pl->host_mem);

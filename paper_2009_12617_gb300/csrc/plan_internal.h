@@ -24,6 +24,23 @@ struct pme_plan {
     void *host_mem = nullptr;       // device staging for pme_compute_host
     int64_t host_cap = 0;
     pme::Ctl *h_ctl = nullptr;      // pinned host copy of the control block
+    unsigned long long gen = 0;     // bumped whenever the kernels' arguments change (box)
+    // Repeated synchronous calls replay a CUDA graph of the whole call, recorded (on a private stream, as
+    // the plan stream may not be capturable) once the same arguments come twice in a row: one for device
+    // arrays (pme_compute) and one for page-locked host arrays (pme_compute_host).
+    struct EvalGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void *pos = nullptr, *q = nullptr, *forces = nullptr, *atoms = nullptr, *staging = nullptr;
+        int64_t n = -1;
+        int mode = -1;
+        unsigned long long gen = ~0ull;
+        bool same(const EvalGraph &o) const {
+            return pos == o.pos && q == o.q && forces == o.forces && atoms == o.atoms && staging == o.staging &&
+                   n == o.n && mode == o.mode && gen == o.gen;
+        }
+    };
+    EvalGraph g_dev, g_host, seen_dev, seen_host;  // recorded graphs, and the previous call's arguments
+    cudaStream_t rec_stream = nullptr;
 };
 
 namespace pme {

@@ -192,6 +192,76 @@ def test_host_pointer_path(pmelib, oracle_mod):
         pmelib.pme_destroy(plan)
 
 
+def test_host_pointer_path_pinned_graph(pmelib):
+    """Page-locked host arrays take the recorded-graph path: its results equal the pageable path's bit for
+    bit, new positions in the same arrays are picked up on replay, and a box change re-records the graph."""
+    torch = pytest.importorskip("torch")
+    s = wl.parity_system()
+    n = s.n
+    pos_t = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    q_t = torch.empty(n, dtype=torch.float32).pin_memory()
+    f_t = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    P, Q, F = pos_t.numpy(), q_t.numpy(), f_t.numpy()
+    Q[:] = s.q
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        L = float(s.box[0, 0])
+        frames = [s.pos.astype(np.float32)]
+        for step in range(2):
+            frames.append(wl.jitter(frames[-1], L, 7, step).astype(np.float32))
+        for box_scale in (1.0, 1.02):
+            if box_scale != 1.0:
+                pmelib.pme_set_box(plan, s.box * box_scale)
+            for fr in frames:
+                P[:] = fr
+                _, E1, v1 = pmelib.pme_compute_host(plan, P, Q, F)
+                F1 = F.copy()
+                F2, E2, v2 = pmelib.pme_compute_host(plan, fr.copy(), s.q.copy())  # pageable: plain path
+                assert E1 == E2
+                assert np.array_equal(F1, F2)
+                assert np.array_equal(v1, v2)
+    finally:
+        pmelib.pme_destroy(plan)
+
+
+def test_compute_repeated_calls(pmelib):
+    """Repeated synchronous calls with the same device arrays are replayed from a recorded graph: results
+    equal a fresh plan's bit for bit, new values in the same arrays are picked up, and a box change and a
+    launch-mode change are honoured."""
+    torch = pytest.importorskip("torch")
+    s = wl.parity_system()
+    dev = torch.device("cuda", 0)
+    L = float(s.box[0, 0])
+    frames = [s.pos.astype(np.float32)]
+    for step in range(3):
+        frames.append(wl.jitter(frames[-1], L, 11, step).astype(np.float32))
+    pos = torch.from_numpy(frames[0]).to(dev)
+    q = torch.from_numpy(s.q.astype(np.float32)).to(dev)
+    F = torch.empty_like(pos)
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        for box_scale, mode in ((1.0, 2), (1.03, 2), (1.03, 0)):
+            if box_scale != 1.0:
+                pmelib.pme_set_box(plan, s.box * box_scale)
+            pmelib.pme_set_launch_mode(mode)
+            for fr in frames:
+                pos.copy_(torch.from_numpy(fr))
+                for _ in range(3):  # eager, recorded, replayed
+                    E, v = pmelib.pme_compute(plan, pos, q, F)
+                    fresh = pmelib.pme_create(s.K, s.p, s.beta, s.box * box_scale)
+                    try:
+                        F2 = torch.empty_like(pos)
+                        E2, v2 = pmelib.pme_compute(fresh, pos, q, F2)
+                    finally:
+                        pmelib.pme_destroy(fresh)
+                    assert E == E2
+                    assert np.array_equal(v, v2)
+                    assert torch.equal(F, F2)
+    finally:
+        pmelib.pme_set_launch_mode(2)
+        pmelib.pme_destroy(plan)
+
+
 def test_enqueue_in_cuda_graph(pmelib):
     """pme_enqueue allocates nothing after pme_reserve, so a torch CUDA graph can capture it; replays give
     the synchronous result bit for bit."""
