@@ -12,10 +12,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pme.h"
 #include "batch_internal.h"
+#include "group.h"
 #include "host_tables.h"
 #include "kernels.h"
 #include "plan_internal.h"
@@ -322,12 +324,117 @@ struct pme_batch {
     WaveState wave;
     size_t smem = 0;
     int grid = 0;
-    // graph of (descriptor upload, persistent kernel, status collection) for the last pointer set
+    // Grouped execution (the default): systems of one mesh shape form a group, evaluated by a chain of six
+    // grouped stage launches; the chains run as parallel branches of the graph. order lists the systems
+    // group by group; d_gsys / h_gsys hold their descriptors in that order.
+    struct Group {
+        int first, count, max_nbin;
+    };
+    std::vector<int> order;
+    std::vector<Group> groups;
+    SysDev *d_gsys = nullptr, *h_gsys = nullptr;
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gevents;
+    // graph of the whole evaluation (descriptor upload, the stages, status collection) for the last
+    // pointer set and mode
     cudaGraphExec_t exec = nullptr;
     const void *g_pos = nullptr, *g_q = nullptr, *g_forces = nullptr, *g_ev = nullptr;
     int stall = 0;
     int64_t stall_ns = 0;
 };
+
+// Grouped evaluation: the persistent kernel is used only while the stall test hook is on (its bounded
+// waits are what that hook exercises).
+static pme_status batch_record_grouped(pme_batch *b, const float *pos, const float *q, float *forces, double *ev_dev) {
+    const int nsys = (int)b->sys.size();
+    for (int i = 0; i < nsys; ++i) {
+        const int s = b->order[i];
+        SysDev d = b->sys[s];
+        d.pos = pos + 3 * b->off[s];
+        d.q = q + b->off[s];
+        d.forces = forces + 3 * b->off[s];
+        d.ev = ev_dev + 7 * s;
+        b->h_gsys[i] = d;
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->d_gsys, b->h_gsys, sizeof(SysDev) * nsys, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(batch descriptors)");
+    const int G = (int)b->groups.size();
+    if ((e = cudaEventRecord(b->gevents[G], b->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int g = 0; g < G; ++g) {
+        const pme_batch::Group &gr = b->groups[g];
+        cudaStream_t gs = b->gstreams[g];
+        if ((e = cudaStreamWaitEvent(gs, b->gevents[G], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        if ((e = launch_group_chain(b->d_gsys + gr.first, gr.count, b->h_gsys[gr.first], gr.max_nbin, gs)) != cudaSuccess)
+            return cuda_fail(e, "grouped stage launch");
+        if ((e = cudaEventRecord(b->gevents[g], gs)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(b->stream, b->gevents[g], 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    if ((e = launch_collect_status(b->d_gsys, nsys, b->wave.d_status, b->stream)) != cudaSuccess)
+        return cuda_fail(e, "status kernel launch");
+    return PME_OK;
+}
+
+// Group the systems by mesh shape and order (and tile edge); returns false if grouping is not possible.
+static bool batch_make_groups(pme_batch *b) {
+    const int nsys = (int)b->sys.size();
+    std::vector<int> idx(nsys);
+    for (int s = 0; s < nsys; ++s) idx[s] = s;
+    auto key = [&](int s) {
+        const SysDev &d = b->sys[s];
+        return std::make_tuple(d.K1, d.K2, d.K3, d.p, d.tlog);
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return key(x) < key(y); });
+    b->order = idx;
+    b->groups.clear();
+    for (int i = 0; i < nsys; ++i) {
+        const SysDev &d = b->sys[idx[i]];
+        if (d.tlog != 3) return false;
+        if (i == 0 || key(idx[i]) != key(idx[i - 1])) b->groups.push_back({i, 0, 0});
+        pme_batch::Group &g = b->groups.back();
+        ++g.count;
+        g.max_nbin = std::max(g.max_nbin, d.nbin);
+    }
+    return true;
+}
+
+static void batch_release_groups(pme_batch *b) {
+    for (cudaStream_t s : b->gstreams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->gevents) cudaEventDestroy(e);
+    b->gstreams.clear();
+    b->gevents.clear();
+    if (b->d_gsys) cudaFree(b->d_gsys);
+    if (b->h_gsys) cudaFreeHost(b->h_gsys);
+    b->d_gsys = b->h_gsys = nullptr;
+    b->groups.clear();
+}
+
+static pme_status batch_init_groups(pme_batch *b) {
+    if (!batch_make_groups(b)) return PME_OK;  // stays on the persistent path
+    const int nsys = (int)b->sys.size(), G = (int)b->groups.size();
+    cudaError_t e;
+    if ((e = configure_group_kernels()) != cudaSuccess) return cuda_fail(e, "configure grouped kernels");
+    if ((e = cudaMalloc(&b->d_gsys, sizeof(SysDev) * nsys)) != cudaSuccess) {
+        b->d_gsys = nullptr;
+        return fail(PME_ENOMEM, "cudaMalloc(batch descriptors): %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMallocHost(&b->h_gsys, sizeof(SysDev) * nsys)) != cudaSuccess) {
+        b->h_gsys = nullptr;
+        return cuda_fail(e, "cudaMallocHost(batch descriptors)");
+    }
+    for (int g = 0; g < G; ++g) {
+        cudaStream_t s;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        b->gstreams.push_back(s);
+    }
+    for (int g = 0; g <= G; ++g) {  // one per group, then the fork
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        b->gevents.push_back(ev);
+    }
+    return PME_OK;
+}
 
 static pme_status batch_record(pme_batch *b, const float *pos, const float *q, float *forces, double *ev_dev) {
     const int nsys = (int)b->sys.size();
@@ -411,6 +518,12 @@ pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, 
     }
     b->smem = batch_smem(b->sys);
     b->grid = batch_grid(b->dev, b->sys[0].p, b->smem);
+    if ((st = batch_init_groups(b)) != PME_OK) {
+        batch_release_groups(b);
+        b->wave.release();
+        delete b;
+        return st;
+    }
     *out = b;
     return PME_OK;
 }
@@ -435,7 +548,9 @@ pme_status pme_batch_enqueue(pme_batch *b, const float *pos, const float *q, flo
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         pme_status st = PME_OK;
-        if (e == cudaSuccess) st = batch_record(b, pos, q, forces, ev_dev);
+        if (e == cudaSuccess)
+            st = (!b->groups.empty() && !b->stall) ? batch_record_grouped(b, pos, q, forces, ev_dev)
+                                                   : batch_record(b, pos, q, forces, ev_dev);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         b->stream = keep;
         cudaStreamDestroy(cs);
@@ -499,6 +614,7 @@ void pme_batch_destroy(pme_batch *b) {
     DeviceGuard g(b->dev);
     cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    batch_release_groups(b);
     b->wave.release();
     delete b;
 }

@@ -3,27 +3,10 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "pdl.cuh"
 #include "stages.cuh"
 
 namespace pme {
-
-// Programmatic dependent launch (optional, launch_mode): a stage kernel launched with programmatic stream
-// serialisation waits for its predecessor to complete (with its memory visible) before touching any data,
-// and lets its successor start launching either at its own start (mode 1) or once each CTA has finished
-// its work (mode 2), so the successor's launch latency overlaps this kernel. Without the launch attribute
-// (mode 0) both instructions are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-struct PdlScope {  // trigger at entry (early) or at exit (late); the kernel argument picks
-    bool late;
-    __device__ explicit PdlScope(bool l) : late(l) {
-        if (!late) pdl_trigger();
-        pdl_wait();
-    }
-    __device__ ~PdlScope() {
-        if (late) pdl_trigger();
-    }
-};
 
 static int g_launch_mode = 2;  // measured fastest on GB300 (late trigger)
 void set_launch_mode(int mode) { g_launch_mode = mode; }
