@@ -676,18 +676,17 @@ def leg_serving(args, sampler, n_req: int = 4000):
                 busy_bufs[i] += 1
                 inflight.append((nxt, i, t))
                 nxt += 1
-            progressed = False
-            while inflight:
-                r, i, t = inflight[0]
-                if pme.pme_poll(srv, t, block=False) != pme.PME_OK:
-                    break
-                inflight.popleft()
-                lat[r] = (time.perf_counter() - t0) - arrival[r]
-                busy_bufs[i] -= 1
-                done += 1
-                progressed = True
-            if not progressed and nxt < n_req and arrival[nxt] > time.perf_counter() - t0 + 20e-6:
-                time.sleep(5e-6)
+            # every in-flight ticket is polled (completions need not come in submission order); the loop
+            # spins rather than sleeps, as a timed sleep would round up to tens of microseconds
+            still = collections.deque()
+            for r, i, t in inflight:
+                if pme.pme_poll(srv, t, block=False) == pme.PME_OK:
+                    lat[r] = (time.perf_counter() - t0) - arrival[r]
+                    busy_bufs[i] -= 1
+                    done += 1
+                else:
+                    still.append((r, i, t))
+            inflight = still
         elapsed = time.perf_counter() - t0
         sampler.window(time.time() - elapsed, time.time())
         stats = pme.pme_server_stats(srv)

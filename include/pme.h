@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 typedef struct pme_plan pme_plan;      /* opaque: one periodic system geometry + its resident device state */
-typedef struct pme_batch pme_batch;    /* opaque: a fixed set of systems evaluated in one persistent launch */
+typedef struct pme_batch pme_batch;    /* opaque: a fixed set of systems evaluated together per call */
 typedef struct pme_server pme_server;  /* opaque: continuous-batching request loop */
 typedef int64_t pme_ticket;
 
@@ -53,7 +53,7 @@ typedef enum {
     PME_ECUDA = 4,         /* a CUDA runtime call failed (detail has the CUDA error string) */
     PME_EOVERFLOW = 5,     /* sum |q| too large for the 64-bit fixed-point charge mesh */
     PME_EAGAIN = 6,        /* server: no slot or memory free right now; retry later */
-    PME_ETIMEOUT = 7,      /* a bounded device-side wait gave up (persistent kernel dependency) */
+    PME_ETIMEOUT = 7,      /* a bounded device-side wait gave up (persistent work-list kernel dependency) */
     PME_PENDING = 8        /* pme_poll: request still in flight */
 } pme_status;
 
@@ -152,13 +152,15 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
                                void *cuda_stream);
 
 /* ------------------------------------------------------------------------------------------------------ */
-/* Batched evaluation: many independent systems in ONE persistent kernel launch                            */
+/* Batched evaluation: many independent systems per call, replayed from one CUDA graph                      */
 
 /* Build a batch over nsys existing plans (not owned by the batch; each must outlive it and must not be
- * used elsewhere while the batch runs). All plans must use the same B-spline order p. Atom counts n[s] are fixed for the batch. Atom arrays of all
- * systems are packed back to back in the order given: system s owns atoms [off_s, off_s + n[s]) with
- * off_s = n[0] + ... + n[s-1]. The batch runs on cuda_stream and captures its launch in a CUDA graph on
- * first use. */
+ * used elsewhere while the batch runs). All plans must use the same B-spline order p. Atom counts n[s] are
+ * fixed for the batch. Atom arrays of all systems are packed back to back in the order given: system s owns
+ * atoms [off_s, off_s + n[s]) with off_s = n[0] + ... + n[s-1]. Systems of one mesh shape are evaluated
+ * together (one launch per stage for the whole group), the groups concurrently; the batch runs on
+ * cuda_stream and records its work as one CUDA graph, re-recorded when the array pointers change. Results
+ * equal each system's single-system evaluation bit for bit. */
 pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, void *cuda_stream, pme_batch **out);
 
 /* Evaluate every system of the batch: pos (Ntot x 3), q (Ntot), forces (Ntot x 3) are packed device
@@ -171,9 +173,9 @@ void pme_batch_destroy(pme_batch *batch);
 /* ------------------------------------------------------------------------------------------------------ */
 /* Serving: continuous batching of independent requests                                                   */
 
-/* A server owns a worker thread that admits submitted requests into "waves" (one persistent launch
- * each) while earlier waves are still running, bounded by max_slots requests in flight and by
- * mem_budget_bytes of device memory held by the plans of in-flight requests. */
+/* A server owns a worker thread that admits submitted requests into "waves" (requests of one mesh shape
+ * share one launch per stage) while earlier waves are still running, bounded by max_slots requests in
+ * flight and by mem_budget_bytes of device memory held by the plans of in-flight requests. */
 pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server **out);
 
 /* Submit one evaluation on a resident plan. pos, q, forces are device arrays that must stay valid until
@@ -202,7 +204,8 @@ const char *pme_strerror(pme_status s);
  * status that produced it (PME_OK if none). */
 pme_status pme_last_error_detail(char *buf, size_t len);
 
-/* Test hook: when set (nonzero) on a batch, its next launch makes one dependency wait on a counter that
+/* Test hook: when set (nonzero) on a batch, the batch runs as one persistent work-list kernel whose
+ * entries wait (bounded) for their dependencies, and its next launch makes one such wait on a counter that
  * nothing advances. The bounded wait gives up after wait_limit_ns (<= 2 s) and the launch reports
  * PME_ETIMEOUT from pme_batch_sync(), leaving the device usable. 0 restores normal operation. */
 pme_status pme_batch_debug_stall(pme_batch *batch, int enable, int64_t wait_limit_ns);

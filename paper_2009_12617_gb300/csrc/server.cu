@@ -2,8 +2,9 @@
 //
 // Requests name a resident plan (its mesh, influence table and buckets stay on the device across
 // requests) and their own device input / output arrays. A worker thread turns pending requests into
-// "waves": each wave is one persistent batched launch (batch.cu) over the admitted requests, on its own
-// stream. New waves are formed while earlier ones still run, so requests that arrive during a wave are
+// "waves": the admitted requests are grouped by mesh shape and each group runs as one chain of six grouped
+// stage launches (group.cu) on the wave's own stream. New waves are formed while earlier ones still run, so
+// requests that arrive during a wave are
 // admitted as soon as a wave slot, request slots and device memory allow, and their work overlaps the
 // tail of the running wave on the GPU. Admission is FIFO with two rules: a plan serves one request at a
 // time (its resident buffers are single-use), and the plans of all in-flight requests must fit in the
@@ -13,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <tuple>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -24,6 +26,7 @@
 
 #include "../../include/pme.h"
 #include "batch_internal.h"
+#include "group.h"
 #include "host_tables.h"
 #include "plan_internal.h"
 
@@ -31,7 +34,7 @@ using namespace pme;
 
 namespace {
 
-constexpr int WAVE_SLOTS = 3;        // persistent launches that may be in flight at once
+constexpr int WAVE_SLOTS = 3;        // waves that may be in flight at once
 constexpr int MAX_WAVE_SYSTEMS = 64;  // requests per wave
 
 double now_us() {
@@ -111,16 +114,13 @@ static void finish_wave(pme_server *sv, Wave &w) {
 static bool launch_wave(pme_server *sv, Wave &w) {
     if (sv->pending.empty()) return false;
     std::unordered_set<pme_plan *> chosen;
-    int p = -1;
     size_t bytes = sv->inflight_bytes;
     for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)w.reqs.size() < MAX_WAVE_SYSTEMS;) {
         Request *r = *it;
         const size_t pb = plan_bytes(r->plan);
-        const bool ok = !sv->busy_plans.count(r->plan) && !chosen.count(r->plan) && (p < 0 || r->plan->p == p) &&
-                        bytes + pb <= sv->budget;
+        const bool ok = !sv->busy_plans.count(r->plan) && !chosen.count(r->plan) && bytes + pb <= sv->budget;
         if (ok) {
             chosen.insert(r->plan);
-            p = r->plan->p;
             bytes += pb;
             w.reqs.push_back(r);
             it = sv->pending.erase(it);
@@ -130,17 +130,18 @@ static bool launch_wave(pme_server *sv, Wave &w) {
     }
     if (w.reqs.empty()) return false;
     const int nsys = (int)w.reqs.size();
+    // Requests of one mesh shape form a group: one launch per stage covers the group (group.cu); groups
+    // follow one another on the wave's stream.
+    auto shape = [](const pme_plan *pl) { return std::make_tuple(pl->K[0], pl->K[1], pl->K[2], pl->p); };
+    std::stable_sort(w.reqs.begin(), w.reqs.end(),
+                     [&](const Request *x, const Request *y) { return shape(x->plan) < shape(y->plan); });
     w.sys.clear();
     for (int s = 0; s < nsys; ++s) {
         Request *r = w.reqs[s];
         w.sys.push_back(plan_descriptor(r->plan, r->pos, r->q, r->n, r->forces, nullptr));
     }
-    build_work_list(w.sys, w.entries, w.count);
-    if (!w.st.dmem || w.entries.size() > w.st.cap_entries) {
-        cudaStreamSynchronize(w.stream);
-        w.st.release();
-        const size_t cap = std::max<size_t>(w.entries.size() * 2, 65536);
-        if (w.st.init(sv->dev, MAX_WAVE_SYSTEMS, cap) != PME_OK) {
+    if (!w.st.dmem) {
+        if (w.st.init(sv->dev, MAX_WAVE_SYSTEMS, 1) != PME_OK) {
             for (Request *r : w.reqs) sv->pending.push_front(r);
             w.reqs.clear();
             sv->fatal = PME_ENOMEM;
@@ -153,13 +154,16 @@ static bool launch_wave(pme_server *sv, Wave &w) {
         sv->busy_plans.insert(w.reqs[s]->plan);
         sv->inflight_bytes += plan_bytes(w.reqs[s]->plan);
     }
-    memcpy(w.st.h_entries, w.entries.data(), sizeof(BatchEntry) * w.entries.size());
-    memcpy(w.st.h_count, w.count.data(), sizeof(unsigned) * w.count.size());
-    const size_t smem = batch_smem(w.sys);
-    const int grid = batch_grid(sv->dev, p, smem);
-    BatchArgs a = w.st.args(nsys, (int)w.entries.size(), 1000000000ull, -1);
-    cudaError_t e = w.st.upload(w.entries.size(), w.stream);
-    if (e == cudaSuccess) e = launch_batch(a, p, grid, smem, w.stream);
+    cudaError_t e = w.st.upload(0, w.stream);
+    for (int g0 = 0; g0 < nsys && e == cudaSuccess;) {
+        int g1 = g0 + 1, max_nbin = w.sys[g0].nbin;
+        while (g1 < nsys && shape(w.reqs[g1]->plan) == shape(w.reqs[g0]->plan) && w.sys[g1].tlog == w.sys[g0].tlog) {
+            max_nbin = std::max(max_nbin, w.sys[g1].nbin);
+            ++g1;
+        }
+        e = launch_group_chain(w.st.d_sys + g0, g1 - g0, w.sys[g0], max_nbin, w.stream);
+        g0 = g1;
+    }
     if (e == cudaSuccess) e = launch_collect_status(w.st.d_sys, nsys, w.st.d_status, w.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w.st.h_ev, w.st.d_ev, sizeof(double) * 8 * nsys, cudaMemcpyDeviceToHost, w.stream);
@@ -205,9 +209,10 @@ static void worker_main(pme_server *sv) {
         if (sv->stop && sv->pending.empty() && !any_busy) break;
         if (!progress) {
             if (any_busy) {
-                // a wave is running: poll its event at a fine granularity, unlocked
+                // a wave is running: poll its event, unlocked, yielding the core between polls (a timed
+                // sleep would round up to the kernel's timer slack, tens of microseconds)
                 lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
+                std::this_thread::yield();
                 lk.lock();
             } else {
                 sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
@@ -227,10 +232,10 @@ pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server 
     cudaGetDevice(&sv->dev);
     sv->budget = mem_budget_bytes;
     sv->max_slots = max_slots;
-    cudaError_t e = configure_batch_kernel();
+    cudaError_t e = configure_group_kernels();
     if (e != cudaSuccess) {
         delete sv;
-        return cuda_fail(e, "configure persistent kernel");
+        return cuda_fail(e, "configure grouped kernels");
     }
     for (Wave &w : sv->waves) {
         if ((e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -238,7 +243,7 @@ pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server 
             pme_server_destroy(sv);
             return cuda_fail(e, "stream / event creation");
         }
-        pme_status st = w.st.init(sv->dev, MAX_WAVE_SYSTEMS, 65536);
+        pme_status st = w.st.init(sv->dev, MAX_WAVE_SYSTEMS, 1);
         if (st != PME_OK) {
             pme_server_destroy(sv);
             return st;
