@@ -149,13 +149,15 @@ static void (*conv_kernel(const SysDev &d))(SysDev) {
 
 template <int P>
 static void launch_tiles_spread(const SysDev &d, cudaStream_t s) {
-    if (d.tlog == 4) launch_pdl(k_spread<P, 16>, d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P, 4), s, d);
-    else launch_pdl(k_spread<P, 8>, d.ntiles + OVF_ITEMS, NT_TILE, smem_spread(P, 3), s, d);
+    const unsigned nt = (unsigned)tile_threads(d, d.n);
+    if (d.tlog == 4) launch_pdl(k_spread<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_spread(P, 4), s, d);
+    else launch_pdl(k_spread<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_spread(P, 3), s, d);
 }
 template <int P>
 static void launch_tiles_gather(const SysDev &d, cudaStream_t s) {
-    if (d.tlog == 4) launch_pdl(k_gather<P, 16>, d.ntiles + OVF_ITEMS, NT_TILE, smem_gather_all(P, 4), s, d);
-    else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, NT_TILE, smem_gather_all(P, 3), s, d);
+    const unsigned nt = (unsigned)tile_threads(d, d.n);
+    if (d.tlog == 4) launch_pdl(k_gather<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 4), s, d);
+    else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 3), s, d);
 }
 
 void launch_stage(const SysDev &d, int stage, cudaStream_t s) {

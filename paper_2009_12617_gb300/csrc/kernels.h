@@ -9,7 +9,13 @@ namespace pme {
 
 constexpr int NT_BIN = 128;    // threads per CTA for binning (BIN_CHUNK atoms per CTA)
 constexpr int NT_SLAB = SLAB_THREADS;  // threads per CTA for the forward / inverse slab FFT stages
-constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interpolation (two per atom)
+constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interpolation (two per atom), at most
+// Spread / gather CTA size for a system whose binned atoms number about n_bins * BIN_CHUNK: two threads per
+// atom, sized to the mean tile occupancy, so sparse tiles (large meshes) do not leave half the CTA idle and
+// twice as many CTAs fit on an SM. Results do not depend on it.
+inline int tile_threads(const SysDev &d, int64_t n) {
+    return (d.ntiles > 0 && n <= (int64_t)64 * d.ntiles) ? 128 : NT_TILE;
+}
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
 constexpr size_t MAX_SMEM_BYTES = 226 * 1024;  // opt-in limit is 227 KB including static shared memory
 
