@@ -1,4 +1,5 @@
-"""GPU tests of the batched persistent launch (many uneven systems in one kernel) and the serving loop.
+"""GPU tests of batched evaluation (grouped stage launches; the persistent work-list kernel behind the stall
+hook) and the serving loop.
 
 Each system's result in a batch or a served mix must equal its result alone (pme_compute) within the
 parity tolerances; the work decomposition of a system is the same in every launch, so the results are
@@ -181,3 +182,77 @@ def test_server_admission_limits(pme, systems):
             check_same(o, F.cpu().numpy(), t.energy.value, np.array(t.virial[:]), exact=True)
     finally:
         pme.pme_server_destroy(srv)
+
+
+def _shaped_systems(pme, specs, seed0):
+    """Water-like boxes with the given (n, K, p); rectangular cells so every mesh spacing is about 1 A."""
+    dev = torch.device("cuda:0")
+    out = []
+    for i, (n, K, p) in enumerate(specs):
+        L = np.array(K, dtype=float) * 1.05
+        pos, q = wl.water_box(n, float(L.min()), seed0 + i)
+        pos = (pos / float(L.min()) * L).astype(np.float32)  # stretch the cubic box onto the cell
+        box = np.diag(L)
+        plan = pme.pme_create(K, p, 0.34, box)
+        P = torch.from_numpy(pos).to(dev)
+        Q = torch.from_numpy(q).to(dev)
+        F = torch.empty_like(P)
+        E, V = pme.pme_compute(plan, P, Q, F)
+        out.append(dict(sys=wl.System(pos, q, box, K, p, 0.34), plan=plan, pos=P, q=Q, F=F.cpu().numpy(), E=E, V=V))
+    return out
+
+
+def test_batch_mixed_shapes_bit_identical(pme, oracle_mod):
+    """Groups of equal and unequal mesh shapes, including lengths without a register plan (30, 36, 50, 54)
+    and non-cubic meshes, which run the general kernels: every system equals its single evaluation bit for
+    bit, repeatedly."""
+    specs = [(3000, (32, 32, 32), 6), (2500, (32, 32, 32), 6), (4000, (30, 36, 40), 6), (3500, (30, 36, 40), 6),
+             (5000, (50, 54, 48), 6), (2000, (24, 24, 24), 6), (6000, (40, 40, 40), 6)]
+    syst = _shaped_systems(pme, specs, 300)
+    try:
+        pos, q, ns = packed(syst)
+        F = torch.full_like(pos, float("nan"))
+        ev = torch.zeros((len(syst), 7), dtype=torch.float64, device="cuda:0")
+        b = pme.pme_batch_create([o["plan"] for o in syst], ns)
+        try:
+            for _ in range(2):
+                pme.pme_batch_enqueue(b, pos, q, F, ev)
+                pme.pme_batch_sync(b)
+                Fh, evh = F.cpu().numpy(), ev.cpu().numpy()
+                off = 0
+                for i, o in enumerate(syst):
+                    check_same(o, Fh[off:off + ns[i]], evh[i, 0], evh[i, 1:], exact=True)
+                    off += ns[i]
+        finally:
+            pme.pme_batch_destroy(b)
+        s = syst[4]["sys"]  # a shape on the general path, against the oracle
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
+        assert rel_energy(syst[4]["E"], r["energy"]) < E_REL_TOL
+        assert rms_force(syst[4]["F"], r["forces"]) < F_RMS_TOL
+    finally:
+        for o in syst:
+            pme.pme_destroy(o["plan"])
+
+
+def test_server_mixed_orders_and_shapes(pme):
+    """Waves that mix B-spline orders and mesh shapes (each shape a group of its own): every result equals
+    the system's single evaluation bit for bit."""
+    specs = [(3000, (32, 32, 32), 4), (3000, (32, 32, 32), 6), (2500, (24, 30, 36), 8), (4000, (40, 40, 40), 4),
+             (3500, (36, 36, 36), 6)]
+    syst = _shaped_systems(pme, specs, 400)
+    srv = pme.pme_server_create(1 << 34, 64)
+    try:
+        tickets = []
+        for rep in range(3):
+            for o in syst:
+                F = torch.full_like(o["pos"], float("nan"))
+                t = pme.pme_submit(srv, o["plan"], o["pos"], o["q"], F)
+                assert t is not None
+                tickets.append((o, F, t))
+        for o, F, t in tickets:
+            assert pme.pme_poll(srv, t, block=True) == pme.PME_OK
+            check_same(o, F.cpu().numpy(), t.energy.value, np.array(t.virial[:]), exact=True)
+    finally:
+        pme.pme_server_destroy(srv)
+        for o in syst:
+            pme.pme_destroy(o["plan"])
