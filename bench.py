@@ -312,10 +312,11 @@ def run_ours(args, dist: Dist):
         sampler.window(t0, time.time())
     result["config"]["eager_us_per_eval"] = round(1000.0 * start.elapsed_time(end) / ne, 3)
 
-    # launch-mode sweep: plain launches and programmatic dependent launch triggered early, same frames, fresh
-    # graphs (the headline above uses the default, late trigger)
+    # launch-mode sweep: plain launches and programmatic dependent launch triggered at kernel start or right
+    # after each kernel's own wait, same frames, fresh graphs (the headline above uses the default, triggered
+    # at CTA exit)
     modes = {}
-    for mode in (0, 1):
+    for mode in (0, 1, 3):
         pme.pme_set_launch_mode(mode)
         gm = []
         with torch.cuda.stream(stream):
@@ -333,7 +334,8 @@ def run_ours(args, dist: Dist):
                 gm[i % 100].replay()
             end.record(stream)
             torch.cuda.synchronize(dev)
-        modes[f"{'pdl_early' if mode == 1 else 'plain_launch'}_us_per_eval"] = round(1000.0 * start.elapsed_time(end) / nm, 3)
+        name = {0: "plain_launch", 1: "pdl_early", 3: "pdl_after_wait"}[mode]
+        modes[f"{name}_us_per_eval"] = round(1000.0 * start.elapsed_time(end) / nm, 3)
         del gm
     pme.pme_set_launch_mode(2)  # the library default
     pme.pme_sync(plan)

@@ -23,7 +23,7 @@ __device__ __forceinline__ int group_load(const GroupArgs &a, SysDev &sd) {
 __global__ void __launch_bounds__(NT_BIN) k_bin_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    PdlScope pdl(a.late != 0);
+    PdlScope pdl(a.late);
     const int item = group_load(a, sd);
     if (item < sd.nbin) stage_bin(sd, item, smem);
 }
@@ -32,7 +32,7 @@ template <int P>
 __global__ void __launch_bounds__(NT_TILE) k_spread_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    PdlScope pdl(a.late != 0);
+    PdlScope pdl(a.late);
     const int item = group_load(a, sd);
     stage_spread<P, 8>(sd, item, smem);
 }
@@ -41,7 +41,7 @@ template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_fwd_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    PdlScope pdl(a.late != 0);
+    PdlScope pdl(a.late);
     const int item = group_load(a, sd);
     stage_fwd<PR, PC>(sd, item, smem);
 }
@@ -50,7 +50,7 @@ template <int P1>
 __global__ void __launch_bounds__(NT_CONV) k_conv_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    PdlScope pdl(a.late != 0);
+    PdlScope pdl(a.late);
     const int item = group_load(a, sd);
     stage_conv<P1>(sd, item, smem);
 }
@@ -59,7 +59,7 @@ template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_inv_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    PdlScope pdl(a.late != 0);
+    PdlScope pdl(a.late);
     const int item = group_load(a, sd);
     stage_inv<PR, PC>(sd, item, smem);
 }
@@ -68,7 +68,7 @@ template <int P>
 __global__ void __launch_bounds__(NT_TILE) k_gather_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    PdlScope pdl(a.late != 0);
+    PdlScope pdl(a.late);
     const int item = group_load(a, sd);
     stage_gather<P, 8>(sd, item, smem);
 }
@@ -156,7 +156,7 @@ static void (*conv_g(const SysDev &d))(GroupArgs) {
 cudaError_t launch_group_chain(const SysDev *sys_dev, int nsys, const SysDev &proto, int max_nbin, cudaStream_t s) {
     GroupArgs a;
     a.sys = sys_dev;
-    a.late = launch_mode() == 2 ? 1 : 0;
+    a.late = pdl_when(launch_mode());
     const SysDev &d = proto;
     cudaError_t e;
     for (int stage = 0; stage < NUM_STAGES; ++stage) {

@@ -11,7 +11,7 @@ namespace pme {
 struct GroupArgs {
     const SysDev *sys;  // the group's descriptors (device memory, nsys entries)
     int ips;            // work items per system of the launched stage
-    int late;           // programmatic launch triggered at CTA exit
+    int late;           // when the programmatic launch of the successor is triggered (PdlScope)
 };
 
 // Raise the dynamic shared-memory limits of the grouped kernels (once per device).

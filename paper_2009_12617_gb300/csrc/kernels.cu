@@ -11,35 +11,36 @@ namespace pme {
 static int g_launch_mode = 2;  // measured fastest on GB300 (late trigger)
 void set_launch_mode(int mode) { g_launch_mode = mode; }
 int launch_mode() { return g_launch_mode; }
+int pdl_when(int mode) { return mode == 1 ? 0 : (mode == 3 ? 2 : 1); }
 
 __global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_bin(d, blockIdx.x, smem);
 }
 
 template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_spread<P, T>(d, blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_SLAB) k_fwd(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_fwd(d, blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_CONV) k_conv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_conv(d, blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_inv(d, blockIdx.x, smem);
 }
 
@@ -50,35 +51,35 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
 template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_fwd_p(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_fwd<PR, PC>(d, blockIdx.x, smem);
 }
 
 template <int P1>
 __global__ void __launch_bounds__(NT_CONV) k_conv_p(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_conv<P1>(d, blockIdx.x, smem);
 }
 
 template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_inv_p(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_inv<PR, PC>(d, blockIdx.x, smem);
 }
 
 template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PdlScope pdl(d.pdl_late != 0);
+    PdlScope pdl(d.pdl_late);
     stage_gather<P, T>(d, blockIdx.x, smem);
 }
 
 static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
                        const SysDev &d0) {
     SysDev d = d0;
-    d.pdl_late = g_launch_mode == 2 ? 1 : 0;
+    d.pdl_late = pdl_when(g_launch_mode);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);

@@ -28,9 +28,12 @@ struct Cubic {
 };
 
 // Launch mode of the per-stage kernels: 0 plain, 1 programmatic dependent launch triggered at kernel entry,
-// 2 triggered at CTA exit. Process-wide; affects launches recorded afterwards.
+// 2 triggered at CTA exit, 3 triggered right after the kernel's own wait. Process-wide; affects launches
+// recorded afterwards.
 void set_launch_mode(int mode);
 int launch_mode();
+// The PdlScope argument of launch mode `mode`.
+int pdl_when(int mode);
 
 // Raise the dynamic shared-memory limit of the large-footprint kernels (once per device).
 cudaError_t configure_kernels();

@@ -493,7 +493,7 @@ pme_status pme_profile_stages(pme_plan *pl, const float *pos, const float *q, in
 }
 
 pme_status pme_set_launch_mode(int mode) {
-    if (mode < 0 || mode > 2) return fail(PME_EINVAL, "launch mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(PME_EINVAL, "launch mode must be 0, 1, 2 or 3");
     set_launch_mode(mode);
     return PME_OK;
 }
