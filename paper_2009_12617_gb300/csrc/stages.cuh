@@ -31,6 +31,22 @@ struct Region {
     static constexpr int VOL = R * R * R;
 };
 
+// Spreading region layout: planes of R x R points padded to PL so that the two half-support lanes of an
+// atom ((P/2) planes apart) sit 16 banks apart: (P/2) PL = 16 (mod 32). Then the 32 lanes of a warp (16
+// atoms x 2 halves) hit distinct banks whenever the atoms' base addresses differ mod 16, which the dealt
+// processing order (stage_spread) arranges.
+constexpr int spread_plane(int R, int P) {
+    int pl = R * R;
+    while (((P / 2) * pl) % 32 != 16) ++pl;
+    return pl;
+}
+template <int P, int T>
+struct SpreadLayout {
+    static constexpr int R = T + P - 1;
+    static constexpr int PL = spread_plane(R, P);
+    static constexpr int VOLP = R * PL;
+};
+
 // ---------------------------------------------------------------------------------------------------------
 // shared-memory sizes (bytes) of each stage for a given system and block size
 
@@ -39,7 +55,12 @@ inline size_t smem_tile_region(int p, int tlog) {
     const size_t r = (size_t)(1 << tlog) + p - 1;
     return r * r * r;
 }
-inline size_t smem_spread(int p, int tlog) { return smem_tile_region(p, tlog) * 2 * sizeof(int); }
+// split accumulators over the padded region (2 x R PL ints), the tile's records (CAP_MAX x (float4 + int2)),
+// the dealt order's keys and inverse (CAP_MAX ints each) and 16 residue counters
+inline size_t smem_spread(int p, int tlog) {
+    const int r = (1 << tlog) + p - 1;
+    return (size_t)2 * r * spread_plane(r, p) * sizeof(int) + (size_t)CAP_MAX * (16 + 8 + 4 + 4) + 16 * sizeof(unsigned);
+}
 inline size_t smem_gather(int p, int tlog) { return smem_tile_region(p, tlog) * sizeof(float); }
 // Two K2 x H3 buffers (the register path uses one, with rows padded by up to 15), then the twiddles.
 inline size_t smem_slab(int K2, int K3) {
@@ -231,30 +252,58 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
             spread_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
         return;
     }
-    constexpr int R = Region<P, T>::R, VOL = Region<P, T>::VOL, H = P - 1;
+    constexpr int R = SpreadLayout<P, T>::R, PL = SpreadLayout<P, T>::PL, VOLP = SpreadLayout<P, T>::VOLP, H = P - 1;
     int *hi = (int *)smem;
-    int *lo = hi + VOL;
+    int *lo = hi + VOLP;
+    float4 *ra_s = (float4 *)(lo + VOLP);  // the tile's records (16-byte aligned: VOLP is even)
+    int2 *rb_s = (int2 *)(ra_s + CAP_MAX);
+    int *key_s = (int *)(rb_s + CAP_MAX);   // per atom: rank << 4 | residue
+    int *inv_s = key_s + CAP_MAX;           // dealt position -> atom
+    unsigned *bins = (unsigned *)(inv_s + CAP_MAX);  // 16 residue counters
     int o1, o2, o3;
     tile_origin(d, item, o1, o2, o3);
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
-    // the count and this thread's first record are loaded together (the record slot is always inside the
-    // bucket; it is used only if it holds an atom)
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
-    const int a0 = imin(tid >> 1, d.cap - 1);
-    const float4 ra0 = ldcg(A + a0);
-    const int2 rb0 = ldcg(B + a0);
-    for (int i = tid; i < VOL; i += nth) {
+    for (int i = tid; i < 16; i += nth) bins[i] = 0u;
+    for (int i = tid; i < VOLP; i += nth) {
         hi[i] = 0;
         lo[i] = 0;
     }
     PME_SYNC();
+    // Dealt order: residue r = (base mod 16) of the atom's highest support point in the padded region;
+    // round k takes the k-th atom of every residue in turn, so 16 consecutive atoms (one warp) mostly have
+    // distinct residues and their shared-memory atomics do not share banks. Results do not depend on the
+    // order (integer sums).
+    for (int a = tid; a < cnt; a += nth) {
+        const float4 ra = ldcg(A + a);
+        const int2 rb = ldcg(B + a);
+        ra_s[a] = ra;
+        rb_s[a] = rb;
+        const int l1 = (rb.x & 1023) - o1 + H, l2 = ((rb.x >> 10) & 1023) - o2 + H, l3 = ((rb.x >> 20) & 1023) - o3 + H;
+        const int res = (l1 * PL + l2 * R + l3) & 15;
+        key_s[a] = ((int)atomic_add_u32(bins + res, 1u) << 4) | res;
+    }
+    PME_SYNC();
+    {
+        unsigned nb[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) nb[b] = bins[b];
+        for (int a = tid; a < cnt; a += nth) {
+            const int key = key_s[a], res = key & 15;
+            const unsigned rk = (unsigned)(key >> 4);
+            unsigned pos = 0;
+#pragma unroll
+            for (int b = 0; b < 16; ++b) pos += (nb[b] < rk ? nb[b] : rk) + ((b < res && nb[b] > rk) ? 1u : 0u);
+            inv_s[pos] = a;
+        }
+    }
+    PME_SYNC();
     // two threads per atom: half h takes the planes j1 in [h P/2, (h + 1) P/2)
     for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
-        const int a = a2 >> 1, half = a2 & 1;
-        const bool first = a2 == tid;
-        const float4 ra = first ? ra0 : ldcg(A + a);
-        const int2 rb = first ? rb0 : ldcg(B + a);
+        const int a = inv_s[a2 >> 1], half = a2 & 1;
+        const float4 ra = ra_s[a];
+        const int2 rb = rb_s[a];
         float th1[P], th2[P], th3[P];
         bspline_w<P>(ra.x, th1);
         bspline_w<P>(ra.y, th2);
@@ -270,7 +319,7 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
                 const float c = ra.w * t1 * th2[j2];
-                const int row = ((l1 - j1) * R + (l2 - j2)) * R + l3;
+                const int row = (l1 - j1) * PL + (l2 - j2) * R + l3;
 #pragma unroll
                 for (int j3 = 0; j3 < P; ++j3) {
                     int h, l;
@@ -282,10 +331,12 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
         }
     }
     PME_SYNC();
-    for (int i = tid; i < VOL; i += nth) {
+    for (int i = tid; i < VOLP; i += nth) {
+        const int i1 = i / PL, rem = i - i1 * PL;
+        if (rem >= R * R) continue;  // plane padding
         const int h = hi[i], l = lo[i];
         if ((h | l) == 0) continue;
-        const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
+        const int i2 = rem / R, i3 = rem - i2 * R;
         const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
         red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
     }
