@@ -331,14 +331,20 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
         }
     }
     PME_SYNC();
-    for (int i = tid; i < VOLP; i += nth) {
-        const int i1 = i / PL, rem = i - i1 * PL;
-        if (rem >= R * R) continue;  // plane padding
-        const int h = hi[i], l = lo[i];
-        if ((h | l) == 0) continue;
-        const int i2 = rem / R, i3 = rem - i2 * R;
-        const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
-        red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
+    // flush: thread t < ng R adds point i3 = t mod R of rows t / R, t / R + ng, ... (as the force stage's
+    // region load)
+    const int ng = nth >= R ? nth / R : 1, rg = nth >= R ? tid / R : 0;
+    for (int i3 = nth >= R ? tid - rg * R : 0; i3 < R; i3 += (nth >= R ? R : 1)) {
+        if (rg >= ng) break;
+        const int k3 = wrapk(o3 - H + i3, d.K3);
+        for (int r = rg; r < R * R; r += ng) {
+            const int i1 = r / R, i2 = r - i1 * R;
+            const int i = i1 * PL + i2 * R + i3;
+            const int h = hi[i], l = lo[i];
+            if ((h | l) == 0) continue;
+            const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2);
+            red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
+        }
     }
 }
 
@@ -1115,20 +1121,34 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         const int a0 = imin(tid >> 1, d.cap - 1);
         const float4 ra0 = ldcg(A + a0);
         const int2 rb0 = ldcg(B + a0);
-        for (int base = tid; base < VOL; base += LOAD_BATCH * nth) {
-            float v[LOAD_BATCH];
+        if (nth >= R) {
+            // thread t < ng R loads point i3 = t mod R of rows t / R, t / R + ng, ... (ng = nth / R row
+            // groups): the k3 index is computed once, each row costs two wraps
+            const int ng = nth / R, rg = tid / R, i3 = tid - rg * R;
+            if (rg < ng) {
+                const int k3 = wrapk(o3 - H + i3, d.K3);
+                for (int r0 = rg; r0 < R * R; r0 += LOAD_BATCH * ng) {
+                    float v[LOAD_BATCH];
 #pragma unroll
-            for (int u = 0; u < LOAD_BATCH; ++u) {
-                const int i = base + u * nth;
-                if (i < VOL) {
-                    const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
-                    const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
-                    v[u] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
+                    for (int u = 0; u < LOAD_BATCH; ++u) {
+                        const int r = r0 + u * ng;
+                        if (r < R * R) {
+                            const int i1 = r / R, i2 = r - i1 * R;
+                            const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2);
+                            v[u] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < LOAD_BATCH; ++u)
+                        if (r0 + u * ng < R * R) reg[(r0 + u * ng) * R + i3] = v[u];
                 }
             }
-#pragma unroll
-            for (int u = 0; u < LOAD_BATCH; ++u)
-                if (base + u * nth < VOL) reg[base + u * nth] = v[u];
+        } else {
+            for (int i = tid; i < VOL; i += nth) {
+                const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
+                const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
+                reg[i] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
+            }
         }
         PME_SYNC();
         if (tid == 0) d.bcount[(size_t)item * BCOUNT_STRIDE] = 0u;  // consumed: ready for the next binning
