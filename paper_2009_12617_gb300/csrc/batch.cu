@@ -479,8 +479,9 @@ pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, 
             return fail(PME_EINVAL, "system %d: NULL plan or n out of range", s);
         }
         if (pl->dev != b->dev) {
+            const int bdev = b->dev;
             delete b;
-            return fail(PME_EINVAL, "system %d: plan lives on device %d, batch on %d", s, pl->dev, b->dev);
+            return fail(PME_EINVAL, "system %d: plan lives on device %d, batch on %d", s, pl->dev, bdev);
         }
         if (pl->p != plans[0]->p) {
             delete b;
