@@ -99,11 +99,12 @@ PME_HD int slab_lane_plan(int N, int ntr) {
 }
 
 // Plan of the influence stage's K1-point transforms: the fewest points per lane, so that the work spreads
-// over as many threads as possible.
+// over as many threads as possible, with at most 16 lanes per transform so that a warp spans at least two
+// adjacent columns (its loads along k1 then use whole 16-byte pieces of each row).
 PME_HD int conv_lane_plan(int N) {
     int best = -1;
     for (int c = 0; c < LANE_PLANS; ++c)
-        if (plan_L(c) * plan_E(c) == N && (best < 0 || plan_E(c) < plan_E(best))) best = c;
+        if (plan_L(c) * plan_E(c) == N && plan_L(c) <= 16 && (best < 0 || plan_E(c) < plan_E(best))) best = c;
     return best;
 }
 // Independent global loads each thread keeps in flight when staging data into shared memory.
