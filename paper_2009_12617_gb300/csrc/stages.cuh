@@ -95,9 +95,9 @@ PME_DEV void copy_batched(T *dst, const T *src, int n) {
 }
 
 // ---------------------------------------------------------------------------------------------------------
-// 64-bit fixed point (scale 2^40) as (hi, lo): v ~ hi * 2^20 + lo with lo in [0, 2^20]. The split is a
-// deterministic function of the float v, used identically by the shared-memory and the global paths, so
-// the mesh does not depend on which path an atom takes.
+// 64-bit fixed point (scale 2^40) as (hi, lo): rn(v) = hi * 2^20 + lo with lo in [-2^19, 2^19]. The split is
+// a deterministic function of the float v, and the global path adds the same integer rn(v) in one 64-bit
+// step, so the mesh does not depend on which path an atom takes.
 
 PME_DEV void fix_split(float v, int &h, int &l) {
     // Round-to-nearest by the float magic number M = 1.5 * 2^23: for |x| < 2^22, x + M carries
