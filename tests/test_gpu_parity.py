@@ -72,7 +72,7 @@ SHAPES = [((8, 10, 12), 4), ((16, 18, 20), 6), ((24, 30, 32), 8), ((36, 40, 48),
 @pytest.mark.parametrize("K,p", SHAPES, ids=[f"{K[0]}x{K[1]}x{K[2]}_p{p}" for K, p in SHAPES])
 def test_parity_mesh_shapes(pmelib, oracle_mod, K, p):
     """Every radix-2/3/5 length from 8 to 128 in some dimension, ragged tiles, orders 4, 6 and 8; register
-    and shared-memory transform paths, with and without the staged inverse plane (K2 (K3/2 + 1) >= 4096)."""
+    (lane-plan) and shared-memory transform paths, specialised and general kernels."""
     L = np.array(K, dtype=float) * 1.1
     box = np.diag(L)
     n = 3000
