@@ -123,8 +123,9 @@ pme_status pme_profile_stages(pme_plan *plan, const float *pos, const float *q, 
 
 /* Launch option of the stage kernels (process-wide, for launches issued afterwards): 0 = plain stream
  * order; 1 = programmatic dependent launch, each kernel letting its successor launch as soon as it starts;
- * 2 (default) = the same, released as each CTA finishes; 3 = released right after each CTA's own wait for
- * its predecessor. Every kernel still waits for its predecessor to complete before touching data, so
+ * 2 (default) = the same, released as each CTA finishes (the influence stage releases the inverse FFT
+ * stage right after its own wait, which measured faster); 3 = released right after each CTA's own wait
+ * for its predecessor. Every kernel still waits for its predecessor to complete before touching data, so
  * results are identical in all modes; only launch latency overlap differs. Returns PME_EINVAL for other
  * values. */
 pme_status pme_set_launch_mode(int mode);

@@ -156,10 +156,10 @@ static void (*conv_g(const SysDev &d))(GroupArgs) {
 cudaError_t launch_group_chain(const SysDev *sys_dev, int nsys, const SysDev &proto, int max_nbin, cudaStream_t s) {
     GroupArgs a;
     a.sys = sys_dev;
-    a.late = pdl_when(launch_mode());
     const SysDev &d = proto;
     cudaError_t e;
     for (int stage = 0; stage < NUM_STAGES; ++stage) {
+        a.late = pdl_when(launch_mode(), stage);
         a.ips = stage == STAGE_BIN ? (max_nbin > 0 ? max_nbin : 1) : group_items(d, stage);
         const unsigned grid = (unsigned)(a.ips * nsys);
         switch (stage) {

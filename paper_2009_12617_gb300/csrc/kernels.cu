@@ -11,7 +11,7 @@ namespace pme {
 static int g_launch_mode = 2;  // measured fastest on GB300 (late trigger)
 void set_launch_mode(int mode) { g_launch_mode = mode; }
 int launch_mode() { return g_launch_mode; }
-int pdl_when(int mode) { return mode == 1 ? 0 : (mode == 3 ? 2 : 1); }
+int pdl_when(int mode, int stage) { return mode == 1 ? 0 : (mode == 3 || stage == STAGE_CONV ? 2 : 1); }
 
 __global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
 }
 
 static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
-                       const SysDev &d0) {
+                       const SysDev &d0, int stage) {
     SysDev d = d0;
-    d.pdl_late = pdl_when(g_launch_mode);
+    d.pdl_late = pdl_when(g_launch_mode, stage);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -151,20 +151,20 @@ static void (*conv_kernel(const SysDev &d))(SysDev) {
 template <int P>
 static void launch_tiles_spread(const SysDev &d, cudaStream_t s) {
     const unsigned nt = (unsigned)tile_threads(d, d.n);
-    if (d.tlog == 4) launch_pdl(k_spread<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_spread(P, 4), s, d);
-    else launch_pdl(k_spread<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_spread(P, 3), s, d);
+    if (d.tlog == 4) launch_pdl(k_spread<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_spread(P, 4), s, d, STAGE_SPREAD);
+    else launch_pdl(k_spread<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_spread(P, 3), s, d, STAGE_SPREAD);
 }
 template <int P>
 static void launch_tiles_gather(const SysDev &d, cudaStream_t s) {
     const unsigned nt = (unsigned)tile_threads(d, d.n);
-    if (d.tlog == 4) launch_pdl(k_gather<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 4), s, d);
-    else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 3), s, d);
+    if (d.tlog == 4) launch_pdl(k_gather<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 4), s, d, STAGE_GATHER);
+    else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 3), s, d, STAGE_GATHER);
 }
 
 void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
     switch (stage) {
         case STAGE_BIN:
-            launch_pdl(k_bin, d.nbin > 0 ? d.nbin : 1, NT_BIN, smem_bin(NT_BIN), s, d);
+            launch_pdl(k_bin, d.nbin > 0 ? d.nbin : 1, NT_BIN, smem_bin(NT_BIN), s, d, STAGE_BIN);
             break;
         case STAGE_SPREAD:
             if (d.p == 4) launch_tiles_spread<4>(d, s);
@@ -172,13 +172,13 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             else launch_tiles_spread<8>(d, s);
             break;
         case STAGE_FWD:
-            launch_pdl(fwd_kernel(d), d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d);
+            launch_pdl(fwd_kernel(d), d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d, STAGE_FWD);
             break;
         case STAGE_CONV:
-            launch_pdl(conv_kernel(d), d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d);
+            launch_pdl(conv_kernel(d), d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d, STAGE_CONV);
             break;
         case STAGE_INV:
-            launch_pdl(inv_kernel(d), d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d);
+            launch_pdl(inv_kernel(d), d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d, STAGE_INV);
             break;
         default:
             if (d.p == 4) launch_tiles_gather<4>(d, s);

@@ -28,12 +28,15 @@ struct Cubic {
 };
 
 // Launch mode of the per-stage kernels: 0 plain, 1 programmatic dependent launch triggered at kernel entry,
-// 2 triggered at CTA exit, 3 triggered right after the kernel's own wait. Process-wide; affects launches
-// recorded afterwards.
+// 2 triggered at CTA exit (the influence stage: right after its own wait), 3 triggered right after the
+// kernel's own wait. Process-wide; affects launches recorded afterwards.
 void set_launch_mode(int mode);
 int launch_mode();
-// The PdlScope argument of launch mode `mode`.
-int pdl_when(int mode);
+// The PdlScope argument of a kernel of stage `stage` in launch mode `mode`. In mode 2 the influence stage
+// releases the inverse stage early: the inverse stage's K1 slab CTAs fit beside the influence CTAs and
+// become resident during them (measured 30.6 vs 31.1 us per 64^3 evaluation); released early, the other
+// stages' successors were slower or no faster (their CTAs then land unevenly on the SMs).
+int pdl_when(int mode, int stage);
 
 // Raise the dynamic shared-memory limit of the large-footprint kernels (once per device).
 cudaError_t configure_kernels();
