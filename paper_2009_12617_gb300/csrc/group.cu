@@ -32,9 +32,10 @@ template <int P>
 __global__ void __launch_bounds__(NT_TILE) k_spread_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
+    spread_clear<P, 8>(smem);  // before the wait: shared memory only
     PdlScope pdl(a.late);
     const int item = group_load(a, sd);
-    stage_spread<P, 8>(sd, item, smem);
+    stage_spread<P, 8>(sd, item, smem, true);
 }
 
 template <int PR, int PC>

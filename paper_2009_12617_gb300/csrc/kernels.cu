@@ -22,8 +22,9 @@ __global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
 template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    spread_clear<P, T>(smem);  // before the wait: shared memory only
     PdlScope pdl(d.pdl_late);
-    stage_spread<P, T>(d, blockIdx.x, smem);
+    stage_spread<P, T>(d, blockIdx.x, smem, true);
 }
 
 __global__ void __launch_bounds__(NT_SLAB) k_fwd(SysDev d) {

@@ -241,8 +241,43 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
     }
 }
 
+// Shared memory of a spreading tile (sizes as smem_spread): split accumulators over the padded region, the
+// tile's records, the dealt order's keys and inverse, and 16 residue counters.
 template <int P, int T>
-PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
+struct SpreadSmem {
+    static constexpr int VOLP = SpreadLayout<P, T>::VOLP;
+    int *hi, *lo;
+    float4 *ra_s;    // the tile's records (16-byte aligned: VOLP is even)
+    int2 *rb_s;
+    int *key_s;      // per atom: rank << 4 | residue
+    int *inv_s;      // dealt position -> atom
+    unsigned *bins;  // 16 residue counters
+    PME_DEV explicit SpreadSmem(void *smem) {
+        hi = (int *)smem;
+        lo = hi + VOLP;
+        ra_s = (float4 *)(lo + VOLP);
+        rb_s = (int2 *)(ra_s + CAP_MAX);
+        key_s = (int *)(rb_s + CAP_MAX);
+        inv_s = key_s + CAP_MAX;
+        bins = (unsigned *)(inv_s + CAP_MAX);
+    }
+};
+
+// Zero the accumulators and residue counters. It touches no global memory, so the stage kernel runs it
+// before waiting for its predecessor (inside the launch window of programmatic dependent launch).
+template <int P, int T>
+PME_DEV void spread_clear(void *smem) {
+    const SpreadSmem<P, T> s(smem);
+    for (int i = PME_TID; i < 16; i += PME_NTH) s.bins[i] = 0u;
+    for (int i = PME_TID; i < SpreadSmem<P, T>::VOLP; i += PME_NTH) {
+        s.hi[i] = 0;
+        s.lo[i] = 0;
+    }
+}
+
+// cleared: spread_clear already ran on this shared memory (and nothing has used it since).
+template <int P, int T>
+PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = false) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {  // bucket-overflow atoms, straight to the global mesh
         const unsigned novf = imin((int)ldcg(&d.ctl->novf), d.n);
@@ -252,24 +287,18 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem) {
             spread_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
         return;
     }
-    constexpr int R = SpreadLayout<P, T>::R, PL = SpreadLayout<P, T>::PL, VOLP = SpreadLayout<P, T>::VOLP, H = P - 1;
-    int *hi = (int *)smem;
-    int *lo = hi + VOLP;
-    float4 *ra_s = (float4 *)(lo + VOLP);  // the tile's records (16-byte aligned: VOLP is even)
-    int2 *rb_s = (int2 *)(ra_s + CAP_MAX);
-    int *key_s = (int *)(rb_s + CAP_MAX);   // per atom: rank << 4 | residue
-    int *inv_s = key_s + CAP_MAX;           // dealt position -> atom
-    unsigned *bins = (unsigned *)(inv_s + CAP_MAX);  // 16 residue counters
+    constexpr int R = SpreadLayout<P, T>::R, PL = SpreadLayout<P, T>::PL, H = P - 1;
+    const SpreadSmem<P, T> sm(smem);
+    int *hi = sm.hi, *lo = sm.lo, *key_s = sm.key_s, *inv_s = sm.inv_s;
+    float4 *ra_s = sm.ra_s;
+    int2 *rb_s = sm.rb_s;
+    unsigned *bins = sm.bins;
     int o1, o2, o3;
     tile_origin(d, item, o1, o2, o3);
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
-    for (int i = tid; i < 16; i += nth) bins[i] = 0u;
-    for (int i = tid; i < VOLP; i += nth) {
-        hi[i] = 0;
-        lo[i] = 0;
-    }
+    if (!cleared) spread_clear<P, T>(smem);
     PME_SYNC();
     // Dealt order: residue r = (base mod 16) of the atom's highest support point in the padded region;
     // round k takes the k-th atom of every residue in turn, so 16 consecutive atoms (one warp) mostly have
