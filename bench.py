@@ -289,7 +289,8 @@ def run_ours(args, dist: Dist):
                    "l2": "inputs larger than L2: 1000 distinct position frames (786 MB) cycled; mesh and tables "
                          "stay L2-resident by design",
                    "launch": "CUDA graphs of ten consecutive frames (60 kernels, programmatic dependent launch "
-                             "released at CTA exit), replayed back to back; exactly `steps` evaluations",
+                             "released at CTA exit, the influence stage's successor right after its wait), "
+                             "replayed back to back; exactly `steps` evaluations",
                    "evals_per_s": round(1e6 / value, 1)},
         "gpu_launches": 6 * args.steps,
     }
@@ -314,7 +315,7 @@ def run_ours(args, dist: Dist):
 
     # launch-mode sweep: plain launches and programmatic dependent launch triggered at kernel start or right
     # after each kernel's own wait, same frames, fresh graphs (the headline above uses the default, triggered
-    # at CTA exit)
+    # at CTA exit except after the influence stage's wait)
     modes = {}
     for mode in (0, 1, 3):
         pme.pme_set_launch_mode(mode)

@@ -214,7 +214,8 @@ def pme_profile_stages(plan: int, pos, q, forces, reps: int = 10) -> dict:
 
 
 def pme_set_launch_mode(mode: int) -> None:
-    """0 plain, 1 programmatic dependent launch triggered at kernel entry, 2 triggered at CTA exit."""
+    """0 plain; programmatic dependent launch triggered 1 at kernel entry, 2 (default) at CTA exit (the influence
+    stage: right after its own wait), 3 right after each kernel's own wait."""
     check(load_library().pme_set_launch_mode(int(mode)))
 
 
