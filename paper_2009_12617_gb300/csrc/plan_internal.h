@@ -24,6 +24,7 @@ struct pme_plan {
     void *host_mem = nullptr;       // device staging for pme_compute_host
     int64_t host_cap = 0;
     pme::Ctl *h_ctl = nullptr;      // pinned host copy of the control block
+    pme::Ctl *h_ctl_dev = nullptr;  // its device-side (mapped) address, or null
     unsigned long long gen = 0;     // bumped whenever the kernels' arguments change (box)
     // Repeated synchronous calls replay a CUDA graph of the whole call, recorded (on a private stream, as
     // the plan stream may not be capturable) once the same arguments come twice in a row: one for device
