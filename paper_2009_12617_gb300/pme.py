@@ -7,8 +7,10 @@ There is no CPU fallback: if the library is missing, loading it raises.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import os
+import threading
 
 import numpy as np
 
@@ -48,6 +50,41 @@ _i64 = ctypes.c_int64
 _st = ctypes.c_int
 
 
+class _AddressCache:
+    """Data addresses of the last few numpy arrays the binding was given. Reading ``a.ctypes.data`` costs about a
+    microsecond; a loop that passes the same buffers every step finds them here. Each entry holds its array, so
+    its id cannot be taken by another object while it is cached."""
+
+    def __init__(self, size: int = 8):
+        self._items: collections.OrderedDict = collections.OrderedDict()
+        self._size = size
+        self._lock = threading.Lock()
+
+    def __call__(self, a: np.ndarray) -> int:
+        with self._lock:
+            hit = self._items.get(id(a))
+            if hit is not None and hit[0] is a:
+                return hit[1]
+            p = a.ctypes.data
+            self._items[id(a)] = (a, p)
+            while len(self._items) > self._size:
+                self._items.popitem(last=False)
+            return p
+
+
+_addr = _AddressCache()
+_tls = threading.local()
+
+
+def _result_buffer():
+    """This thread's 7 doubles receiving energy and virial, and their address."""
+    b = getattr(_tls, "ev", None)
+    if b is None:
+        arr = np.zeros(7)
+        b = _tls.ev = (arr, arr.ctypes.data)
+    return b
+
+
 def load_library(path: str | None = None):
     """Load libpme_gb300.so (built by __graft_entry__.build() / paper_2009_12617_gb300.build)."""
     global _lib
@@ -65,7 +102,7 @@ def load_library(path: str | None = None):
         "pme_enqueue": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
         "pme_reserve": (_st, [_vp, _i64]),
         "pme_sync": (_st, [_vp]),
-        "pme_compute_host": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "pme_compute_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
         "pme_profile_stages": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pme_set_launch_mode": (_st, [ctypes.c_int]),
         "pme_plan_device_bytes": (ctypes.c_size_t, [_vp]),
@@ -186,8 +223,10 @@ def pme_sync(plan: int) -> None:
 
 def pme_compute_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray | None = None):
     """Evaluation on HOST numpy arrays (float32); returns (forces, E, virial[6])."""
-    pos = np.ascontiguousarray(pos, dtype=np.float32)
-    q = np.ascontiguousarray(q, dtype=np.float32)
+    if pos.dtype != np.float32 or not pos.flags.c_contiguous:
+        pos = np.ascontiguousarray(pos, dtype=np.float32)
+    if q.dtype != np.float32 or not q.flags.c_contiguous:
+        q = np.ascontiguousarray(q, dtype=np.float32)
     n = int(q.shape[0])
     if pos.shape != (n, 3):
         raise ValueError("pos must be (n, 3)")
@@ -195,11 +234,9 @@ def pme_compute_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarr
         forces = np.empty((n, 3), dtype=np.float32)
     if forces.dtype != np.float32 or forces.shape != (n, 3) or not forces.flags.c_contiguous:
         raise ValueError("forces must be a contiguous float32 (n, 3) array")
-    e = ctypes.c_double()
-    vir = (ctypes.c_double * 6)()
-    check(load_library().pme_compute_host(_vp(plan), _vp(pos.ctypes.data), _vp(q.ctypes.data), n,
-                                          _vp(forces.ctypes.data), ctypes.byref(e), vir))
-    return forces, e.value, np.array(vir[:])
+    ev, at = _result_buffer()
+    check(load_library().pme_compute_host(plan, _addr(pos), _addr(q), n, _addr(forces), at, at + 8))
+    return forces, float(ev[0]), ev[1:].copy()
 
 
 STAGE_NAMES = ("bin", "spread", "fft_fwd", "influence", "fft_inv", "gather")
