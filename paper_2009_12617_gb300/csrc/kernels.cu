@@ -22,9 +22,12 @@ __global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
 template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
-    spread_clear<P, T>(smem);  // before the wait: shared memory only
+    // before the wait: shared memory and kernel parameters only
+    spread_clear<P, T>(smem);
+    int org[3] = {0, 0, 0};
+    if ((int)blockIdx.x < d.ntiles) tile_origin(d, blockIdx.x, org[0], org[1], org[2]);
     PdlScope pdl(d.pdl_late);
-    stage_spread<P, T>(d, blockIdx.x, smem, true);
+    stage_spread<P, T>(d, blockIdx.x, smem, true, org);
 }
 
 __global__ void __launch_bounds__(NT_SLAB) k_fwd(SysDev d) {
@@ -73,8 +76,10 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv_p(SysDev d) {
 template <int P, int T>
 __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
+    int org[3] = {0, 0, 0};  // before the wait: kernel parameters only
+    if ((int)blockIdx.x < d.ntiles) tile_origin(d, blockIdx.x, org[0], org[1], org[2]);
     PdlScope pdl(d.pdl_late);
-    stage_gather<P, T>(d, blockIdx.x, smem);
+    stage_gather<P, T>(d, blockIdx.x, smem, org);
 }
 
 static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, size_t smem, cudaStream_t s,

@@ -275,9 +275,10 @@ PME_DEV void spread_clear(void *smem) {
     }
 }
 
-// cleared: spread_clear already ran on this shared memory (and nothing has used it since).
+// cleared: spread_clear already ran on this shared memory (and nothing has used it since). org: the tile's
+// origin (tile_origin), when the caller computed it already.
 template <int P, int T>
-PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = false) {
+PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = false, const int *org = nullptr) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {  // bucket-overflow atoms, straight to the global mesh
         const unsigned novf = imin((int)ldcg(&d.ctl->novf), d.n);
@@ -294,7 +295,13 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     int2 *rb_s = sm.rb_s;
     unsigned *bins = sm.bins;
     int o1, o2, o3;
-    tile_origin(d, item, o1, o2, o3);
+    if (org) {
+        o1 = org[0];
+        o2 = org[1];
+        o3 = org[2];
+    } else {
+        tile_origin(d, item, o1, o2, o3);
+    }
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
@@ -1129,8 +1136,9 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
     force_from_grad<P>(d, ra.w, rb.y, gh[0][0] + gh[1][0], gh[0][1] + gh[1][1], gh[0][2] + gh[1][2]);
 }
 
+// org: the tile's origin (tile_origin), when the caller computed it already.
 template <int P, int T>
-PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
+PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org = nullptr) {
     const int tid = PME_TID, nth = PME_NTH;
     if (item >= d.ntiles) {
         if (item == d.ntiles) reduce_level2(d, smem);  // every inverse-slab item has finished
@@ -1141,7 +1149,13 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem) {
         constexpr int R = Region<P, T>::R, VOL = Region<P, T>::VOL, H = P - 1;
         float *reg = (float *)smem;
         int o1, o2, o3;
-        tile_origin(d, item, o1, o2, o3);
+        if (org) {
+            o1 = org[0];
+            o2 = org[1];
+            o3 = org[2];
+        } else {
+            tile_origin(d, item, o1, o2, o3);
+        }
         const float4 *A = d.bka + (size_t)item * d.cap;
         const int2 *B = d.bkb + (size_t)item * d.cap;
         // the count and this thread's first record in flight with the region loads (the record slot is
