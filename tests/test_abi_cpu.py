@@ -73,3 +73,37 @@ def test_null_arguments(lib):
     assert lib.pme_compute(None, None, None, 0, None, None, None) == pme.PME_EINVAL
     assert lib.pme_sync(None) == pme.PME_EINVAL
     lib.pme_destroy(None)
+
+
+def test_binding_address_cache():
+    """The host-array binding's address cache returns each array's own data address, evicts the oldest
+    entries beyond its size, and never answers for a different object that happens to get a cached id."""
+    cache = pme._AddressCache(size=4)
+    keep = [np.zeros((16, 3), np.float32) for _ in range(6)]
+    for a in keep:
+        assert cache(a) == a.ctypes.data
+    assert len(cache._items) == 4
+    for a in keep:  # evicted ones are recomputed, cached ones come back unchanged
+        assert cache(a) == a.ctypes.data
+    view = keep[0][2:]  # a new object over the same buffer: its own address
+    assert cache(view) == view.ctypes.data != keep[0].ctypes.data
+    b = np.zeros(8, np.float32)
+    cache(b)
+    del b
+    for _ in range(50):  # fresh objects may reuse a freed id; the identity check keeps them apart
+        c = np.ones(8, np.float32)
+        assert cache(c) == c.ctypes.data
+
+
+def test_binding_result_buffer_per_thread():
+    """Energy and virial land in a 7-double buffer owned by the calling thread."""
+    import threading
+
+    ev, at = pme._result_buffer()
+    assert ev.shape == (7,) and ev.dtype == np.float64 and at == ev.ctypes.data
+    assert pme._result_buffer()[1] == at
+    other = []
+    t = threading.Thread(target=lambda: other.append(pme._result_buffer()[1]))
+    t.start()
+    t.join()
+    assert other[0] != at
