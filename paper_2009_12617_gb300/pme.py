@@ -7,10 +7,10 @@ There is no CPU fallback: if the library is missing, loading it raises.
 """
 from __future__ import annotations
 
-import collections
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -52,24 +52,29 @@ _st = ctypes.c_int
 
 class _AddressCache:
     """Data addresses of the last few numpy arrays the binding was given. Reading ``a.ctypes.data`` costs about a
-    microsecond; a loop that passes the same buffers every step finds them here. Each entry holds its array, so
-    its id cannot be taken by another object while it is cached."""
+    microsecond; a loop that passes the same buffers every step finds them here. Entries hold weak references
+    (no caller's buffer is kept alive), and a hit needs the very same live object, so an id reused by a new
+    array is never mistaken for a cached one."""
 
     def __init__(self, size: int = 8):
-        self._items: collections.OrderedDict = collections.OrderedDict()
+        self._items: dict = {}  # id -> (weak reference, address), oldest first
         self._size = size
-        self._lock = threading.Lock()
 
     def __call__(self, a: np.ndarray) -> int:
-        with self._lock:
-            hit = self._items.get(id(a))
-            if hit is not None and hit[0] is a:
-                return hit[1]
-            p = a.ctypes.data
-            self._items[id(a)] = (a, p)
-            while len(self._items) > self._size:
-                self._items.popitem(last=False)
-            return p
+        # no lock: each dict operation is atomic under the interpreter lock, and a race costs at most a
+        # recomputed address
+        items = self._items
+        hit = items.get(id(a))
+        if hit is not None and hit[0]() is a:
+            return hit[1]
+        p = a.ctypes.data
+        items[id(a)] = (weakref.ref(a), p)
+        while len(items) > self._size:
+            try:
+                del items[next(iter(items))]
+            except (KeyError, RuntimeError, StopIteration):  # another thread changed it meanwhile
+                break
+        return p
 
 
 _addr = _AddressCache()

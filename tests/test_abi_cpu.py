@@ -87,9 +87,15 @@ def test_binding_address_cache():
         assert cache(a) == a.ctypes.data
     view = keep[0][2:]  # a new object over the same buffer: its own address
     assert cache(view) == view.ctypes.data != keep[0].ctypes.data
+    import gc
+    import weakref
+
     b = np.zeros(8, np.float32)
     cache(b)
+    wb = weakref.ref(b)
     del b
+    gc.collect()
+    assert wb() is None  # the cache does not keep a caller's array alive
     for _ in range(50):  # fresh objects may reuse a freed id; the identity check keeps them apart
         c = np.ones(8, np.float32)
         assert cache(c) == c.ctypes.data
