@@ -77,6 +77,8 @@ pme_status pme_set_box(pme_plan *plan, const double box[9]);
 
 /* One SPME evaluation, synchronous: enqueues the pipeline on the plan stream, waits for it, and returns
  * energy (host double*) and virial (host double[6]); either may be NULL. n = 0 gives energy 0, virial 0.
+ * A call with the same arrays and n as the previous one records the six stages and the kernel that writes
+ * energy, virial and status to host memory as one CUDA graph, which later identical calls replay.
  * pos, q, forces are device pointers (see conventions). The first call with a given n (or a larger n
  * than before) may allocate per-atom scratch; later calls allocate nothing. Returns PME_EINVAL for a
  * non-finite position or charge, PME_EOVERFLOW when sum |q| >= 2^22 e (the fixed-point mesh headroom);
@@ -107,10 +109,11 @@ pme_status pme_sync(pme_plan *plan);
 /* pme_compute with HOST arrays (pos, q, forces in pageable or pinned host memory): the library copies
  * inputs to its own device staging, evaluates, and copies forces back, all on the plan stream, and
  * returns when forces, energy and virial are in host memory. When all three arrays are page-locked
- * (cudaHostAlloc / cudaHostRegister), nothing is copied: the kernels read positions and charges and write
- * forces in host memory directly over the CPU-GPU link, and the first call records the six stages as one
- * CUDA graph that later calls with the same arrays and n replay (one launch per call); the arrays must then
- * stay page-locked and allocated while the plan uses them. */
+ * (cudaHostAlloc / cudaHostRegister), no copy engine is used: the binning kernel reads positions and charges
+ * in host memory over the CPU-GPU link, and one copy kernel writes the forces (from device staging) and the
+ * control block to host memory; a call with the same arrays and n as the previous one records the stages
+ * and that kernel as one CUDA graph, which later identical calls replay (one launch per call). The arrays
+ * must then stay page-locked and allocated while the plan uses them. */
 pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                             double *energy, double *virial);
 
