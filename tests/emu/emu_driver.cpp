@@ -31,6 +31,31 @@ struct EmuState {
     std::vector<unsigned char> smem;
 };
 
+// Tile items alternate between the two ways the library calls the tile bodies: as the per-stage kernels do
+// (shared memory cleared and the tile origin decoded before the programmatic-launch wait, then passed in) and
+// as the batch and allocation-free paths do (the body does both itself). Results must not depend on it.
+template <int P, int T>
+static void spread_item(const SysDev &d, int it, void *sp) {
+    if (it % 2 == 0) {
+        spread_clear<P, T>(sp);
+        int org[3] = {0, 0, 0};
+        if (it < d.ntiles) tile_origin(d, it, org[0], org[1], org[2]);
+        stage_spread<P, T>(d, it, sp, true, org);
+    } else {
+        stage_spread<P, T>(d, it, sp);
+    }
+}
+template <int P, int T>
+static void gather_item(const SysDev &d, int it, void *sp) {
+    if (it % 2 == 0) {
+        int org[3] = {0, 0, 0};
+        if (it < d.ntiles) tile_origin(d, it, org[0], org[1], org[2]);
+        stage_gather<P, T>(d, it, sp, org);
+    } else {
+        stage_gather<P, T>(d, it, sp);
+    }
+}
+
 extern "C" {
 
 // One or more evaluations (repeat >= 1, same inputs) of the emulated pipeline. Outputs: forces (n*3),
@@ -99,12 +124,12 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
         for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
             const int key = p * 10 + d.tlog;
             switch (key) {
-                case 43: stage_spread<4, 8>(d, it, sp); break;
-                case 63: stage_spread<6, 8>(d, it, sp); break;
-                case 83: stage_spread<8, 8>(d, it, sp); break;
-                case 44: stage_spread<4, 16>(d, it, sp); break;
-                case 64: stage_spread<6, 16>(d, it, sp); break;
-                default: stage_spread<8, 16>(d, it, sp); break;
+                case 43: spread_item<4, 8>(d, it, sp); break;
+                case 63: spread_item<6, 8>(d, it, sp); break;
+                case 83: spread_item<8, 8>(d, it, sp); break;
+                case 44: spread_item<4, 16>(d, it, sp); break;
+                case 64: spread_item<6, 16>(d, it, sp); break;
+                default: spread_item<8, 16>(d, it, sp); break;
             }
         }
         if (grid_out) memcpy(grid_out, s.grid.data(), s.grid.size() * 8);
@@ -114,12 +139,12 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
         for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
             const int key = p * 10 + d.tlog;
             switch (key) {
-                case 43: stage_gather<4, 8>(d, it, sp); break;
-                case 63: stage_gather<6, 8>(d, it, sp); break;
-                case 83: stage_gather<8, 8>(d, it, sp); break;
-                case 44: stage_gather<4, 16>(d, it, sp); break;
-                case 64: stage_gather<6, 16>(d, it, sp); break;
-                default: stage_gather<8, 16>(d, it, sp); break;
+                case 43: gather_item<4, 8>(d, it, sp); break;
+                case 63: gather_item<6, 8>(d, it, sp); break;
+                case 83: gather_item<8, 8>(d, it, sp); break;
+                case 44: gather_item<4, 16>(d, it, sp); break;
+                case 64: gather_item<6, 16>(d, it, sp); break;
+                default: gather_item<8, 16>(d, it, sp); break;
             }
         }
         status = s.ctl.status;
