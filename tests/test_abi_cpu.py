@@ -113,3 +113,27 @@ def test_binding_result_buffer_per_thread():
     t.start()
     t.join()
     assert other[0] != at
+
+
+def test_product_never_reaches_the_oracle(tmp_path):
+    """The package imports nothing from oracle/ (a fresh interpreter that imports it loads no oracle module),
+    no product source names it in an import, and a missing CUDA library raises instead of falling back."""
+    import subprocess
+    import sys
+
+    code = ("import sys; import paper_2009_12617_gb300, paper_2009_12617_gb300.pme, paper_2009_12617_gb300.build, "
+            "paper_2009_12617_gb300.workloads; "
+            "print(sorted(m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, check=True).stdout
+    assert out.strip() == "[]"
+    pkg = os.path.join(ROOT, "paper_2009_12617_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+                assert "oracle/" not in src and "liboracle" not in src, f
+    code = ("from paper_2009_12617_gb300 import pme\n"
+            "try:\n    pme.load_library(%r)\nexcept RuntimeError as e:\n    print('raised', e)\n" % str(tmp_path / "missing.so"))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, check=True).stdout
+    assert out.startswith("raised")
