@@ -36,8 +36,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC]
+        # OpenMP where the compiler has it (results do not depend on the thread count); serial otherwise
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,7 +74,22 @@ def _load():
         L.oracle_ewald_real.restype = ctypes.c_int
         L.oracle_ewald_self.argtypes = [ctypes.c_int64, _dp, ctypes.c_double]
         L.oracle_ewald_self.restype = ctypes.c_double
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_max_threads.restype = ctypes.c_int
+        _lib.oracle_set_threads(1)  # single-threaded unless a caller asks for more (set_threads)
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the parallel loops (OpenMP build); results are identical for any count. Returns the
+    count now in effect (1 when the oracle was built without OpenMP)."""
+    L = _load()
+    L.oracle_set_threads(int(n))
+    return int(L.oracle_max_threads())
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
 
 
 def _d(a) -> np.ndarray:

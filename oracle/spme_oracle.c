@@ -34,8 +34,29 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_PI 3.14159265358979323846
+
+/* Threads. Where a loop runs in parallel (built with OpenMP), each output element is computed by exactly
+ * one thread with the same operations in the same order as the serial loop, so results do not depend on
+ * the thread count; sums over many atoms or mesh points that feed one output stay serial. */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------------------------------------ */
 /* (1) cell geometry                                                                                       */
@@ -172,6 +193,7 @@ void oracle_dft3(const int K[3], int sign, const double *in_re, const double *in
     twiddle_table(K2, sign, tK2r, tK2i);
     twiddle_table(K3, sign, tK3r, tK3i);
     /* along k3 */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int64_t a = 0; a < K1; ++a)
         for (int64_t b = 0; b < K2; ++b)
             for (int64_t m = 0; m < K3; ++m) {
@@ -186,6 +208,7 @@ void oracle_dft3(const int K[3], int sign, const double *in_re, const double *in
                 bi[(a * K2 + b) * K3 + m] = si;
             }
     /* along k2 */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int64_t a = 0; a < K1; ++a)
         for (int64_t c3 = 0; c3 < K3; ++c3)
             for (int64_t m = 0; m < K2; ++m) {
@@ -200,6 +223,7 @@ void oracle_dft3(const int K[3], int sign, const double *in_re, const double *in
                 ai[(a * K2 + m) * K3 + c3] = si;
             }
     /* along k1 */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int64_t b = 0; b < K2; ++b)
         for (int64_t c3 = 0; c3 < K3; ++c3)
             for (int64_t m = 0; m < K1; ++m) {
@@ -283,6 +307,7 @@ static void recip_vector(const int64_t m[3], const int K[3], const double recip[
 void oracle_influence(const int K[3], int p, double beta, const double box[9], double *BC) {
     double recip[9], vol;
     oracle_recip(box, recip, &vol);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int64_t m1 = 0; m1 < K[0]; ++m1)
         for (int64_t m2 = 0; m2 < K[1]; ++m2)
             for (int64_t m3 = 0; m3 < K[2]; ++m3) {
@@ -360,6 +385,7 @@ int oracle_spme(int64_t n, const double *pos, const double *q, const int K[3], i
 
     /* eq. (10): forces, visiting the same support points as the spreading step */
     const int64_t K2 = K[1], K3 = K[2];
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double u[3];
         scaled_coords(pos + 3 * i, K, recip, u);
@@ -482,6 +508,9 @@ int oracle_ewald_real(int64_t n, const double *pos, const double *q, double beta
     double E = 0.0;
     for (int64_t i = 0; i < 3 * n; ++i) forces[i] = 0.0;
     const double c2 = 2.0 * beta / sqrt(OR_PI);
+    /* per-atom partial energies Ei (one thread per atom i), summed over i in order afterwards */
+    double *Ei = (double *)calloc(n > 0 ? (size_t)n : 1, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = 0; j < n; ++j)
             for (int64_t a = -nmax[0]; a <= nmax[0]; ++a)
@@ -495,10 +524,12 @@ int oracle_ewald_real(int64_t n, const double *pos, const double *q, double beta
                         if (r2 > rcut * rcut) continue;
                         double r = sqrt(r2);
                         double qq = q[i] * q[j];
-                        E += 0.5 * qq * erfc(beta * r) / r;
+                        Ei[i] += 0.5 * qq * erfc(beta * r) / r;
                         double s = qq * (erfc(beta * r) / r + c2 * exp(-beta * beta * r2)) / r2;
                         for (int k = 0; k < 3; ++k) forces[3 * i + k] += s * d[k];
                     }
+    for (int64_t i = 0; i < n; ++i) E += Ei[i];
+    free(Ei);
     *energy = E;
     return 0;
 }

@@ -376,3 +376,37 @@ def test_spme_empty_and_single_charge(oracle_mod):
     e0 = oracle_mod.spme([[1.0, 2.0, 3.0]], [1.0], (16, 16, 16), 6, 0.3, box)["energy"]
     e1 = oracle_mod.spme([[4.2, 7.1, 0.3]], [1.0], (16, 16, 16), 6, 0.3, box)["energy"]
     assert e0 > 0 and e1 == pytest.approx(e0, rel=1e-4)
+
+
+def test_oracle_results_do_not_depend_on_thread_count(oracle_mod):
+    """The OpenMP loops give each output to one thread with the serial loop's operations in order: energy,
+    virial, forces and both meshes are bit-identical for 1 and 4 threads (Ewald real-space sum too)."""
+    s = wl.parity_system()
+    try:
+        oracle_mod.set_threads(1)
+        r1 = oracle_mod.spme(s.pos, s.q, s.K, 6, s.beta, s.box, want_mesh=True)
+        e1 = oracle_mod.ewald_real(s.pos[:400], s.q[:400], 0.34, s.box)
+        oracle_mod.set_threads(4)
+        r4 = oracle_mod.spme(s.pos, s.q, s.K, 6, s.beta, s.box, want_mesh=True)
+        e4 = oracle_mod.ewald_real(s.pos[:400], s.q[:400], 0.34, s.box)
+    finally:
+        oracle_mod.set_threads(1)
+    assert r1["energy"] == r4["energy"] and np.array_equal(r1["virial"], r4["virial"])
+    assert np.array_equal(r1["forces"], r4["forces"]) and np.array_equal(r1["phi"], r4["phi"])
+    assert np.array_equal(r1["Q"], r4["Q"])
+    assert e1["energy"] == e4["energy"] and np.array_equal(e1["forces"], e4["forces"])
+
+
+@pytest.mark.parametrize("K,p,tri", [((32, 32, 32), 4, False), ((30, 32, 36), 6, False), ((30, 32, 36), 6, True)])
+def test_numpy_fft_baseline_matches_oracle(oracle_mod, K, p, tri):
+    """The FP64 numpy-FFT context baseline (timed beside the oracle) evaluates the same sums: it agrees with
+    the direct-DFT oracle to FP64 rounding in energy, forces and virial, orthogonal and triclinic."""
+    from oracle import numpy_spme
+
+    s = wl.parity_system()
+    box = np.array([[27.4, 0, 0], [3.1, 26.0, 0], [-2.0, 4.0, 28.0]]) if tri else s.box
+    r = oracle_mod.spme(s.pos, s.q, K, p, s.beta, box)
+    x = numpy_spme.spme(s.pos, s.q, K, p, s.beta, box)
+    assert abs(x["energy"] - r["energy"]) <= 1e-12 * abs(r["energy"])
+    assert np.abs(x["forces"] - r["forces"]).max() <= 1e-12 * np.abs(r["forces"]).max()
+    assert np.abs(x["virial"] - r["virial"]).max() <= 1e-12 * np.abs(r["virial"]).max()
