@@ -60,6 +60,10 @@ typedef enum {
 /* ------------------------------------------------------------------------------------------------------ */
 /* Single system                                                                                           */
 
+/* Paper: Sec. III-A (Long-Range Pipeline) and its "Charge Spreading" and "FFT" parts fix what a plan holds:
+ * the mesh of K1 x K2 x K3 points the charges are spread onto with order-p cardinal B-splines, and the
+ * Green's-function (influence) data multiplied between the forward and inverse transforms, which the paper
+ * keeps resident in HBM (Sec. V-C). */
 /* Create a plan for mesh K[3] (K1, K2, K3), B-spline order p, Ewald splitting parameter beta (1/A) and
  * periodic cell box[9] (rows are the cell vectors a, b, c in A; any non-singular, right- or left-handed
  * cell). cuda_stream is a cudaStream_t (NULL = the legacy default stream) on the current device; every
@@ -71,10 +75,16 @@ typedef enum {
  * point). On success *out receives the plan; on failure *out is NULL. */
 pme_status pme_create(const int K[3], int p, double beta, const double box[9], void *cuda_stream, pme_plan **out);
 
+/* Paper: Sec. III-A "FFT" (the Green's-function data multiplied between the transforms depends on the cell
+ * through |m'| and V) and Sec. V-C (that data is kept in device memory, so a new cell rewrites it). */
 /* Replace the periodic cell (e.g. after a barostat step); recomputes the influence table. Same box
  * rules as pme_create. Synchronous with respect to the plan stream. */
 pme_status pme_set_box(pme_plan *plan, const double box[9]);
 
+/* Paper: Sec. III-A (Long-Range Pipeline): each timestep takes atom positions and charges and returns the
+ * long-range force on every atom, through charge spreading, the forward 3D FFT, the Green's-function
+ * multiply, the inverse 3D FFT and force interpolation with the B-spline derivatives. Energy and virial
+ * are the standard SPME sums over the same spectrum (the method the paper cites in Sec. II). */
 /* One SPME evaluation, synchronous: enqueues the pipeline on the plan stream, waits for it, and returns
  * energy (host double*) and virial (host double[6]); either may be NULL. n = 0 gives energy 0, virial 0.
  * A call with the same arrays and n as the previous one records the six stages and the kernel that writes
@@ -86,6 +96,8 @@ pme_status pme_set_box(pme_plan *plan, const double box[9]);
 pme_status pme_compute(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, double *energy,
                        double *virial);
 
+/* Paper: Sec. III-A "Charge Spreading" (the FFT input volume it builds) and "FFT" (the potential mesh the
+ * inverse transform hands to force interpolation). */
 /* pme_compute with diagnostic taps: when non-NULL, mesh_dev (DEVICE, K1*K2*K3 int64, [k1][k2][k3] with k3
  * fastest) receives the charge mesh after spreading as fixed-point integers round(Q * 2^40) summed
  * exactly, and phi_dev (DEVICE, K1*K2*K3 float) the potential mesh phi after the inverse FFT. Meant for
@@ -93,6 +105,8 @@ pme_status pme_compute(pme_plan *plan, const float *pos, const float *q, int64_t
 pme_status pme_compute_debug(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                              double *energy, double *virial, int64_t *mesh_dev, float *phi_dev);
 
+/* Paper: Sec. III (System Architecture): many timesteps run on the accelerator with no host traffic beyond
+ * initialization and result collection; this call enqueues one timestep's evaluation without a host wait. */
 /* Asynchronous form of pme_compute: enqueues the pipeline and returns without waiting. ev_dev is a
  * DEVICE pointer to 7 doubles that receives (energy, virial[6]) when the stream reaches that point.
  * Allocates nothing once pme_reserve(plan, n) (or an earlier call with at least n atoms) has run, so it
@@ -100,12 +114,16 @@ pme_status pme_compute_debug(pme_plan *plan, const float *pos, const float *q, i
  * pme_sync(). */
 pme_status pme_enqueue(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, double *ev_dev);
 
+/* Paper: Sec. III (initialization before the timestep loop, so the loop itself needs no host work). */
 /* Pre-allocate per-atom scratch for up to n atoms (so later pme_enqueue calls allocate nothing). */
 pme_status pme_reserve(pme_plan *plan, int64_t n);
 
+/* Paper: Sec. III (result collection after the timesteps the accelerator ran on its own). */
 /* Wait for the plan stream and return (and clear) any device-side error latched by enqueued work. */
 pme_status pme_sync(pme_plan *plan);
 
+/* Paper: Sec. III-A (Long-Range Pipeline) with the host application of Fig. "MDOverview" on the other side:
+ * positions and charges come from host memory and the forces go back to it every timestep. */
 /* pme_compute with HOST arrays (pos, q, forces in pageable or pinned host memory): the library copies
  * inputs to its own device staging, evaluates, and copies forces back, all on the plan stream, and
  * returns when forces, energy and virial are in host memory. When all three arrays are page-locked
@@ -117,6 +135,8 @@ pme_status pme_sync(pme_plan *plan);
 pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                             double *energy, double *virial);
 
+/* Paper: Sec. V-B and V-C, which time the stages of the pipeline separately (Table IV brackets the forward
+ * and inverse FFTs with timestamps). */
 /* Per-stage device time: runs reps evaluations, each stage kernel bracketed by CUDA events on the plan
  * stream, and returns the mean microseconds per stage in stage_us[6] = (bin, spread, forward FFT,
  * influence multiply + energy/virial, inverse FFT, force interpolation). Arrays as in pme_compute;
@@ -124,6 +144,8 @@ pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, in
 pme_status pme_profile_stages(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, int reps,
                               double stage_us[6]);
 
+/* Paper: Sec. III-A (Fig. "LRPipe"): the stages are pipelined, each starting on its input while the one
+ * before it drains; on this GPU that overlap is programmatic dependent launch between the stage kernels. */
 /* Launch option of the stage kernels (process-wide, for launches issued afterwards): 0 = plain stream
  * order; 1 = programmatic dependent launch, each kernel letting its successor launch as soon as it starts;
  * 2 (default) = the same, released as each CTA finishes (the influence stage releases the inverse FFT
@@ -133,9 +155,12 @@ pme_status pme_profile_stages(pme_plan *plan, const float *pos, const float *q, 
  * values. */
 pme_status pme_set_launch_mode(int mode);
 
+/* Paper: Sec. V-C (which problem sizes fit in on-chip memory and which need HBM); here the figure the
+ * serving loop admits requests by. */
 /* Device bytes the plan holds right now (mesh, tables, per-atom scratch). */
 size_t pme_plan_device_bytes(const pme_plan *plan);
 
+/* Releases everything pme_create and later calls allocated for the plan. The plan must be idle. */
 void pme_destroy(pme_plan *plan);
 
 /* Allocation-free evaluation of one small system, for callers that must not allocate device memory:
@@ -159,6 +184,9 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
 /* ------------------------------------------------------------------------------------------------------ */
 /* Batched evaluation: many independent systems per call, replayed from one CUDA graph                      */
 
+/* Paper: Sec. V-C runs several CS / FI pipelines per board and across boards (configurations 1_1 to 4_2)
+ * and reports time against problem size in atoms; on one GPU the counterpart is evaluating many
+ * independent systems of different sizes together, so that the device stays full. */
 /* Build a batch over nsys existing plans (not owned by the batch; each must outlive it and must not be
  * used elsewhere while the batch runs). All plans must use the same B-spline order p. Atom counts n[s] are
  * fixed for the batch. Atom arrays of all systems are packed back to back in the order given: system s owns
@@ -168,21 +196,43 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
  * equal each system's single-system evaluation bit for bit. */
 pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, void *cuda_stream, pme_batch **out);
 
+/* Paper: Sec. III-A per system, as for pme_compute; the batch analogue of pme_enqueue. */
 /* Evaluate every system of the batch: pos (Ntot x 3), q (Ntot), forces (Ntot x 3) are packed device
  * arrays; ev_dev is a DEVICE array of nsys x 7 doubles (energy, virial[6] per system). Asynchronous:
  * call pme_batch_sync() to wait and collect device-side errors. */
 pme_status pme_batch_enqueue(pme_batch *batch, const float *pos, const float *q, float *forces, double *ev_dev);
+/* Wait for the batch's stream and return (and clear) any device-side error of the last evaluation. Paper:
+ * Sec. III (result collection). */
 pme_status pme_batch_sync(pme_batch *batch);
+
+/* How a batch runs its systems. PME_BATCH_GROUPED: systems of one mesh shape share one launch per stage,
+ * the shapes' launch chains run as parallel branches of the batch's graph. PME_BATCH_PERSISTENT: one
+ * persistent kernel takes (system, stage, item range) entries from a work list in order, each entry
+ * waiting (bounded, PME_ETIMEOUT past 1 s) only for its own system's previous stage, so the stages of
+ * different systems overlap. PME_BATCH_AUTO (the default): the grouped chains where the systems allow
+ * them. Every strategy gives each system its single-system result bit for bit. Takes effect at the next
+ * pme_batch_enqueue (which then re-records the graph). Returns PME_EUNSUPPORTED for PME_BATCH_GROUPED
+ * when a plan uses 16^3 spreading tiles. Paper: Sec. V-C (several pipelines at once); the work list is
+ * this library's own scheduling. */
+enum { PME_BATCH_AUTO = 0, PME_BATCH_GROUPED = 1, PME_BATCH_PERSISTENT = 2 };
+pme_status pme_batch_set_strategy(pme_batch *batch, int strategy);
+/* The strategy the next pme_batch_enqueue uses (PME_BATCH_GROUPED or PME_BATCH_PERSISTENT), or -1 for a
+ * NULL batch. */
+int pme_batch_get_strategy(const pme_batch *batch);
+/* Releases the batch's own state (not its plans). The batch must be idle. */
 void pme_batch_destroy(pme_batch *batch);
 
 /* ------------------------------------------------------------------------------------------------------ */
 /* Serving: continuous batching of independent requests                                                   */
 
+/* The paper has no serving counterpart: this request loop is an interface of the library for callers that
+ * submit independent evaluations (different systems, different atom counts and meshes) as they arrive. */
 /* A server owns a worker thread that admits submitted requests into "waves" (requests of one mesh shape
  * share one launch per stage) while earlier waves are still running, bounded by max_slots requests in
  * flight and by mem_budget_bytes of device memory held by the plans of in-flight requests. */
 pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server **out);
 
+/* No counterpart in the paper (serving interface); each request is one Sec. III-A evaluation. */
 /* Submit one evaluation on a resident plan. pos, q, forces are device arrays that must stay valid until
  * pme_poll returns PME_OK or an error; energy (double*) and virial (double[6]) are host pointers written
  * before completion is reported (either may be NULL). Requests on the same plan run one at a time, in
@@ -191,24 +241,41 @@ pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server 
 pme_status pme_submit(pme_server *srv, pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                       double *energy, double *virial, pme_ticket *out);
 
+/* No counterpart in the paper (serving interface). */
 /* Query a ticket: PME_OK when done (results written; the ticket is then retired), PME_PENDING while in
  * flight, or the request's error. block != 0 waits until it is done. */
 pme_status pme_poll(pme_server *srv, pme_ticket ticket, int block);
 
+/* No counterpart in the paper (serving interface). */
 /* Device-side latency statistics of completed requests (microseconds from submit to completion). */
 pme_status pme_server_stats(pme_server *srv, int64_t *completed, double *p50_us, double *p99_us, int64_t *waves);
 
+/* Stops the worker after the requests in flight complete and releases the server. */
 void pme_server_destroy(pme_server *srv);
 
 /* ------------------------------------------------------------------------------------------------------ */
 /* Errors and test hooks                                                                                   */
 
+/* No counterpart in the paper: error reporting of this library. Static text for a status code. */
 const char *pme_strerror(pme_status s);
 
+/* No counterpart in the paper: error reporting of this library. */
 /* Copy the calling thread's last error message (NUL-terminated, truncated to len) into buf. Returns the
  * status that produced it (PME_OK if none). */
 pme_status pme_last_error_detail(char *buf, size_t len);
 
+/* No counterpart in the paper: a throughput probe of the resource the charge-spreading step (Sec. III-A
+ * "Charge Spreading") is bound by on this GPU, for stating its achieved rate against a measured peak.
+ * Enqueues one probe kernel of ctas CTAs on cuda_stream and returns in *ops the number of operations it
+ * performs (time it with events on that stream): kind 0 = conflict-free shared-memory 32-bit integer
+ * atomicAdd (buf: DEVICE, at least 4 bytes per CTA, receives a checksum per CTA); kind 1 = 64-bit integer
+ * reductions into global memory spread over buf (DEVICE, buf_bytes, keep it L2-sized; its contents are
+ * incremented). Returns PME_EINVAL for other kinds, sizes or NULL pointers. */
+pme_status pme_probe_launch(int kind, int ctas, int rounds, void *buf, size_t buf_bytes, void *cuda_stream,
+                            double *ops);
+
+/* No counterpart in the paper: failure detection of this library (a bounded device-side wait that gives
+ * up and reports, instead of hanging). */
 /* Test hook: when set (nonzero) on a batch, the batch runs as one persistent work-list kernel whose
  * entries wait (bounded) for their dependencies, and its next launch makes one such wait on a counter that
  * nothing advances. The bounded wait gives up after wait_limit_ns (<= 2 s) and the launch reports

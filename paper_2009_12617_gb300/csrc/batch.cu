@@ -341,10 +341,17 @@ struct pme_batch {
     const void *g_pos = nullptr, *g_q = nullptr, *g_forces = nullptr, *g_ev = nullptr;
     int stall = 0;
     int64_t stall_ns = 0;
+    int strategy = PME_BATCH_AUTO;  // pme_batch_set_strategy
+    int g_persistent = -1;          // whether the recorded graph is the persistent launch
 };
 
-// Grouped evaluation: the persistent kernel is used only while the stall test hook is on (its bounded
-// waits are what that hook exercises).
+// The persistent work-list kernel runs when asked for, while the stall hook is on (its bounded waits are
+// what that hook exercises), or when the systems cannot be grouped; otherwise the grouped stage chains.
+static bool batch_use_persistent(const pme_batch *b) {
+    return b->stall || b->groups.empty() || b->strategy == PME_BATCH_PERSISTENT;
+}
+
+// Grouped evaluation: one chain of six grouped stage launches per mesh shape, the chains as parallel branches.
 static pme_status batch_record_grouped(pme_batch *b, const float *pos, const float *q, float *forces, double *ev_dev) {
     const int nsys = (int)b->sys.size();
     for (int i = 0; i < nsys; ++i) {
@@ -536,7 +543,9 @@ pme_status pme_batch_enqueue(pme_batch *b, const float *pos, const float *q, flo
     if (ntot > 0 && (!pos || !q || !forces)) return fail(PME_EINVAL, "pos, q and forces must be non-NULL");
     DeviceGuard g(b->dev);
     cudaError_t e;
-    if (!b->exec || b->g_pos != pos || b->g_q != q || b->g_forces != forces || b->g_ev != ev_dev) {
+    const bool persistent = batch_use_persistent(b);
+    if (!b->exec || b->g_pos != pos || b->g_q != q || b->g_forces != forces || b->g_ev != ev_dev ||
+        b->g_persistent != (int)persistent) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
@@ -550,8 +559,7 @@ pme_status pme_batch_enqueue(pme_batch *b, const float *pos, const float *q, flo
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         pme_status st = PME_OK;
         if (e == cudaSuccess)
-            st = (!b->groups.empty() && !b->stall) ? batch_record_grouped(b, pos, q, forces, ev_dev)
-                                                   : batch_record(b, pos, q, forces, ev_dev);
+            st = persistent ? batch_record(b, pos, q, forces, ev_dev) : batch_record_grouped(b, pos, q, forces, ev_dev);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         b->stream = keep;
         cudaStreamDestroy(cs);
@@ -571,6 +579,7 @@ pme_status pme_batch_enqueue(pme_batch *b, const float *pos, const float *q, flo
         b->g_q = q;
         b->g_forces = forces;
         b->g_ev = ev_dev;
+        b->g_persistent = (int)persistent;
     }
     if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return PME_OK;
@@ -595,6 +604,21 @@ pme_status pme_batch_sync(pme_batch *b) {
     memset(b->wave.h_status, 0, sizeof(unsigned) * nsys);
     cudaMemsetAsync(b->wave.d_status, 0, sizeof(unsigned) * nsys, b->stream);
     return status_from_bits(bits);
+}
+
+pme_status pme_batch_set_strategy(pme_batch *b, int strategy) {
+    if (!b) return fail(PME_EINVAL, "batch is NULL");
+    if (strategy != PME_BATCH_AUTO && strategy != PME_BATCH_GROUPED && strategy != PME_BATCH_PERSISTENT)
+        return fail(PME_EINVAL, "strategy must be PME_BATCH_AUTO, PME_BATCH_GROUPED or PME_BATCH_PERSISTENT");
+    if (strategy == PME_BATCH_GROUPED && b->groups.empty())
+        return fail(PME_EUNSUPPORTED, "these systems cannot be grouped (a plan uses 16^3 tiles)");
+    b->strategy = strategy;  // the next enqueue re-records the graph if the choice changed
+    return PME_OK;
+}
+
+int pme_batch_get_strategy(const pme_batch *b) {
+    if (!b) return -1;
+    return batch_use_persistent(b) ? PME_BATCH_PERSISTENT : PME_BATCH_GROUPED;
 }
 
 pme_status pme_batch_debug_stall(pme_batch *b, int enable, int64_t wait_limit_ns) {

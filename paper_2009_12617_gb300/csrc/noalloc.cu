@@ -146,18 +146,39 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_eval_noalloc(NoallocArgs A)
     }
     grid.sync();
     // 2..7: the six pipeline stages, each over its work items, with a grid barrier in between
+    // A CTA that takes several items of one stage waits at a CTA barrier after each: the next item's first
+    // shared-memory writes (spread_clear, the gather's region load) must not overtake warps still reading
+    // the previous item's tile.
     const int nbin = d.nbin;
-    for (int it = blockIdx.x; it < nbin; it += gridDim.x) stage_bin(d, it, smem);
+    for (int it = blockIdx.x; it < nbin; it += gridDim.x) {
+        stage_bin(d, it, smem);
+        __syncthreads();
+    }
     grid.sync();
-    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) stage_spread<P, 8>(d, it, smem);
+    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) {
+        stage_spread<P, 8>(d, it, smem);
+        __syncthreads();
+    }
     grid.sync();
-    for (int it = blockIdx.x; it < d.K1; it += gridDim.x) stage_fwd(d, it, smem);
+    for (int it = blockIdx.x; it < d.K1; it += gridDim.x) {
+        stage_fwd(d, it, smem);
+        __syncthreads();
+    }
     grid.sync();
-    for (int it = blockIdx.x; it < d.nconv; it += gridDim.x) stage_conv(d, it, smem);
+    for (int it = blockIdx.x; it < d.nconv; it += gridDim.x) {
+        stage_conv(d, it, smem);
+        __syncthreads();
+    }
     grid.sync();
-    for (int it = blockIdx.x; it < d.K1; it += gridDim.x) stage_inv(d, it, smem);
+    for (int it = blockIdx.x; it < d.K1; it += gridDim.x) {
+        stage_inv(d, it, smem);
+        __syncthreads();
+    }
     grid.sync();
-    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) stage_gather<P, 8>(d, it, smem);
+    for (int it = blockIdx.x; it < d.ntiles + OVF_ITEMS; it += gridDim.x) {
+        stage_gather<P, 8>(d, it, smem);
+        __syncthreads();
+    }
 }
 
 struct NoallocDevice {

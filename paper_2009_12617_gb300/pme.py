@@ -26,6 +26,10 @@ PME_EAGAIN = 6
 PME_ETIMEOUT = 7
 PME_PENDING = 8
 
+PME_BATCH_AUTO = 0
+PME_BATCH_GROUPED = 1
+PME_BATCH_PERSISTENT = 2
+
 STATUS_NAMES = {0: "PME_OK", 1: "PME_EINVAL", 2: "PME_EUNSUPPORTED", 3: "PME_ENOMEM", 4: "PME_ECUDA",
                 5: "PME_EOVERFLOW", 6: "PME_EAGAIN", 7: "PME_ETIMEOUT", 8: "PME_PENDING"}
 
@@ -34,7 +38,8 @@ EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme
            "pme_profile_stages", "pme_set_launch_mode", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
            "pme_batch_destroy", "pme_server_create", "pme_submit", "pme_poll", "pme_server_stats",
            "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall",
-           "pme_compute_noalloc")
+           "pme_compute_noalloc", "pme_batch_set_strategy", "pme_batch_get_strategy",
+           "pme_probe_launch")
 
 
 class PMEError(RuntimeError):
@@ -117,6 +122,9 @@ def load_library(path: str | None = None):
         "pme_batch_sync": (_st, [_vp]),
         "pme_batch_destroy": (None, [_vp]),
         "pme_batch_debug_stall": (_st, [_vp, ctypes.c_int, _i64]),
+        "pme_batch_set_strategy": (_st, [_vp, ctypes.c_int]),
+        "pme_batch_get_strategy": (ctypes.c_int, [_vp]),
+        "pme_probe_launch": (_st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_double)]),
         "pme_server_create": (_st, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
         "pme_submit": (_st, [_vp, _vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
         "pme_poll": (_st, [_vp, _i64, ctypes.c_int]),
@@ -292,6 +300,14 @@ def pme_batch_destroy(batch: int) -> None:
         load_library().pme_batch_destroy(_vp(batch))
 
 
+def pme_batch_set_strategy(batch: int, strategy: int) -> None:
+    check(load_library().pme_batch_set_strategy(_vp(batch), int(strategy)))
+
+
+def pme_batch_get_strategy(batch: int) -> int:
+    return int(load_library().pme_batch_get_strategy(_vp(batch)))
+
+
 def pme_batch_debug_stall(batch: int, enable: bool, wait_limit_ns: int = 200_000_000) -> None:
     check(load_library().pme_batch_debug_stall(_vp(batch), int(bool(enable)), int(wait_limit_ns)))
 
@@ -342,15 +358,35 @@ def pme_server_destroy(srv: int) -> None:
 def pme_compute_noalloc(K, p: int, beta: float, box, pos, q, forces, stream=None) -> tuple[float, np.ndarray]:
     """Allocation-free evaluation of one small system (see include/pme.h): the library allocates no device
     memory for it, using a fixed static device array instead. Returns (E, virial[6]); forces filled."""
+    import torch
+
+    n = int(q.shape[0])
+    if int(pos.shape[0]) != n or int(forces.shape[0]) != n:
+        raise ValueError(f"pos {tuple(pos.shape)}, q {tuple(q.shape)} and forces {tuple(forces.shape)} need the same n")
+    cur = torch.cuda.current_device()
+    for name, t in (("pos", pos), ("q", q), ("forces", forces)):
+        if t.is_cuda and t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, but the call runs on the current device cuda:{cur}")
+    if stream is None:  # the caller's current torch stream, so the call orders after the work that made pos / q
+        stream = torch.cuda.current_stream(cur)
     Kc = (ctypes.c_int * 3)(*[int(k) for k in K])
     bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
     e = ctypes.c_double()
     vir = (ctypes.c_double * 6)()
     check(load_library().pme_compute_noalloc(Kc, int(p), float(beta), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                             _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), int(q.shape[0]),
+                                             _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), n,
                                              _vp(_f32(forces, (3,), "forces")), ctypes.byref(e), vir,
                                              _vp(_stream_handle(stream))))
     return e.value, np.array(vir[:])
+
+
+def pme_probe_launch(kind: int, ctas: int, rounds: int, buf, stream=None) -> float:
+    """Enqueue one atomic-throughput probe kernel (kind 0: shared-memory int32 atomics, 1: global int64
+    reductions) on buf (a CUDA tensor); returns the operations it performs."""
+    ops = ctypes.c_double()
+    check(load_library().pme_probe_launch(int(kind), int(ctas), int(rounds), _vp(_ptr(buf)),
+                                          buf.numel() * buf.element_size(), _vp(_stream_handle(stream)), ctypes.byref(ops)))
+    return ops.value
 
 
 def pme_strerror(status: int) -> str:

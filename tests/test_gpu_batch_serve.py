@@ -1,5 +1,5 @@
-"""GPU tests of batched evaluation (grouped stage launches; the persistent work-list kernel behind the stall
-hook) and the serving loop.
+"""GPU tests of batched evaluation (grouped stage launches; the persistent work-list kernel, in normal
+operation and behind the stall hook) and the serving loop.
 
 Each system's result in a batch or a served mix must equal its result alone (pme_compute) within the
 parity tolerances; the work decomposition of a system is the same in every launch, so the results are
@@ -77,6 +77,44 @@ def test_batch_matches_single_systems(pme, systems, oracle_mod):
         r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
         assert rel_energy(evh[0, 0], r["energy"]) < E_REL_TOL
         assert rms_force(Fh[:ns[0]], r["forces"]) < F_RMS_TOL
+    finally:
+        pme.pme_batch_destroy(b)
+
+
+def test_batch_persistent_strategy_matches_single_systems(pme, systems, oracle_mod):
+    """The persistent work-list kernel (one launch for all 12 uneven systems, entries waiting only on their
+    own system's previous stage) in normal operation: every system equals its single evaluation bit for bit
+    over graph replays, one system matches the oracle, and switching back to grouped launches re-records."""
+    pos, q, ns = packed(systems)
+    F = torch.full_like(pos, float("nan"))
+    ev = torch.zeros((len(systems), 7), dtype=torch.float64, device="cuda:0")
+    b = pme.pme_batch_create([o["plan"] for o in systems], ns)
+    try:
+        assert pme.pme_batch_get_strategy(b) == pme.PME_BATCH_GROUPED
+        pme.pme_batch_set_strategy(b, pme.PME_BATCH_PERSISTENT)
+        assert pme.pme_batch_get_strategy(b) == pme.PME_BATCH_PERSISTENT
+        for rep in range(3):  # replays: the last CTA out resets every counter of the work list
+            F.fill_(float("nan"))
+            pme.pme_batch_enqueue(b, pos, q, F, ev)
+            pme.pme_batch_sync(b)
+            Fh, evh = F.cpu().numpy(), ev.cpu().numpy()
+            off = 0
+            for i, o in enumerate(systems):
+                check_same(o, Fh[off:off + ns[i]], evh[i, 0], evh[i, 1:], exact=True)
+                off += ns[i]
+        s = systems[5]["sys"]
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
+        off = sum(ns[:5])
+        assert rel_energy(evh[5, 0], r["energy"]) < E_REL_TOL
+        assert rms_force(Fh[off:off + ns[5]], r["forces"]) < F_RMS_TOL
+        assert rel_virial(evh[5, 1:], r["virial"]) < V_TOL
+        pme.pme_batch_set_strategy(b, pme.PME_BATCH_GROUPED)
+        F.fill_(float("nan"))
+        pme.pme_batch_enqueue(b, pos, q, F, ev)
+        pme.pme_batch_sync(b)
+        assert np.array_equal(F.cpu().numpy(), Fh) and np.array_equal(ev.cpu().numpy(), evh)
+        with pytest.raises(pme.PMEError):
+            pme.pme_batch_set_strategy(b, 7)
     finally:
         pme.pme_batch_destroy(b)
 

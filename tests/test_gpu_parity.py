@@ -324,3 +324,30 @@ def test_invalid_inputs_report_and_recover(pmelib, oracle_mod):
         assert rel_energy(g["energy"], r["energy"]) < E_REL_TOL
     finally:
         pmelib.pme_destroy(plan)
+
+
+def test_headline_trajectory_every_100th_frame(pmelib, oracle_mod):
+    """The paper-sized system over 1000 successive frames, each jittered by N(0, 0.01 A) from the one before
+    (cumulative, wrapped): every frame is evaluated on device arrays through the synchronous entry point
+    (its recorded-graph replay after the first two calls), and frames 0, 100, ..., 900 are compared with the
+    FP64 oracle on the same FP32 positions at the energy, force and virial tolerances."""
+    s = wl.headline_system()
+    L = float(s.box[0, 0])
+    dev = torch.device("cuda:0")
+    pos = torch.from_numpy(s.pos).to(dev)
+    q = torch.from_numpy(s.q).to(dev)
+    F = torch.empty_like(pos)
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        cur = s.pos
+        for f in range(1000):
+            pos.copy_(torch.from_numpy(cur))
+            E, V = pmelib.pme_compute(plan, pos, q, F)
+            if f % 100 == 0:
+                r = oracle_mod.spme(cur.astype(np.float64), s.q.astype(np.float64), s.K, s.p, s.beta, s.box)
+                assert rel_energy(E, r["energy"]) < E_REL_TOL, (f, E, r["energy"])
+                assert rms_force(F.cpu().numpy(), r["forces"]) < F_RMS_TOL, f
+                assert rel_virial(V, r["virial"]) < V_TOL, f
+            cur = wl.jitter(cur, L, 77, f)
+    finally:
+        pmelib.pme_destroy(plan)
