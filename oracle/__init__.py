@@ -11,7 +11,8 @@ Parity status of each function (what pins it is in tests/test_oracle_pins.py):
   bmod2, influence         pinned: closed-form p = 4 modulus; convergence of SPME to Ewald
   spme (E, virial, F)      pinned: Ewald convergence, NaCl Madelung constant, finite differences of E
                            (positions and strain), phi identity, one-cell translation invariance
-  ewald_recip/real/self    pinned: independent numpy Ewald, Madelung constant at two beta values, FD forces
+  ewald_recip/real/self    pinned: independent numpy Ewald, Madelung constant at two beta values, FD forces;
+                           real-space virial by central differences of the energy under strain
 """
 from __future__ import annotations
 
@@ -70,7 +71,7 @@ def _load():
                                          _dp, _dp]
         L.oracle_ewald_recip.restype = ctypes.c_int
         L.oracle_ewald_real.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, ctypes.c_double, _dp,
-                                        _dp]
+                                        _dp, _dp]
         L.oracle_ewald_real.restype = ctypes.c_int
         L.oracle_ewald_self.argtypes = [ctypes.c_int64, _dp, ctypes.c_double]
         L.oracle_ewald_self.restype = ctypes.c_double
@@ -217,17 +218,18 @@ def ewald_recip(pos, q, beta, box, mcut: float | None = None) -> dict:
 
 
 def ewald_real(pos, q, beta, box, rcut: float | None = None) -> dict:
-    """Real-space Ewald sum over images within rcut (default beta * rcut = 6): {'energy', 'forces'}."""
+    """Real-space Ewald sum over images within rcut (default beta * rcut = 6): {'energy', 'forces', 'virial'}."""
     pos = _d(pos).reshape(-1, 3)
     q = _d(q).reshape(-1)
     box = _d(box).reshape(9)
     rcut = 6.0 / beta if rcut is None else rcut
     e = ctypes.c_double()
     F = np.zeros_like(pos)
+    vir = np.zeros(6)
     if _load().oracle_ewald_real(pos.shape[0], _p(pos), _p(q), float(beta), _p(box), float(rcut), ctypes.byref(e),
-                                 _p(F)) != 0:
+                                 _p(F), _p(vir)) != 0:
         raise ValueError("singular box")
-    return {"energy": e.value, "forces": F}
+    return {"energy": e.value, "forces": F, "virial": vir}
 
 
 def ewald_self(q, beta) -> float:

@@ -493,9 +493,11 @@ int oracle_ewald_recip(int64_t n, const double *pos, const double *q, double bet
 
 /* Real-space Ewald term E = 1/2 sum_{i,j,n}' q_i q_j erfc(beta r)/r over all lattice images n with
  * r = |r_i - r_j + n| <= rcut (the primed sum skips i == j at n = 0), and its forces
- * F_i = sum q_i q_j [erfc(beta r)/r + 2 beta/sqrt(pi) exp(-beta^2 r^2)] (r_i - r_j + n) / r^2. */
+ * F_i = sum q_i q_j [erfc(beta r)/r + 2 beta/sqrt(pi) exp(-beta^2 r^2)] (r_i - r_j + n) / r^2, and (when
+ * virial is not NULL) its virial Pi_ab = -dE/d eps_ab = 1/2 sum' s_ij d_a d_b with s_ij the scalar factor of
+ * the force above and d = r_i - r_j + n (the pair potential depends on the strain only through |d|). */
 int oracle_ewald_real(int64_t n, const double *pos, const double *q, double beta, const double box[9],
-                      double rcut, double *energy, double *forces) {
+                      double rcut, double *energy, double *forces, double *virial) {
     double recip[9], vol;
     if (oracle_recip(box, recip, &vol) != 0) return -1;
     /* image range: n_alpha with |n_alpha| <= ceil(rcut * |a*_alpha|) + 1 covers every image within rcut
@@ -508,8 +510,9 @@ int oracle_ewald_real(int64_t n, const double *pos, const double *q, double beta
     double E = 0.0;
     for (int64_t i = 0; i < 3 * n; ++i) forces[i] = 0.0;
     const double c2 = 2.0 * beta / sqrt(OR_PI);
-    /* per-atom partial energies Ei (one thread per atom i), summed over i in order afterwards */
+    /* per-atom partial energies Ei and virials Wi (one thread per atom i), summed over i in order afterwards */
     double *Ei = (double *)calloc(n > 0 ? (size_t)n : 1, sizeof(double));
+    double *Wi = (double *)calloc(n > 0 ? (size_t)(6 * n) : 6, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = 0; j < n; ++j)
@@ -527,9 +530,21 @@ int oracle_ewald_real(int64_t n, const double *pos, const double *q, double beta
                         Ei[i] += 0.5 * qq * erfc(beta * r) / r;
                         double s = qq * (erfc(beta * r) / r + c2 * exp(-beta * beta * r2)) / r2;
                         for (int k = 0; k < 3; ++k) forces[3 * i + k] += s * d[k];
+                        Wi[6 * i + 0] += 0.5 * s * d[0] * d[0];
+                        Wi[6 * i + 1] += 0.5 * s * d[1] * d[1];
+                        Wi[6 * i + 2] += 0.5 * s * d[2] * d[2];
+                        Wi[6 * i + 3] += 0.5 * s * d[0] * d[1];
+                        Wi[6 * i + 4] += 0.5 * s * d[0] * d[2];
+                        Wi[6 * i + 5] += 0.5 * s * d[1] * d[2];
                     }
     for (int64_t i = 0; i < n; ++i) E += Ei[i];
+    if (virial) {
+        for (int k = 0; k < 6; ++k) virial[k] = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < 6; ++k) virial[k] += Wi[6 * i + k];
+    }
     free(Ei);
+    free(Wi);
     *energy = E;
     return 0;
 }

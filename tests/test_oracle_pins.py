@@ -197,6 +197,7 @@ def _np_ewald_real(pos, q, beta, box, rcut):
 
     E = 0.0
     F = np.zeros_like(pos)
+    V = np.zeros(6)
     rinv = np.linalg.inv(box)
     nmax = [int(math.ceil(rcut * np.linalg.norm(rinv[:, a]))) + 1 for a in range(3)]
     shifts = np.array([(a, b, c) for a in range(-nmax[0], nmax[0] + 1) for b in range(-nmax[1], nmax[1] + 1)
@@ -211,7 +212,9 @@ def _np_ewald_real(pos, q, beta, box, rcut):
         s = np.where(mask, q[i] * q[None, :] * (erfc(beta * rr) / rr + 2 * beta / math.sqrt(math.pi)
                                                  * np.exp(-beta ** 2 * rr ** 2)) / rr ** 2, 0.0)
         F[i] = np.sum(s[:, :, None] * d, axis=(0, 1))
-    return E, F
+        for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+            V[k] += 0.5 * np.sum(s * d[:, :, a] * d[:, :, b])
+    return E, F, V
 
 
 def _tri_box():
@@ -233,10 +236,11 @@ def test_ewald_terms_match_independent_numpy(oracle_mod, tri):
     assert r["energy"] == pytest.approx(E, rel=1e-12)
     np.testing.assert_allclose(r["forces"], F, rtol=1e-10, atol=1e-12)
     np.testing.assert_allclose(r["virial"], V, rtol=1e-10, atol=1e-12)
-    Er, Fr = _np_ewald_real(pos, q, beta, box, 6.0 / beta)
+    Er, Fr, Vr = _np_ewald_real(pos, q, beta, box, 6.0 / beta)
     rr = oracle_mod.ewald_real(pos, q, beta, box)
     assert rr["energy"] == pytest.approx(Er, rel=1e-12)
     np.testing.assert_allclose(rr["forces"], Fr, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(rr["virial"], Vr, rtol=1e-10, atol=1e-12)
     assert oracle_mod.ewald_self(q, beta) == pytest.approx(-beta / math.sqrt(math.pi) * np.sum(q ** 2), rel=1e-14)
 
 
@@ -410,3 +414,36 @@ def test_numpy_fft_baseline_matches_oracle(oracle_mod, K, p, tri):
     assert abs(x["energy"] - r["energy"]) <= 1e-12 * abs(r["energy"])
     assert np.abs(x["forces"] - r["forces"]).max() <= 1e-12 * np.abs(r["forces"]).max()
     assert np.abs(x["virial"] - r["virial"]).max() <= 1e-12 * np.abs(r["virial"]).max()
+
+
+@pytest.mark.parametrize("tri", [False, True])
+def test_ewald_real_virial_and_forces_are_derivatives(oracle_mod, tri):
+    """Real-space term: Pi_ab = -dE/d eps_ab (strain at fixed fractional coordinates) and F = -dE/dr, by
+    central differences, with beta * rcut = 6 so no pair crosses the cutoff discontinuously."""
+    rng = np.random.default_rng(29)
+    box = _tri_box() if tri else np.diag([9.0, 10.0, 11.0])
+    n = 20
+    frac = rng.random((n, 3))
+    q = rng.normal(size=n)
+    q -= q.mean()
+    beta = 0.55
+    r = oracle_mod.ewald_real(frac @ box, q, beta, box)
+    h = 1e-6
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for k, (a, b) in enumerate(pairs):
+        es = []
+        for sgn in (+1, -1):
+            eps = np.zeros((3, 3))
+            eps[a, b] = sgn * h
+            bx = box @ (np.eye(3) + eps).T
+            es.append(oracle_mod.ewald_real(frac @ bx, q, beta, bx)["energy"])
+        fd = -(es[0] - es[1]) / (2 * h)
+        assert r["virial"][k] == pytest.approx(fd, rel=1e-6, abs=1e-8), (k, r["virial"][k], fd)
+    pos = frac @ box
+    for i in (0, 7):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = -(oracle_mod.ewald_real(pp, q, beta, box)["energy"] - oracle_mod.ewald_real(pm, q, beta, box)["energy"]) / (2 * h)
+            assert r["forces"][i, d] == pytest.approx(fd, rel=1e-6, abs=1e-8)
