@@ -6,9 +6,10 @@ are resident in HBM (786 MB, larger than L2), replayed from per-frame CUDA graph
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs N independent replicas (one per GPU, launched by torchrun); the single-system evaluation does
-not shard, so there is no data-path collective, only a barrier and a max over ranks around the timed region.
---impl reference times the FP64 CPU oracle on the same workload.
+N > 1 runs one process per GPU (under torchrun; without it, bench.py starts torchrun itself). The
+single-system headline runs as N independent replicas; the batched and served legs shard their systems
+across the ranks. There is no data-path collective, only barriers and a max over ranks around the timed
+regions. --impl reference times the FP64 CPU oracle on the same workload.
 """
 from __future__ import annotations
 
@@ -29,6 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "us per PME eval (65536 atoms, 64^3, p=4)"
 UNIT = "us/eval"
+WORKLOAD = ("65536-atom water-like box (21844 triplets + 2 ion pairs), cubic 86.9 A, 64^3 mesh, p=4, beta=0.34/A, "
+            "1000 jittered frames N(0,0.01 A)")
 PAPER_US = 206.0  # 4 x Stratix 10, same workload size (context; the paper's own hardware)
 N_FRAMES = 1000
 
@@ -40,8 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, batch, serving and CPU baseline legs")
-    ap.add_argument("--legs", default="", help="comma list of extra legs to run alone (batched, serving, large); "
-                                               "skips the headline (for profiling one leg)")
+    ap.add_argument("--legs", default="", help="comma list of extra legs to run alone (batched, serving, large, "
+                                               "profile); skips the headline (profile: a short fixed sequence "
+                                               "for ncu captures)")
     return ap.parse_args()
 
 
@@ -82,6 +86,56 @@ class Dist:
 def shard(items: list, rank: int, world: int) -> list:
     """Round-robin share of independent systems for one rank (batched / served work needs no collective)."""
     return items[rank::world]
+
+
+def gather_all(dist: "Dist", obj):
+    """Every rank's obj as a list (rank order); [obj] on one process."""
+    if not dist.pg:
+        return [obj]
+    out = [None] * dist.world
+    dist.pg.all_gather_object(out, obj)
+    return out
+
+
+def cpu_model() -> str:
+    """CPU model name (lscpu, else /proc/cpuinfo; Arm part numbers of the Neoverse cores named)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    parts = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2"}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+                if ln.lower().startswith("cpu part"):
+                    v = ln.split(":", 1)[1].strip()
+                    return parts.get(v, f"Arm part {v}")
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+def errors_vs_oracle(E, V, F, sysobj, threads: int | None = None) -> dict:
+    """Relative energy, RMS force and virial error of one GPU result against the FP64 oracle."""
+    import oracle
+
+    oracle.build()
+    oracle.set_threads(threads or os.cpu_count() or 1)
+    try:
+        r = oracle.spme(sysobj.pos.astype(np.float64), sysobj.q.astype(np.float64), sysobj.K, sysobj.p, sysobj.beta,
+                        sysobj.box)
+    finally:
+        oracle.set_threads(1)
+    F = np.asarray(F, dtype=np.float64)
+    return {"rel_energy_error": float(abs(E - r["energy"]) / abs(r["energy"])),
+            "rms_force_error": float(np.sqrt(np.mean((F - r["forces"]) ** 2) / np.mean(r["forces"] ** 2))),
+            "rel_virial_error": float(np.max(np.abs(np.asarray(V) - r["virial"])) / np.max(np.abs(r["virial"]))),
+            "tolerance": {"rel_energy": 1e-6, "rms_force": 1e-5, "rel_virial": 1e-5}}
 
 
 # ---------------------------------------------------------------------------------------------------------
@@ -138,17 +192,57 @@ class ClockSampler:
 
 
 def stage_bytes(n: int, K, p: int) -> dict:
+    """Algorithmic bytes per stage launch: what each step of the method must read and write at the least,
+    whatever the implementation (the library's own bucket records and its wider influence table are not
+    counted). Per atom: 12 B position + 4 B charge in, 12 B force out; per mesh point: 8 B int64 charge mesh,
+    4 B potential; per half-spectrum point: 8 B complex FP32 in and out, 8 B FP64 influence value."""
     K1, K2, K3 = K
     mesh = K1 * K2 * K3
     half = K1 * K2 * (K3 // 2 + 1)
     return {
-        "bin": n * (12 + 4 + 24),            # position + charge in, bucket record out
-        "spread": n * 24 + mesh * 8,         # bucket records in, int64 mesh out
+        "bin": n * (16 + 16),                # position + charge in; mesh base (3 int32) + order key out
+        "spread": n * 16 + mesh * 8,         # atoms in, int64 charge mesh out
         "fft_fwd": mesh * 8 + half * 8,      # int64 mesh in, complex half spectrum out
-        "influence": half * (8 + 16 + 8),    # spectrum in, influence table (float4) in, spectrum out
+        "influence": half * (8 + 8 + 8),     # spectrum in, FP64 influence value in, spectrum out
         "fft_inv": half * 8 + mesh * 4,      # spectrum in, phi out
-        "gather": mesh * 4 + n * (24 + 12),  # phi in, records in, forces out
+        "gather": mesh * 4 + n * (16 + 12),  # phi in, atoms in, forces out
     }
+
+
+def spread_atomics(n: int, p: int) -> int:
+    """32-bit shared-memory atomics the spreading stage needs: n p^3 contributions, each a 64-bit fixed-point
+    addition made of two native 32-bit atomics (this part has no native 64-bit shared-memory atomicAdd)."""
+    return 2 * n * p ** 3
+
+
+def measure_atomic_peaks(dev) -> dict:
+    """Conflict-free shared-memory int32 atomicAdd and global int64 reduction throughput of this GPU, each
+    probe kernel timed alone with CUDA events on its stream (best of 5 after warm-up)."""
+    import torch
+
+    from paper_2009_12617_gb300 import pme
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    for kind, name, ctas, rounds, nbytes in ((0, "smem_i32_atomics_per_s", 4 * sms, 256, 4 * 4 * sms),
+                                             (1, "global_i64_red_per_s", 4 * sms, 32, 4 << 20)):
+        buf = torch.zeros(nbytes // 4, dtype=torch.int32, device=dev)
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 0.0
+        with torch.cuda.stream(stream):
+            for rep in range(8):
+                st.record(stream)
+                ops = pme.pme_probe_launch(kind, ctas, rounds, buf, stream)
+                en.record(stream)
+                en.synchronize()
+                if rep >= 3:
+                    best = max(best, ops / (st.elapsed_time(en) * 1e-3))
+        out[name] = best
+    out["how"] = ("probe kernels of this library (pme_probe_launch): 4 CTAs of 512 threads per SM, 8 independent "
+                  "atomics per thread per round; smem: distinct words, one bank per lane; global: a 4 MiB "
+                  "L2-resident buffer, consecutive 64-bit words per warp")
+    return out
 
 
 def measured_peaks():
@@ -225,6 +319,8 @@ def run_ours(args, dist: Dist):
         frames_np[f] = cur
         cur = wl.jitter(cur, L, 1000 + dist.rank, f)
     frames = torch.from_numpy(frames_np).to(dev)
+    SAMPLE = 500  # the frame whose result is checked against the oracle
+    sample_pos = frames_np[SAMPLE].copy()
     del frames_np
     q = torch.from_numpy(s.q).to(dev)
     forces = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
@@ -284,8 +380,7 @@ def run_ours(args, dist: Dist):
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 6), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": round(value / PAPER_US, 6), "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "65536-atom water-like box (21844 triplets + 2 ion pairs), cubic 86.9 A, "
-                               "64^3 mesh, p=4, beta=0.34/A, 1000 jittered frames N(0,0.01 A)",
+        "config": {"workload": WORKLOAD,
                    "l2": "inputs larger than L2: 1000 distinct position frames (786 MB) cycled; mesh and tables "
                          "stay L2-resident by design",
                    "launch": "CUDA graphs of ten consecutive frames (60 kernels, programmatic dependent launch "
@@ -365,15 +460,36 @@ def run_ours(args, dist: Dist):
     # per-stage kernel time (CUDA events around each kernel, same stream) for the roofline
     stage_us = pme.pme_profile_stages(plan, frames[0], q, forces, reps=200)
     result["stage_us"] = {k: round(v, 3) for k, v in stage_us.items()}
+    # Each isolated time includes that kernel's own launch and drain, so they sum to more than one pipelined
+    # evaluation; the shares below scale them onto the measured step.
+    tot_iso = sum(stage_us.values())
+    result["stage_us_share_of_step"] = {k: round(v / tot_iso * value, 3) for k, v in stage_us.items()}
     sb = stage_bytes(s.n, s.K, s.p)
     dom = max(stage_us, key=stage_us.get)
     peak, src = measured_peaks()
-    achieved = sb[dom] / (stage_us[dom] * 1e-6) / 1e9
+    atom = measure_atomic_peaks(dev)
+    result["atomic_peaks"] = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in atom.items()}
+    achieved_b = sb[dom] / (stage_us[dom] * 1e-6) / 1e9
     traffic = traffic_record(dom)
-    result["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                          "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
-                          "algorithmic_bytes": sb[dom], "kernel_us": round(stage_us[dom], 3)}
+    hbm_line = {"kernel": dom, "bound": "hbm", "achieved": round(achieved_b, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved_b / peak, 4), "traffic": traffic,
+                "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)", "algorithmic_bytes": sb[dom],
+                "kernel_us": round(stage_us[dom], 3)}
+    if dom == "spread":
+        # spreading is bound by its shared-memory atomics: n p^3 64-bit additions (two 32-bit atomics each)
+        na = spread_atomics(s.n, s.p)
+        rate = na / (stage_us[dom] * 1e-6)
+        result["roofline"] = {"kernel": dom, "bound": "atomic", "achieved": round(rate, 1),
+                              "peak": round(atom["smem_i32_atomics_per_s"], 1), "unit": "atomic/s",
+                              "frac": round(rate / atom["smem_i32_atomics_per_s"], 4), "traffic": traffic,
+                              "peak_source": "measured in this run: conflict-free shared-memory int32 atomicAdd "
+                                             "probe (atomic_peaks)",
+                              "algorithmic_atomics": na, "kernel_us": round(stage_us[dom], 3),
+                              "frac_in_step": round(na / (result["stage_us_share_of_step"][dom] * 1e-6)
+                                                    / atom["smem_i32_atomics_per_s"], 4)}
+        result["roofline_hbm"] = hbm_line
+    else:
+        result["roofline"] = hbm_line
     # The meshes stay in L2 between stages, so L2 bandwidth is the other ceiling: per stage (its algorithmic
     # bytes over its own launch time) and for the whole evaluation (all stages' bytes over the pipelined time
     # per evaluation), against an L2-resident copy measured here.
@@ -389,6 +505,36 @@ def run_ours(args, dist: Dist):
                        "frac_l2": round(sb[k] / (stage_us[k] * 1e-6) / 1e9 / l2, 4),
                        "frac_hbm": round(sb[k] / (stage_us[k] * 1e-6) / 1e9 / peak, 4)} for k in sb},
     }
+    # oracle error of one evaluated frame (frame 500 of the trajectory, through the synchronous entry point)
+    with torch.cuda.stream(stream):
+        pos_s = torch.from_numpy(sample_pos).to(dev)
+        E_s, V_s = pme.pme_compute(plan, pos_s, q, forces)
+        F_s = forces.cpu().numpy()
+    result["accuracy"] = {"sample": f"frame {SAMPLE} of the jittered trajectory",
+                          **errors_vs_oracle(E_s, V_s, F_s, wl.System(sample_pos, s.q, s.box, s.K, s.p, s.beta))}
+
+    # cuFFT, for comparison only (never part of the library): a 64^3 real-to-complex and complex-to-real
+    # transform pair of torch.fft with an elementwise multiply between them, against this library's transform
+    # and influence stages
+    x = torch.randn(s.K, device=dev)
+    tab = torch.rand((s.K[0], s.K[1], s.K[2] // 2 + 1), device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            y = torch.fft.irfftn(torch.fft.rfftn(x) * tab, s=s.K)
+        nr = 500
+        start.record(stream)
+        for _ in range(nr):
+            y = torch.fft.irfftn(torch.fft.rfftn(x) * tab, s=s.K)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    result["cufft_comparison"] = {
+        "rfftn_multiply_irfftn_us": round(1000.0 * start.elapsed_time(end) / nr, 3),
+        "ours_fwd_influence_inv_us_isolated": round(stage_us["fft_fwd"] + stage_us["influence"] + stage_us["fft_inv"], 3),
+        "ours_fwd_influence_inv_us_share_of_step": round(sum(result["stage_us_share_of_step"][k]
+                                                             for k in ("fft_fwd", "influence", "fft_inv")), 3),
+        "note": "torch.fft (cuFFT) on the same GPU, FP32, 64^3, eager launches; ours includes the energy and virial "
+                "reduction and the int64 mesh conversion; comparison only"}
+    del y, x, tab
     return result, sampler, plan, locals()
 
 
@@ -416,73 +562,102 @@ def run_e2e(pme, plan, s, steps: int):
         (time.time() - dt, time.time())
 
 
-def cpu_baseline(target_seconds: float = 15.0):
-    """The FP64 oracle as it stands (single thread), timed on full evaluations of the same workload."""
+def cpu_baseline(target_seconds: float = 12.0):
+    """The FP64 oracle as it stands, timed on full evaluations of the headline workload: single-threaded
+    (the reported value), then across all host cores (its OpenMP loops), plus the numpy-FFT FP64 context
+    baseline. Median of the runs; table set-up excluded from the numpy figure, included in the oracle's
+    (the oracle recomputes its tables every call)."""
     import oracle
+    from oracle import numpy_spme
     from paper_2009_12617_gb300 import workloads as wl
 
     oracle.build()
     s = wl.headline_system(seed=2)
     pos, q = s.pos.astype(np.float64), s.q.astype(np.float64)
-    times = []
-    t_start = time.perf_counter()
-    while True:
-        t0 = time.perf_counter()
-        oracle.spme(pos, q, s.K, s.p, s.beta, s.box)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > target_seconds or len(times) >= 10:
-            break
-    v = 1e6 * statistics.median(times)
-    return {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full evaluations of the 65536-atom 64^3 p=4 box (median)",
-            "cpu": _cpu_model()}
+    nproc = os.cpu_count() or 1
 
+    def timed(fn, budget, cap=10):
+        times, t_start = [], time.perf_counter()
+        while True:
+            t0 = time.perf_counter()
+            fn()
+            times.append(time.perf_counter() - t0)
+            if time.perf_counter() - t_start > budget or len(times) >= cap:
+                return 1e6 * statistics.median(times), len(times)
 
-def _cpu_model() -> str:
+    oracle.set_threads(1)
+    v1, n1 = timed(lambda: oracle.spme(pos, q, s.K, s.p, s.beta, s.box), target_seconds)
+    used = oracle.set_threads(nproc)
     try:
-        with open("/proc/cpuinfo") as f:
-            for ln in f:
-                if ln.lower().startswith(("model name", "cpu part", "hardware")):
-                    return ln.split(":", 1)[1].strip()
-    except OSError:
-        pass
-    return os.uname().machine
+        vall, nall = timed(lambda: oracle.spme(pos, q, s.K, s.p, s.beta, s.box), target_seconds / 2)
+    finally:
+        oracle.set_threads(1)
+    plan = numpy_spme.Plan(s.K, s.p, s.beta, s.box)
+    vnp, nnp = timed(lambda: plan.evaluate(pos, q), target_seconds / 2)
+    return {"value": round(v1, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n1} full evaluations of the 65536-atom 64^3 p=4 box, single thread (median)",
+            "cpu": cpu_model(), "nproc": nproc,
+            "all_cores": {"value": round(vall, 1), "unit": UNIT, "cores": used, "kind": "oracle",
+                          "sample": f"{nall} full evaluations, OpenMP over {used} threads (median)"},
+            "numpy_fft_fp64": {"value": round(vnp, 1), "unit": UNIT, "cores": 1, "kind": "context baseline",
+                               "sample": f"{nnp} evaluations with numpy's pocketfft in FP64, tables precomputed "
+                                         "(median); not the oracle"}}
 
 
 def run_reference(args, dist: Dist):
+    """The reference arm: the FP64 oracle, single-threaded, one full evaluation of the headline box per step
+    (W warm-up steps, then K timed steps, capped near two minutes of work)."""
     if dist.rank != 0:
         return
     import oracle
     from paper_2009_12617_gb300 import workloads as wl
 
     oracle.build()
+    oracle.set_threads(1)
     s = wl.headline_system(seed=2)
     pos, q = s.pos.astype(np.float64), s.q.astype(np.float64)
     t0 = time.perf_counter()
-    for _ in range(max(1, min(args.warmup, 1))):
+    for _ in range(max(1, args.warmup)):
         oracle.spme(pos, q, s.K, s.p, s.beta, s.box)
-    t_one = time.perf_counter() - t0
-    executed = max(1, min(args.steps, int(120.0 / max(t_one, 1e-3))))
+    t_one = (time.perf_counter() - t0) / max(1, args.warmup)
+    executed = max(1, min(args.steps, int(150.0 / max(t_one, 1e-3))))
     times = []
     for i in range(executed):
         t0 = time.perf_counter()
         oracle.spme(pos, q, s.K, s.p, s.beta, s.box)
         times.append(time.perf_counter() - t0)
     v = 1e6 * statistics.mean(times)
-    sample = (f"{executed} of {args.steps} requested steps, each one full FP64 oracle evaluation of the "
-              f"65536-atom 64^3 p=4 box (capped to about 2 minutes)")
+    sample = (f"{executed} of {args.steps} requested steps timed, each one full FP64 oracle evaluation of the "
+              f"65536-atom 64^3 p=4 box (frame 0), single thread, after {max(1, args.warmup)} warm-up steps")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": dist.world,
-            "steps": executed, "warmup": 1, "ms_per_step": round(v / 1000.0, 3), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": round(v / PAPER_US, 3), "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "65536-atom water-like box, cubic 86.9 A, 64^3 mesh, p=4, beta=0.34/A"},
-            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": executed, "warmup": max(1, args.warmup), "ms_per_step": round(v / 1000.0, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": round(v / PAPER_US, 3), "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def spawn_ranks(args) -> int:
+    """--gpus N > 1 outside torchrun: run this command again under torchrun with N processes."""
+    import socket
+
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args))
     dist = Dist()
+    if dist.world != args.gpus and dist.rank == 0:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE {dist.world}; using {dist.world} ranks", file=sys.stderr)
     try:
         if args.impl == "reference":
             run_reference(args, dist)
@@ -498,9 +673,9 @@ def main():
             torch.cuda.set_device(dist.local)
             sampler = ClockSampler(dist.local)
             out = {}
-            table = {"batched": leg_batched, "serving": leg_serving, "large": leg_large}
+            table = {"batched": leg_batched, "serving": leg_serving, "large": leg_large, "profile": leg_profile}
             for name in args.legs.split(","):
-                out.update(table[name](args, sampler))
+                out.update(table[name](args, sampler, dist))
             out["clocks"] = sampler.summary()
             if dist.rank == 0:
                 print(json.dumps(out), flush=True)
@@ -508,17 +683,24 @@ def main():
         result, sampler, plan, ctx = run_ours(args, dist)
         from paper_2009_12617_gb300 import pme
 
-        if dist.rank == 0:
-            if not args.no_extras:
+        if not args.no_extras:
+            if dist.rank == 0:
                 e2e, win = run_e2e(pme, plan, ctx["s"], steps=max(20, min(args.steps // 20, 500)))
                 sampler.window(*win)
                 result["e2e"] = e2e
-                for extra in _extras():
-                    try:
-                        result.update(extra(args, sampler))
-                    except Exception as exc:  # an extra leg failing must not hide the headline number
+            for extra in _extras():
+                if extra is leg_large and dist.rank != 0:
+                    continue
+                try:
+                    out = extra(args, sampler, dist)
+                    if dist.rank == 0:
+                        result.update(out)
+                except Exception as exc:  # an extra leg failing must not hide the headline number
+                    if dist.rank == 0:
                         result.setdefault("errors", []).append(f"{extra.__name__}: {exc}")
+            if dist.rank == 0:
                 result["cpu_baseline"] = cpu_baseline()
+        if dist.rank == 0:
             result["clocks"] = sampler.summary()
             print(json.dumps(result), flush=True)
         else:
@@ -528,17 +710,46 @@ def main():
         dist.close()
 
 
-def leg_batched(args, sampler):
-    """64 uneven water-like systems (atom counts log-uniform 1024..32768, meshes 32..64) evaluated through the
-    batch API (one graph per step: grouped stage launches, the mesh-shape groups in parallel), against one
-    launch sequence per system (eager, and replayed from a graph)."""
+def _time_batch(pme, b, pos, q, F, ev, stream, reps, sampler, dist=None):
+    """ms per batch evaluation: warm-up, then reps graph replays bracketed by CUDA events on the batch stream
+    (and, across ranks, by barriers with the max taken)."""
+    import torch
+
+    st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            pme.pme_batch_enqueue(b, pos, q, F, ev)
+        pme.pme_batch_sync(b)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.time()
+        st.record(stream)
+        for _ in range(reps):
+            pme.pme_batch_enqueue(b, pos, q, F, ev)
+        en.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        sampler.window(t0, time.time())
+        pme.pme_batch_sync(b)
+    ms = st.elapsed_time(en) / reps
+    return dist.max(ms) if dist else ms
+
+
+def leg_batched(args, sampler, dist):
+    """64 uneven water-like systems (atom counts log-uniform 1024..32768, meshes 32..64), sharded across the
+    ranks, evaluated through the batch API (one graph per step: grouped stage launches, the mesh-shape groups
+    in parallel; and, for comparison, the persistent work-list kernel), against one launch sequence per
+    system (eager, and replayed from a graph). One system's result is checked against the oracle."""
     import torch
 
     from paper_2009_12617_gb300 import pme
     from paper_2009_12617_gb300 import workloads as wl
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    systems = wl.batch_systems(64, seed=4)
+    all_systems = wl.batch_systems(64, seed=4)
+    systems = shard(all_systems, dist.rank, dist.world)
     stream = torch.cuda.Stream(dev)
     plans = [pme.pme_create(s.K, s.p, s.beta, s.box, stream=stream) for s in systems]
     ns = [s.n for s in systems]
@@ -552,20 +763,13 @@ def leg_batched(args, sampler):
     reps = 20
     out = {}
     try:
+        t_batch = _time_batch(pme, b, pos, q, F, ev, stream, reps, sampler, dist)  # ms per batch, max over ranks
+        Fb, evb = F.clone(), ev.clone()
+        pme.pme_batch_set_strategy(b, pme.PME_BATCH_PERSISTENT)
+        t_pers = _time_batch(pme, b, pos, q, F, ev, stream, reps, sampler, dist)
+        same_pers = bool(torch.equal(F, Fb) and torch.equal(ev, evb))
+        pme.pme_batch_set_strategy(b, pme.PME_BATCH_AUTO)
         with torch.cuda.stream(stream):
-            for _ in range(3):
-                pme.pme_batch_enqueue(b, pos, q, F, ev)
-            pme.pme_batch_sync(b)
-            t0 = time.time()
-            st.record(stream)
-            for _ in range(reps):
-                pme.pme_batch_enqueue(b, pos, q, F, ev)
-            en.record(stream)
-            torch.cuda.synchronize(dev)
-            sampler.window(t0, time.time())
-            pme.pme_batch_sync(b)
-            t_batch = st.elapsed_time(en) / reps  # ms per batch of 64
-            Fb, evb = F.clone(), ev.clone()
             # one launch sequence per system, same stream
             for i, pl in enumerate(plans):
                 pme.pme_reserve(pl, ns[i])
@@ -579,7 +783,7 @@ def leg_batched(args, sampler):
                     pme.pme_enqueue(pl, *views[i])
             en.record(stream)
             torch.cuda.synchronize(dev)
-            t_eager = st.elapsed_time(en) / reps
+            t_eager = dist.max(st.elapsed_time(en) / reps)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
                 for i, pl in enumerate(plans):
@@ -591,25 +795,33 @@ def leg_batched(args, sampler):
                 g.replay()
             en.record(stream)
             torch.cuda.synchronize(dev)
-            t_graph = st.elapsed_time(en) / reps
+            t_graph = dist.max(st.elapsed_time(en) / reps)
             for pl in plans:
                 pme.pme_sync(pl)
         same = bool(torch.equal(F, Fb) and torch.equal(ev, evb))
-        nsys, atoms = len(systems), int(sum(ns))
-        alg = sum(sum(stage_bytes(s.n, s.K, s.p).values()) for s in systems)
+        # oracle error of the batch's result for one system (the largest of this rank's share)
+        k = int(np.argmax(ns))
+        acc = errors_vs_oracle(float(evb[k, 0]), evb[k, 1:].cpu().numpy(), Fb[offs[k]:offs[k + 1]].cpu().numpy(),
+                               systems[k])
+        nsys, atoms = len(all_systems), int(sum(s.n for s in all_systems))
+        alg = sum(sum(stage_bytes(s.n, s.K, s.p).values()) for s in all_systems)
         peak, src = measured_peaks()
         achieved = alg / (t_batch * 1e-3) / 1e9
         out = {"batched": {
             "workload": "64 water-like boxes, N log-uniform in [1024, 32768] (seed 4), 0.1 atoms/A^3, K in {32,40,48,64} "
                         "by 1.4 A spacing, p=4; per step one CUDA graph: systems grouped by mesh shape, one launch "
                         "per stage per group, the groups as parallel branches",
-            "systems": nsys, "atoms": atoms, "meshes": sorted({s.K[0] for s in systems}),
+            "systems": nsys, "atoms": atoms, "meshes": sorted({s.K[0] for s in all_systems}), "ranks": dist.world,
             "evals_per_s": round(nsys / (t_batch * 1e-3), 1), "us_per_batch": round(t_batch * 1e3, 2),
             "atom_evals_per_s": round(atoms / (t_batch * 1e-3), 1),
+            "persistent_work_list": {"evals_per_s": round(nsys / (t_pers * 1e-3), 1),
+                                     "us_per_batch": round(t_pers * 1e3, 2), "bit_identical_to_grouped": same_pers},
             "one_system_per_launch": {"eager_evals_per_s": round(nsys / (t_eager * 1e-3), 1),
                                       "graph_evals_per_s": round(nsys / (t_graph * 1e-3), 1)},
             "speedup_vs_graph_of_single_launches": round(t_graph / t_batch, 3),
             "bit_identical_to_single": same,
+            "accuracy": {"sample": f"system {dist.rank + k * dist.world} ({systems[k].n} atoms, {systems[k].K[0]}^3), "
+                                   "batch result", **acc},
             "gpu_launches_per_step": 2 + 6 * len({(s.K, s.p) for s in systems}),
             "roofline": {"kernel": "all grouped stage launches of one step (64 systems)", "bound": "hbm",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -622,11 +834,27 @@ def leg_batched(args, sampler):
     return out
 
 
-def leg_serving(args, sampler, n_req: int = 4000):
+def serving_stream(n_req: int, rank: int, world: int):
+    """The served request stream (Poisson arrivals at 20k/s, seed 5; 90% over the 64 batch systems, 10% over
+    8 headline systems: global pool indices 0..71) and this rank's part of it: the pool indices it owns
+    (round robin), and the arrival times and local pool indices of the requests for those systems."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    gaps = rng.exponential(1.0 / 20000.0, n_req)
+    arrival_all = np.cumsum(gaps)
+    which_all = np.where(rng.random(n_req) < 0.9, rng.integers(0, 64, n_req), 64 + rng.integers(0, 8, n_req))
+    mine = shard(list(range(72)), rank, world)
+    local = {g: i for i, g in enumerate(mine)}
+    keep = np.array([int(w) in local for w in which_all])
+    which = np.array([local[int(w)] for w in which_all[keep]], dtype=np.int64)
+    return arrival_all, which_all, mine, arrival_all[keep], which
+
+
+def leg_serving(args, sampler, dist, n_req: int = 4000):
     """Poisson arrivals (20k requests/s, seed 5) drawing 90% from 64 config-4 systems and 10% from 8
     65536-atom / 64^3 systems, all with resident plans; every request uses a freshly jittered frame. The
     server admits by a 40 GB device budget and 128 slots; the comparison serves the same stream one system
-    per launch, synchronously, in arrival order."""
+    per launch, synchronously, in arrival order. Across ranks the systems are sharded and each rank serves
+    the requests for its own systems; one served result is checked against the oracle."""
     import collections
 
     import torch
@@ -637,21 +865,19 @@ def leg_serving(args, sampler, n_req: int = 4000):
     dev = torch.device("cuda", torch.cuda.current_device())
     small = wl.batch_systems(64, seed=4)
     big = [wl.headline_system(seed=10 + i) for i in range(8)]
-    pool = small + big
+    arrival_all, which_all, mine, arrival, which = serving_stream(n_req, dist.rank, dist.world)
+    pool = [(small + big)[g] for g in mine]
     plans = [pme.pme_create(s.K, s.p, s.beta, s.box) for s in pool]
     NF, NBUF = 2, 4
     frames, qs, outs = [], [], []
     for i, s in enumerate(pool):
         L = float(s.box[0, 0])
-        f1 = wl.jitter(s.pos, L, 500 + i, 0)
+        f1 = wl.jitter(s.pos, L, 500 + mine[i], 0)
         frames.append([torch.from_numpy(s.pos).to(dev), torch.from_numpy(f1).to(dev)])
         qs.append(torch.from_numpy(s.q).to(dev))
         outs.append([torch.empty((s.n, 3), dtype=torch.float32, device=dev) for _ in range(NBUF)])
         pme.pme_reserve(plans[i], s.n)
-    rng = np.random.Generator(np.random.PCG64(5))
-    gaps = rng.exponential(1.0 / 20000.0, n_req)
-    arrival = np.cumsum(gaps)
-    which = np.where(rng.random(n_req) < 0.9, rng.integers(0, 64, n_req), 64 + rng.integers(0, 8, n_req))
+    n_all, n_req = n_req, len(which)
     srv = pme.pme_server_create(40 * (1 << 30), 128)
     lat = np.zeros(n_req)
     uses = collections.Counter()
@@ -664,6 +890,8 @@ def leg_serving(args, sampler, n_req: int = 4000):
         busy_bufs = collections.Counter()
         done = 0
         nxt = 0
+        torch.cuda.synchronize()
+        dist.barrier()
         t0 = time.perf_counter()
         while done < n_req:
             now = time.perf_counter() - t0
@@ -693,6 +921,12 @@ def leg_serving(args, sampler, n_req: int = 4000):
         elapsed = time.perf_counter() - t0
         sampler.window(time.time() - elapsed, time.time())
         stats = pme.pme_server_stats(srv)
+        # one served result against the oracle: a 65536-atom system if this rank has one, frame 0
+        k = max(range(len(pool)), key=lambda i: pool[i].n)
+        Fk = torch.full_like(frames[k][0], float("nan"))
+        t = pme.pme_submit(srv, plans[k], frames[k][0], qs[k], Fk)
+        pme.pme_poll(srv, t, block=True)
+        acc = errors_vs_oracle(t.energy.value, np.array(t.virial[:]), Fk.cpu().numpy(), pool[k])
     finally:
         pme.pme_server_destroy(srv)
     atoms = np.array([pool[i].n for i in which])
@@ -710,13 +944,25 @@ def leg_serving(args, sampler, n_req: int = 4000):
     elapsed1 = time.perf_counter() - t0
     for pl in plans:
         pme.pme_destroy(pl)
+    parts = gather_all(dist, (lat.tolist(), lat1.tolist(), float(elapsed), float(elapsed1), int(atoms.sum()),
+                              stats["p50_us"], stats["p99_us"], stats["waves"]))
+    lat = np.concatenate([np.array(x[0]) for x in parts])
+    lat1 = np.concatenate([np.array(x[1]) for x in parts])
+    elapsed, elapsed1 = max(x[2] for x in parts), max(x[3] for x in parts)
+    atoms = np.array([sum(x[4] for x in parts)])
+    n_req = n_all
+    if dist.world > 1:  # server-side percentiles: the worst rank's
+        stats = {"p50_us": max(x[5] for x in parts), "p99_us": max(x[6] for x in parts),
+                 "waves": sum(x[7] for x in parts)}
+    arrival = arrival_all
     return {"serving": {
         "workload": "Poisson arrivals 20k req/s (seed 5), 90% from 64 config-4 boxes, 10% from 8 65536-atom 64^3 boxes, "
                     "resident plans, jittered frames, budget 40 GB, 128 slots",
         "requests": n_req, "offered_req_per_s": round(n_req / arrival[-1], 1),
         "throughput_req_per_s": round(n_req / elapsed, 1), "atom_evals_per_s": round(atoms.sum() / elapsed, 1),
         "p50_us": round(1e6 * float(np.percentile(lat, 50)), 2), "p99_us": round(1e6 * float(np.percentile(lat, 99)), 2),
-        "latency_from": "request arrival time to completion seen by the client",
+        "latency_from": "request arrival time to completion seen by the client", "ranks": dist.world,
+        "accuracy": {"sample": f"one served request on a {pool[k].n}-atom system, frame 0", **acc},
         "server_p50_us": round(stats["p50_us"], 2), "server_p99_us": round(stats["p99_us"], 2),
         "waves": stats["waves"],
         "one_system_per_launch": {"throughput_req_per_s": round(n_req / elapsed1, 1),
@@ -724,13 +970,12 @@ def leg_serving(args, sampler, n_req: int = 4000):
                                   "p99_us": round(1e6 * float(np.percentile(lat1, 99)), 2)}}}
 
 
-def leg_large(args, sampler):
+def leg_large(args, sampler, dist=None):
     """Precision study at the largest mesh: 262144 water-like atoms, 137.9 A, 128^3, p = 6. Time per
     evaluation (CUDA graph replays) and the energy / RMS-force / virial error of the FP32 path against the
     FP64 oracle on the same inputs."""
     import torch
 
-    import oracle
     from paper_2009_12617_gb300 import pme
     from paper_2009_12617_gb300 import workloads as wl
 
@@ -762,18 +1007,41 @@ def leg_large(args, sampler):
             sampler.window(t0, time.time())
         us = 1000.0 * st.elapsed_time(en) / reps
         stages = pme.pme_profile_stages(plan, pos, q, F, reps=20)
-        oracle.build()
-        r = oracle.spme(s.pos.astype(np.float64), s.q.astype(np.float64), s.K, s.p, s.beta, s.box)
-        Fh = F.cpu().numpy().astype(np.float64)
+        acc = errors_vs_oracle(E, V, F.cpu().numpy(), s)
         return {"large_grid": {
             "workload": "262144 water-like atoms (87380 triplets + 2 pairs), cubic 137.9 A, 128^3, p=6, beta=0.34/A",
             "us_per_eval": round(us, 2), "stage_us": {k: round(v, 2) for k, v in stages.items()},
             "path": "FP32 mesh arithmetic (int64 fixed-point charge mesh, double-float energy sums)",
-            "rel_energy_error": float(abs(E - r["energy"]) / abs(r["energy"])),
-            "rms_force_error": float(np.sqrt(np.mean((Fh - r["forces"]) ** 2) / np.mean(r["forces"] ** 2))),
-            "rel_virial_error": float(np.max(np.abs(V - r["virial"])) / np.max(np.abs(r["virial"])))}}
+            **{k: acc[k] for k in ("rel_energy_error", "rms_force_error", "rel_virial_error")}}}
     finally:
         pme.pme_destroy(plan)
+
+
+def leg_profile(args, sampler, dist=None):
+    """A short fixed sequence for ncu captures: 10 evaluations of the 65536-atom 64^3 p=4 box, then 5 of the
+    262144-atom 128^3 p=6 box, eager launches on device arrays (six stage kernels each, in stage order)."""
+    import torch
+
+    from paper_2009_12617_gb300 import pme
+    from paper_2009_12617_gb300 import workloads as wl
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    for name, s, reps in (("headline", wl.headline_system(seed=2), 10), ("large", wl.large_system(seed=3), 5)):
+        plan = pme.pme_create(s.K, s.p, s.beta, s.box)
+        try:
+            pos = torch.from_numpy(s.pos).to(dev)
+            q = torch.from_numpy(s.q).to(dev)
+            F = torch.empty_like(pos)
+            ev = torch.zeros(7, dtype=torch.float64, device=dev)
+            pme.pme_reserve(plan, s.n)
+            for _ in range(reps):
+                pme.pme_enqueue(plan, pos, q, F, ev)
+            pme.pme_sync(plan)
+            out[name] = {"evaluations": reps, "energy": float(ev[0])}
+        finally:
+            pme.pme_destroy(plan)
+    return {"profile": out}
 
 
 def _extras():
