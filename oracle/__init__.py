@@ -12,7 +12,8 @@ Parity status of each function (what pins it is in tests/test_oracle_pins.py):
   spme (E, virial, F)      pinned: Ewald convergence, NaCl Madelung constant, finite differences of E
                            (positions and strain), phi identity, one-cell translation invariance
   ewald_recip/real/self    pinned: independent numpy Ewald, Madelung constant at two beta values, FD forces;
-                           real-space virial by central differences of the energy under strain
+                           real-space virial by central differences of the energy under strain;
+  ewald_real_rows          pinned: equals ewald_real's forces and per-atom energies row by row
 """
 from __future__ import annotations
 
@@ -73,6 +74,9 @@ def _load():
         L.oracle_ewald_real.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, ctypes.c_double, _dp,
                                         _dp, _dp]
         L.oracle_ewald_real.restype = ctypes.c_int
+        L.oracle_ewald_real_rows.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, _dp, ctypes.c_double,
+                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _dp, _dp]
+        L.oracle_ewald_real_rows.restype = ctypes.c_int
         L.oracle_ewald_self.argtypes = [ctypes.c_int64, _dp, ctypes.c_double]
         L.oracle_ewald_self.restype = ctypes.c_double
         L.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -230,6 +234,21 @@ def ewald_real(pos, q, beta, box, rcut: float | None = None) -> dict:
                                  _p(F), _p(vir)) != 0:
         raise ValueError("singular box")
     return {"energy": e.value, "forces": F, "virial": vir}
+
+
+def ewald_real_rows(pos, q, beta, box, rows, rcut: float | None = None) -> dict:
+    """Real-space sum for the listed atoms only: {'e' (per row: sum_j q_i q_j erfc/r), 'forces' (rows, 3)}."""
+    pos = _d(pos).reshape(-1, 3)
+    q = _d(q).reshape(-1)
+    box = _d(box).reshape(9)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    rcut = 6.0 / beta if rcut is None else rcut
+    e = np.zeros(len(rows))
+    F = np.zeros((len(rows), 3))
+    if _load().oracle_ewald_real_rows(pos.shape[0], _p(pos), _p(q), float(beta), _p(box), float(rcut), len(rows),
+                                      rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(e), _p(F)) != 0:
+        raise ValueError("singular box")
+    return {"e": e, "forces": F}
 
 
 def ewald_self(q, beta) -> float:

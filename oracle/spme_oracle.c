@@ -16,7 +16,8 @@
  *       M_p'(x) = M_{p-1}(x) - M_{p-1}(x - 1).
  *   (3) Q(k) = sum_i q_i prod_alpha sum_{n in Z} M_p(u_i,alpha - k_alpha - n K_alpha).
  *   (4) Qhat(m) = sum_k Q(k) exp(+2 pi i sum_alpha m_alpha k_alpha / K_alpha)   (direct, unnormalised).
- *   (5) |b_alpha(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K_alpha)|^2 ; B(m) = prod |b_alpha|^2.
+ *   (5) |b_alpha(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K_alpha)|^2 ; B(m) = prod |b_alpha|^2
+ *       (odd p: at m = K/2, where the sum vanishes, the mean of the neighbouring denominators).
  *   (6) m' = sum_alpha mt_alpha a*_alpha with mt = m for m <= K/2 else m - K ;
  *       C(m) = exp(-pi^2 |m'|^2 / beta^2) / (pi V |m'|^2), C(0) = 0.
  *   (7) E = 1/2 sum_m B C |Qhat|^2.
@@ -279,8 +280,8 @@ void oracle_dft3_full(const int K[3], int sign, const double *in_re, const doubl
 /* ------------------------------------------------------------------------------------------------------ */
 /* (5)/(6) B-spline moduli and influence function                                                          */
 
-/* |b(m)|^2 for one dimension of length K, eq. (5). */
-double oracle_bmod2(int K, int p, int m) {
+/* The denominator |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K)|^2 of eq. (5). */
+static double bmod_denominator(int K, int p, int m) {
     double sr = 0.0, si = 0.0;
     for (int k = 0; k <= p - 2; ++k) {
         double c, s;
@@ -289,7 +290,17 @@ double oracle_bmod2(int K, int p, int m) {
         sr += M * c;
         si += M * s;
     }
-    return 1.0 / (sr * sr + si * si);
+    return sr * sr + si * si;
+}
+
+/* |b(m)|^2 for one dimension of length K, eq. (5). For odd p and even K the denominator vanishes at
+ * m = K/2 (the knot values M_p(1..p-1) are symmetric, so their alternating sum is zero); there the
+ * denominator is taken as the mean of its two neighbours m = K/2 - 1 and K/2 + 1 (the paper is silent: it
+ * uses p = 4 only; this is the usual convention of SPME codes for odd orders). */
+double oracle_bmod2(int K, int p, int m) {
+    if ((p & 1) && (K & 1) == 0 && 2 * m == K && K >= 4)
+        return 1.0 / (0.5 * (bmod_denominator(K, p, m - 1) + bmod_denominator(K, p, m + 1)));
+    return 1.0 / bmod_denominator(K, p, m);
 }
 
 static int64_t signed_freq(int64_t m, int64_t K) { return (m <= K / 2) ? m : m - K; }
@@ -546,6 +557,45 @@ int oracle_ewald_real(int64_t n, const double *pos, const double *q, double beta
     free(Ei);
     free(Wi);
     *energy = E;
+    return 0;
+}
+
+/* The same real-space sum restricted to the listed atoms: for each i = rows[k], e_rows[k] = sum_{j,n}' q_i q_j
+ * erfc(beta r)/r (so E_real = 1/2 sum_i e_i) and f_rows[3k..3k+2] = F_i, with the loops of oracle_ewald_real.
+ * For checking single atoms of systems too large for the full double sum. */
+int oracle_ewald_real_rows(int64_t n, const double *pos, const double *q, double beta, const double box[9],
+                           double rcut, int64_t nrows, const int64_t *rows, double *e_rows, double *f_rows) {
+    double recip[9], vol;
+    if (oracle_recip(box, recip, &vol) != 0) return -1;
+    int64_t nmax[3];
+    for (int al = 0; al < 3; ++al) {
+        const double *r = recip + 3 * al;
+        nmax[al] = (int64_t)ceil(rcut * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2])) + 1;
+    }
+    const double c2 = 2.0 * beta / sqrt(OR_PI);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nrows; ++k) {
+        const int64_t i = rows[k];
+        double e = 0.0, f[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t a = -nmax[0]; a <= nmax[0]; ++a)
+                for (int64_t b = -nmax[1]; b <= nmax[1]; ++b)
+                    for (int64_t c = -nmax[2]; c <= nmax[2]; ++c) {
+                        if (i == j && a == 0 && b == 0 && c == 0) continue;
+                        double d[3];
+                        for (int m = 0; m < 3; ++m)
+                            d[m] = pos[3 * i + m] - pos[3 * j + m] + a * box[m] + b * box[3 + m] + c * box[6 + m];
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 > rcut * rcut) continue;
+                        double r = sqrt(r2);
+                        double qq = q[i] * q[j];
+                        e += qq * erfc(beta * r) / r;
+                        double s = qq * (erfc(beta * r) / r + c2 * exp(-beta * beta * r2)) / r2;
+                        for (int m = 0; m < 3; ++m) f[m] += s * d[m];
+                    }
+        e_rows[k] = e;
+        for (int m = 0; m < 3; ++m) f_rows[3 * k + m] = f[m];
+    }
     return 0;
 }
 

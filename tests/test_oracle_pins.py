@@ -447,3 +447,62 @@ def test_ewald_real_virial_and_forces_are_derivatives(oracle_mod, tri):
             pm[i, d] -= h
             fd = -(oracle_mod.ewald_real(pp, q, beta, box)["energy"] - oracle_mod.ewald_real(pm, q, beta, box)["energy"]) / (2 * h)
             assert r["forces"][i, d] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_ewald_real_rows_match_full_sum(oracle_mod):
+    """The per-atom form (used to check single atoms of large systems) reproduces the full real-space sum:
+    its forces row by row, and 1/2 sum_i e_i = E_real."""
+    rng = np.random.default_rng(41)
+    box = _tri_box()
+    pos = rng.random((30, 3)) @ box
+    q = rng.normal(size=30)
+    q -= q.mean()
+    full = oracle_mod.ewald_real(pos, q, 0.5, box, rcut=7.0)
+    rows = oracle_mod.ewald_real_rows(pos, q, 0.5, box, np.arange(30), rcut=7.0)
+    np.testing.assert_allclose(rows["forces"], full["forces"], rtol=1e-13, atol=1e-14)
+    assert 0.5 * rows["e"].sum() == pytest.approx(full["energy"], rel=1e-13)
+
+
+@pytest.mark.parametrize("K", [8, 16, 30])
+def test_bmod_odd_order(oracle_mod, K):
+    """p = 5: the denominator |sum M5(k+1) e^{i k t}|^2 = |(1 + 11 e^{it} + 11 e^{2it} + e^{3it}) / 24|^2 has
+    the closed form ((2 cos(3t/2) + 22 cos(t/2)) / 24)^2 (knot values 1/24, 11/24, 11/24, 1/24); it vanishes
+    at t = pi (m = K/2), where the modulus takes the mean of the two neighbouring denominators."""
+    def den(t):
+        return ((2 * math.cos(1.5 * t) + 22 * math.cos(0.5 * t)) / 24) ** 2
+
+    for m in range(K):
+        t = 2 * math.pi * m / K
+        if 2 * m == K:
+            want = 1.0 / (0.5 * (den(2 * math.pi * (m - 1) / K) + den(2 * math.pi * (m + 1) / K)))
+        else:
+            want = 1.0 / den(t)
+        assert oracle_mod.bmod2(K, 5, m) == pytest.approx(want, rel=1e-12), m
+    # the knot values are symmetric, so the alternating sum (t = pi) is exactly zero
+    assert abs(den(math.pi)) < 1e-30
+
+
+def test_spme_odd_order_converges_and_forces_are_gradient(oracle_mod):
+    """p = 5 on a water-like box: SPME -> Ewald with slope >= p - 1 in energy and forces as the mesh doubles,
+    and the forces are -dE/dr by central differences (the m = K/2 modulus reading keeps E smooth)."""
+    pos, q, box = _small_water()
+    beta = 0.34
+    ref = oracle_mod.ewald_recip(pos, q, beta, box)
+    errE, errF = [], []
+    for K in (12, 24, 48):
+        r = oracle_mod.spme(pos, q, (K, K, K), 5, beta, box)
+        errE.append(abs(r["energy"] - ref["energy"]) / abs(ref["energy"]))
+        errF.append(np.sqrt(np.mean((r["forces"] - ref["forces"]) ** 2) / np.mean(ref["forces"] ** 2)))
+    for err in (errE, errF):
+        slopes = [math.log2(err[i] / err[i + 1]) for i in range(len(err) - 1)]
+        assert min(slopes) >= 4, (err, slopes)
+    K = (16, 18, 20)
+    r = oracle_mod.spme(pos, q, K, 5, beta, box)
+    h = 1e-5
+    for i in (0, 31):
+        for d in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = -(oracle_mod.spme(pp, q, K, 5, beta, box)["energy"] - oracle_mod.spme(pm, q, K, 5, beta, box)["energy"]) / (2 * h)
+            assert r["forces"][i, d] == pytest.approx(fd, rel=1e-6, abs=1e-9)
