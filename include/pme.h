@@ -48,7 +48,7 @@ typedef int64_t pme_ticket;
 typedef enum {
     PME_OK = 0,
     PME_EINVAL = 1,        /* invalid argument, or a non-finite / absurdly far position or charge */
-    PME_EUNSUPPORTED = 2,  /* valid SPME parameters this build does not implement (e.g. odd p) */
+    PME_EUNSUPPORTED = 2,  /* valid SPME parameters this build does not implement (e.g. p = 7) */
     PME_ENOMEM = 3,        /* device or host allocation failed, or over the server memory budget */
     PME_ECUDA = 4,         /* a CUDA runtime call failed (detail has the CUDA error string) */
     PME_EOVERFLOW = 5,     /* sum |q| too large for the 64-bit fixed-point charge mesh */
@@ -69,8 +69,9 @@ typedef enum {
  * cell). cuda_stream is a cudaStream_t (NULL = the legacy default stream) on the current device; every
  * launch of the plan goes to it.
  * Requirements: each K_alpha even, 8 <= K_alpha <= 128 and with no prime factor other than 2, 3, 5;
- * p in {4, 6, 8} and p <= min(K); beta > 0 and finite. Invalid values return PME_EINVAL; odd p returns
- * PME_EUNSUPPORTED. The plan precomputes the influence-function table B(m)C(m) in FP64 (stored as an
+ * p in {4, 5, 6, 8} and p <= min(K); beta > 0 and finite. Invalid values return PME_EINVAL; other orders
+ * return PME_EUNSUPPORTED. For the odd order the B-spline modulus denominator, which vanishes at m = K/2,
+ * takes the mean of its two neighbours there. The plan precomputes the influence-function table B(m)C(m) in FP64 (stored as an
  * unevaluated sum of two floats) and the FFT twiddles, and allocates the mesh (about 30 bytes per mesh
  * point). On success *out receives the plan; on failure *out is NULL. */
 pme_status pme_create(const int K[3], int p, double beta, const double box[9], void *cuda_stream, pme_plan **out);
@@ -182,6 +183,106 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
                                void *cuda_stream);
 
 /* ------------------------------------------------------------------------------------------------------ */
+/* Autotuning of the launch configuration                                                                  */
+
+/* Paper: Sec. IV-A and Table III size the FFT and spreading pipelines to each problem size on the FPGA; the
+ * GPU counterpart is choosing, per mesh and atom density, the spreading / force-interpolation tile edge
+ * (8^3 or 16^3 mesh points) and CTA size (128 or 256 threads). Every such choice gives bit-identical results
+ * (an exact integer charge mesh; each atom's force summed over its support in a fixed order), so tuning
+ * changes only speed. */
+typedef struct {
+    int tile_edge;       /* chosen tile edge (8 or 16 mesh points) */
+    int tile_threads;    /* chosen spread / force CTA size (128 or 256) */
+    double us_per_eval;  /* its time per evaluation (0 when taken from the cache) */
+    double default_us;   /* the default configuration's time (0 when taken from the cache) */
+    int candidates;      /* configurations tried */
+    int rejected;        /* configurations whose results differed from the default's (never expected) */
+    int from_cache;      /* 1 when the choice came from the cache file */
+} pme_tune_result;
+enum { PME_TUNE_FORCE = 1 };
+
+/* Choose the plan's configuration for n atoms like these: unless flags has PME_TUNE_FORCE, a choice cached
+ * for (device, mesh, order, atoms-per-tile class) is applied; otherwise every candidate runs reps timed
+ * evaluations (CUDA events on the plan stream) on the caller's DEVICE arrays pos, q, forces (forces receive
+ * the last result), its results are compared bit for bit with the default configuration's, and the fastest
+ * identical one is kept for the plan and written to the cache. Synchronous; do not call while capturing a
+ * graph. out (host) may be NULL. */
+pme_status pme_autotune(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces, int reps, int flags,
+                        pme_tune_result *out);
+
+/* Cache file of tuned choices (JSON, read on first use and rewritten after each tuning); NULL or "" keeps
+ * choices in memory only. Process-wide. */
+pme_status pme_tune_cache(const char *path);
+
+/* Set the plan's tile edge (0 = default, 8 or 16) and spread / force CTA size (0 = by atom density, 128 or
+ * 256) by hand; the current configuration is reported by pme_plan_get_tiling. Batches built on the plan pick
+ * the change up at their next pme_batch_enqueue. */
+pme_status pme_plan_set_tiling(pme_plan *plan, int tile_edge, int tile_threads);
+pme_status pme_plan_get_tiling(const pme_plan *plan, int *tile_edge, int *tile_threads);
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* Real-space and self terms (the rest of the Ewald sum)                                                   */
+
+/* Paper: Sec. II splits the electrostatics by the Ewald method into the long-range part SPME evaluates and
+ * a short-range real-space pair sum, which the paper's system computes on its own pipelines beside the
+ * long-range one (Sec. III, Fig. "MDOverview"). These calls evaluate that pair sum and the self term on the
+ * GPU, so that E = E_rec (pme_compute) + E_real + E_self is the full Ewald energy of point charges:
+ *   E_real = 1/2 sum_{i,j,n}' q_i q_j erfc(beta r) / r  over all periodic images with r = |r_i - r_j + n| <= rcut
+ *            (the primed sum skips i = j in the home cell),
+ *   F_i    = sum' q_i q_j [erfc(beta r) / r + 2 beta / sqrt(pi) exp(-beta^2 r^2)] (r_i - r_j + n) / r^2,
+ *   Pi_ab  = 1/2 sum' q_i q_j [erfc(beta r) / r + 2 beta / sqrt(pi) exp(-beta^2 r^2)] d_a d_b / r^2,
+ *   E_self = -beta / sqrt(pi) sum_i q_i^2.
+ * Units as for pme_compute. Use the same beta as the reciprocal plan. */
+typedef struct pme_real pme_real;  /* opaque: cell grid and scratch of one periodic cell */
+
+/* Create a real-space context for cell box[9] (rows a, b, c), splitting parameter beta (1/A) and cutoff
+ * rcut (A), launching on cuda_stream (NULL = legacy default stream) of the current device. Any cutoff up to
+ * four cell widths along each axis works (images of an atom itself included); a larger one, or a cell grid
+ * over 2^22 cells, returns PME_EUNSUPPORTED. Invalid values return PME_EINVAL. */
+pme_status pme_real_create(const double box[9], double beta, double rcut, void *cuda_stream, pme_real **out);
+
+/* Replace the cell (same rules as pme_real_create). Synchronous with respect to the context's stream. */
+pme_status pme_real_set_box(pme_real *rs, const double box[9]);
+
+/* Pre-allocate per-atom scratch for up to n atoms, so pme_real_enqueue allocates nothing afterwards. */
+pme_status pme_real_reserve(pme_real *rs, int64_t n);
+
+/* Asynchronous evaluation on DEVICE arrays pos (n x 3), q (n), forces (n x 3): the real-space forces are
+ * written to forces (accumulate = 0) or added to it (accumulate != 0, e.g. after pme_enqueue on the same
+ * stream wrote the reciprocal forces). When ev_dev (DEVICE, 8 doubles) is not NULL it receives (E_real,
+ * E_self, virial[6]) when the stream reaches that point. Results are bit-reproducible run to run and do not
+ * depend on the order of the atoms except through the summation order of each atom's neighbours. */
+pme_status pme_real_enqueue(pme_real *rs, const float *pos, const float *q, int64_t n, float *forces, int accumulate,
+                            double *ev_dev);
+
+/* Synchronous evaluation: forces (DEVICE, overwritten), and on the host e_real, e_self and virial[6]
+ * (either may be NULL). Returns PME_EINVAL for a non-finite or absurdly far position or charge. */
+pme_status pme_real_compute(pme_real *rs, const float *pos, const float *q, int64_t n, float *forces,
+                            double *e_real, double *e_self, double *virial);
+
+/* Release the context (it must be idle). */
+void pme_real_destroy(pme_real *rs);
+
+/* ------------------------------------------------------------------------------------------------------ */
+/* Multi-step loop on the device                                                                           */
+
+/* Paper: Sec. III runs multiple timesteps on the accelerators with no host communication beyond
+ * initialization and result collection. This call enqueues `steps` time steps on the plan stream, each:
+ * reciprocal-space forces of the plan into forces, plus (when rs is not NULL) the real-space forces of rs
+ * added to them, then a leapfrog update
+ *     v += (F * inv_mass) * dt,   x += v * dt     (each product and sum rounded once in FP32),
+ * all on DEVICE arrays: pos and vel (n x 3, updated in place), q (n), inv_mass (n, or NULL for unit mass),
+ * forces (n x 3, holds the last step's forces). Positions may leave the cell (every stage wraps them).
+ * When ev_steps (DEVICE, steps x 15 doubles) is not NULL, step s stores (E_rec, virial_rec[6], E_real,
+ * E_self, virial_real[6]) at ev_steps + 15 s (the real-space part zero without rs). Units as for
+ * pme_compute (dt in units where F * inv_mass * dt is a velocity in A per time unit). Chunks of up to 32
+ * steps are recorded once as one CUDA graph and replayed, so the host only enqueues; the call returns
+ * without waiting: pme_sync(plan) waits and reports device-side errors. rs must use the plan's device; its
+ * own stream is not used here. Results equal the same steps driven from the host bit for bit. */
+pme_status pme_run_steps(pme_plan *plan, pme_real *rs, float *pos, float *vel, const float *q, const float *inv_mass,
+                         int64_t n, float *forces, double dt, int steps, double *ev_steps);
+
+/* ------------------------------------------------------------------------------------------------------ */
 /* Batched evaluation: many independent systems per call, replayed from one CUDA graph                      */
 
 /* Paper: Sec. V-C runs several CS / FI pipelines per board and across boards (configurations 1_1 to 4_2)
@@ -216,6 +317,14 @@ pme_status pme_batch_sync(pme_batch *batch);
  * this library's own scheduling. */
 enum { PME_BATCH_AUTO = 0, PME_BATCH_GROUPED = 1, PME_BATCH_PERSISTENT = 2 };
 pme_status pme_batch_set_strategy(pme_batch *batch, int strategy);
+/* Tune a batch on its own packed DEVICE arrays (as for pme_batch_enqueue): the grouped strategy with every
+ * plan's spread / force CTA size at 128, 256 and the density rule, and the persistent strategy, each timed
+ * over reps evaluations after a bit-for-bit comparison with the first; the fastest identical one is kept
+ * (plans are set to 8^3 tiles, which grouped launches need). *strategy and *us_per_batch (host, either may
+ * be NULL) report the choice. Synchronous. */
+pme_status pme_batch_autotune(pme_batch *batch, const float *pos, const float *q, float *forces, double *ev_dev,
+                              int reps, int *strategy, double *us_per_batch);
+
 /* The strategy the next pme_batch_enqueue uses (PME_BATCH_GROUPED or PME_BATCH_PERSISTENT), or -1 for a
  * NULL batch. */
 int pme_batch_get_strategy(const pme_batch *batch);
@@ -263,6 +372,12 @@ const char *pme_strerror(pme_status s);
 /* Copy the calling thread's last error message (NUL-terminated, truncated to len) into buf. Returns the
  * status that produced it (PME_OK if none). */
 pme_status pme_last_error_detail(char *buf, size_t len);
+
+/* No counterpart in the paper: failure injection for tests of this library. When nth > 0, the nth
+ * allocation the library makes from now on (a host object, device memory or page-locked host memory; every
+ * entry point counts) fails as if the system were out of memory, and the call that made it returns
+ * PME_ENOMEM after releasing what it had allocated; nth = 0 disarms. Process-wide. */
+pme_status pme_debug_fail_alloc(int nth);
 
 /* No counterpart in the paper: a throughput probe of the resource the charge-spreading step (Sec. III-A
  * "Charge Spreading") is bound by on this GPU, for stating its achieved rate against a measured peak.

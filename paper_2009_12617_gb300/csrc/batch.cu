@@ -76,6 +76,7 @@ __device__ __forceinline__ void run_stage(const SysDev &d, int stage, int item, 
         case STAGE_BIN: call_bin(d, item, smem); break;
         case STAGE_SPREAD:
             if (d.p == 4) call_spread<4>(d, item, smem);
+            else if (d.p == 5) call_spread<5>(d, item, smem);
             else if (d.p == 6) call_spread<6>(d, item, smem);
             else call_spread<8>(d, item, smem);
             break;
@@ -84,6 +85,7 @@ __device__ __forceinline__ void run_stage(const SysDev &d, int stage, int item, 
         case STAGE_INV: call_inv(d, item, smem); break;
         default:
             if (d.p == 4) call_gather<4>(d, item, smem);
+            else if (d.p == 5) call_gather<5>(d, item, smem);
             else if (d.p == 6) call_gather<6>(d, item, smem);
             else call_gather<8>(d, item, smem);
             break;
@@ -229,13 +231,13 @@ pme_status WaveState::init(int dev_, int cap_sys_, size_t cap_entries_) {
     const size_t o_ctrl = off; off = al(off + sizeof(BatchCtrl));
     const size_t o_ev = off;   off = al(off + sizeof(double) * 8 * cap_sys);
     const size_t o_st = off;   off = al(off + sizeof(unsigned) * cap_sys);
-    cudaError_t e = cudaMalloc(&dmem, off);
+    cudaError_t e = lib_malloc(&dmem, off);
     if (e != cudaSuccess) {
         dmem = nullptr;
         return fail(PME_ENOMEM, "cudaMalloc(%zu bytes) for a batch: %s", off, cudaGetErrorString(e));
     }
     if ((e = cudaMemset(dmem, 0, off)) != cudaSuccess) return cuda_fail(e, "cudaMemset(batch state)");
-    if ((e = cudaMallocHost(&hmem, off)) != cudaSuccess) {
+    if ((e = lib_malloc_host(&hmem, off)) != cudaSuccess) {
         hmem = nullptr;
         return cuda_fail(e, "cudaMallocHost(batch staging)");
     }
@@ -343,6 +345,7 @@ struct pme_batch {
     int64_t stall_ns = 0;
     int strategy = PME_BATCH_AUTO;  // pme_batch_set_strategy
     int g_persistent = -1;          // whether the recorded graph is the persistent launch
+    std::vector<unsigned long long> plan_gen;  // each plan's generation when its descriptor was taken
 };
 
 // The persistent work-list kernel runs when asked for, while the stall hook is on (its bounded waits are
@@ -422,11 +425,11 @@ static pme_status batch_init_groups(pme_batch *b) {
     const int nsys = (int)b->sys.size(), G = (int)b->groups.size();
     cudaError_t e;
     if ((e = configure_group_kernels()) != cudaSuccess) return cuda_fail(e, "configure grouped kernels");
-    if ((e = cudaMalloc(&b->d_gsys, sizeof(SysDev) * nsys)) != cudaSuccess) {
+    if ((e = lib_malloc((void **)&b->d_gsys, sizeof(SysDev) * nsys)) != cudaSuccess) {
         b->d_gsys = nullptr;
         return fail(PME_ENOMEM, "cudaMalloc(batch descriptors): %s", cudaGetErrorString(e));
     }
-    if ((e = cudaMallocHost(&b->h_gsys, sizeof(SysDev) * nsys)) != cudaSuccess) {
+    if ((e = lib_malloc_host((void **)&b->h_gsys, sizeof(SysDev) * nsys)) != cudaSuccess) {
         b->h_gsys = nullptr;
         return cuda_fail(e, "cudaMallocHost(batch descriptors)");
     }
@@ -439,6 +442,37 @@ static pme_status batch_init_groups(pme_batch *b) {
         cudaEvent_t ev;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
         b->gevents.push_back(ev);
+    }
+    return PME_OK;
+}
+
+// Re-read the plans' descriptors when any plan changed since the batch took them (a new cell from
+// pme_set_box, a new tiling from the autotuner or pme_plan_set_tiling): work list, groups and graph follow.
+static pme_status batch_refresh(pme_batch *b) {
+    bool stale = false;
+    for (size_t s = 0; s < b->plans.size(); ++s) stale = stale || b->plans[s]->gen != b->plan_gen[s];
+    if (!stale) return PME_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    pme_status st;
+    for (size_t s = 0; s < b->plans.size(); ++s) {
+        pme_plan *pl = b->plans[s];
+        if ((st = plan_reserve(pl, b->n[s])) != PME_OK) return st;
+        b->sys[s] = plan_descriptor(pl, nullptr, nullptr, b->n[s], nullptr, nullptr);
+        b->plan_gen[s] = pl->gen;
+    }
+    build_work_list(b->sys, b->entries, b->count);
+    if (b->entries.size() > b->wave.cap_entries) {
+        b->wave.release();
+        if ((st = b->wave.init(b->dev, (int)b->sys.size(), b->entries.size())) != PME_OK) return st;
+    }
+    b->smem = batch_smem(b->sys);
+    b->grid = batch_grid(b->dev, b->sys[0].p, b->smem);
+    batch_release_groups(b);
+    if ((st = batch_init_groups(b)) != PME_OK) return st;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
     }
     return PME_OK;
 }
@@ -474,7 +508,7 @@ pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, 
     if (!out) return fail(PME_EINVAL, "out is NULL");
     *out = nullptr;
     if (nsys < 1 || nsys > 4096 || !plans || !n) return fail(PME_EINVAL, "need 1..4096 systems, plans and n");
-    pme_batch *b = new (std::nothrow) pme_batch();
+    pme_batch *b = lib_new<pme_batch>();
     if (!b) return fail(PME_ENOMEM, "host allocation failed");
     b->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&b->dev);
@@ -509,6 +543,7 @@ pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, 
         b->n.push_back(n[s]);
         b->off.push_back(off);
         b->sys.push_back(plan_descriptor(pl, nullptr, nullptr, n[s], nullptr, nullptr));
+        b->plan_gen.push_back(pl->gen);
         off += n[s];
     }
     build_work_list(b->sys, b->entries, b->count);
@@ -542,6 +577,8 @@ pme_status pme_batch_enqueue(pme_batch *b, const float *pos, const float *q, flo
     int64_t ntot = b->off.back() + b->n.back();
     if (ntot > 0 && (!pos || !q || !forces)) return fail(PME_EINVAL, "pos, q and forces must be non-NULL");
     DeviceGuard g(b->dev);
+    pme_status rst = batch_refresh(b);
+    if (rst != PME_OK) return rst;
     cudaError_t e;
     const bool persistent = batch_use_persistent(b);
     if (!b->exec || b->g_pos != pos || b->g_q != q || b->g_forces != forces || b->g_ev != ev_dev ||
@@ -619,6 +656,72 @@ pme_status pme_batch_set_strategy(pme_batch *b, int strategy) {
 int pme_batch_get_strategy(const pme_batch *b) {
     if (!b) return -1;
     return batch_use_persistent(b) ? PME_BATCH_PERSISTENT : PME_BATCH_GROUPED;
+}
+
+pme_status pme_batch_autotune(pme_batch *b, const float *pos, const float *q, float *forces, double *ev_dev, int reps,
+                              int *strategy, double *us_per_batch) {
+    if (!b) return fail(PME_EINVAL, "batch is NULL");
+    if (reps < 1 || reps > 100000) return fail(PME_EINVAL, "reps must be in [1, 100000]");
+    const int64_t ntot = b->off.back() + b->n.back();
+    if (!ev_dev || (ntot > 0 && (!pos || !q || !forces))) return fail(PME_EINVAL, "pos, q, forces and ev_dev must be non-NULL");
+    DeviceGuard g(b->dev);
+    const int nsys = (int)b->sys.size();
+    struct Cand {
+        int strategy, nt;
+        double us;
+        bool same;
+    };
+    std::vector<Cand> cands = {{PME_BATCH_GROUPED, 0, 0.0, true}, {PME_BATCH_GROUPED, 128, 0.0, false},
+                               {PME_BATCH_GROUPED, 256, 0.0, false}, {PME_BATCH_PERSISTENT, 0, 0.0, false}};
+    std::vector<float> F0((size_t)(ntot > 0 ? ntot : 1) * 3), F1(F0.size());
+    std::vector<double> ev0((size_t)nsys * 7), ev1(ev0.size());
+    cudaEvent_t ea, eb;
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    pme_status st = PME_OK;
+    auto apply = [&](const Cand &c) -> pme_status {
+        for (int s = 0; s < nsys; ++s) {
+            pme_status r = plan_retile(b->plans[s], 3, c.nt, b->n[s]);
+            if (r != PME_OK) return r;
+        }
+        b->strategy = c.strategy;
+        return PME_OK;
+    };
+    for (size_t c = 0; c < cands.size() && st == PME_OK; ++c) {
+        if ((st = apply(cands[c])) != PME_OK) break;
+        if ((st = pme_batch_enqueue(b, pos, q, forces, ev_dev)) != PME_OK || (st = pme_batch_sync(b)) != PME_OK) break;
+        std::vector<float> &F = c == 0 ? F0 : F1;
+        std::vector<double> &ev = c == 0 ? ev0 : ev1;
+        cudaError_t e = cudaMemcpy(F.data(), forces, (size_t)ntot * 12, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(ev.data(), ev_dev, ev.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaMemcpy(tuning results)");
+            break;
+        }
+        if (c > 0)
+            cands[c].same = memcmp(F0.data(), F1.data(), (size_t)ntot * 12) == 0 &&
+                            memcmp(ev0.data(), ev1.data(), ev0.size() * sizeof(double)) == 0;
+        if (!cands[c].same) continue;
+        for (int i = 0; i < 2 && st == PME_OK; ++i) st = pme_batch_enqueue(b, pos, q, forces, ev_dev);
+        if (st != PME_OK) break;
+        cudaEventRecord(ea, b->stream);
+        for (int i = 0; i < reps && st == PME_OK; ++i) st = pme_batch_enqueue(b, pos, q, forces, ev_dev);
+        cudaEventRecord(eb, b->stream);
+        if (st != PME_OK || (st = pme_batch_sync(b)) != PME_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ea, eb);
+        cands[c].us = 1000.0 * ms / reps;
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (st != PME_OK) return st;
+    size_t best = 0;
+    for (size_t c = 1; c < cands.size(); ++c)
+        if (cands[c].same && cands[c].us < cands[best].us) best = c;
+    if ((st = apply(cands[best])) != PME_OK) return st;
+    if (strategy) *strategy = cands[best].strategy;
+    if (us_per_batch) *us_per_batch = cands[best].us;
+    return PME_OK;
 }
 
 pme_status pme_batch_debug_stall(pme_batch *b, int enable, int64_t wait_limit_ns) {

@@ -145,6 +145,7 @@ struct SysDev {
     int lp_rows, lp_cols, lp_k1; // lane plans (PME_LANE_CASES) of the K3/2, K2 and K1 transforms, -1: none
     int lane_slab, lane_conv;    // slab stages / influence stage take the register path (1) or not (0)
     int pdl_late;                // when a stage kernel triggers its successor's launch (PdlScope, pdl.cuh)
+    int nt_tile;                 // spread / force CTA threads (128 or 256) chosen by the tuner; 0: density rule
     float kinv[3];               // 1 / K_alpha
     // u_alpha = sum_j r_j C[j][alpha], C[j][alpha] = K_alpha a*_alpha[j], as an unevaluated float sum
     // chi + clo (about 48 significant bits), index 3*j + alpha.

@@ -80,10 +80,10 @@ static cudaError_t set_limit(const void *fn) {
 }
 
 cudaError_t configure_group_kernels() {
-    const void *fns[] = {(const void *)k_bin_g,          (const void *)k_spread_g<4>,        (const void *)k_spread_g<6>,
-                         (const void *)k_spread_g<8>,    (const void *)k_fwd_g<-1, -1>,      (const void *)k_conv_g<-1>,
-                         (const void *)k_inv_g<-1, -1>,  (const void *)k_gather_g<4>,        (const void *)k_gather_g<6>,
-                         (const void *)k_gather_g<8>};
+    const void *fns[] = {(const void *)k_bin_g,          (const void *)k_spread_g<4>,        (const void *)k_spread_g<5>,
+                         (const void *)k_spread_g<6>,    (const void *)k_spread_g<8>,        (const void *)k_fwd_g<-1, -1>,
+                         (const void *)k_conv_g<-1>,     (const void *)k_inv_g<-1, -1>,      (const void *)k_gather_g<4>,
+                         (const void *)k_gather_g<5>,    (const void *)k_gather_g<6>,        (const void *)k_gather_g<8>};
     for (const void *f : fns) {
         cudaError_t e = set_limit(f);
         if (e != cudaSuccess) return e;
@@ -166,14 +166,14 @@ cudaError_t launch_group_chain(const SysDev *sys_dev, int nsys, const SysDev &pr
         switch (stage) {
             case STAGE_BIN: e = launch_ex(k_bin_g, grid, NT_BIN, smem_bin(NT_BIN), s, a); break;
             case STAGE_SPREAD:
-                e = launch_ex(d.p == 4 ? k_spread_g<4> : (d.p == 6 ? k_spread_g<6> : k_spread_g<8>), grid,
+                e = launch_ex(d.p == 4 ? k_spread_g<4> : (d.p == 5 ? k_spread_g<5> : (d.p == 6 ? k_spread_g<6> : k_spread_g<8>)), grid,
                               (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK), smem_spread(d.p, 3), s, a);
                 break;
             case STAGE_FWD: e = launch_ex(fwd_g(d), grid, NT_SLAB, smem_slab(d.K2, d.K3), s, a); break;
             case STAGE_CONV: e = launch_ex(conv_g(d), grid, NT_CONV, smem_conv(d.K1, NT_CONV), s, a); break;
             case STAGE_INV: e = launch_ex(inv_g(d), grid, NT_SLAB, smem_inv(d.K2, d.K3), s, a); break;
             default:
-                e = launch_ex(d.p == 4 ? k_gather_g<4> : (d.p == 6 ? k_gather_g<6> : k_gather_g<8>), grid,
+                e = launch_ex(d.p == 4 ? k_gather_g<4> : (d.p == 5 ? k_gather_g<5> : (d.p == 6 ? k_gather_g<6> : k_gather_g<8>)), grid,
                               (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK), smem_gather_all(d.p, 3), s, a);
                 break;
         }

@@ -34,8 +34,8 @@ inline int validate_params(const int K[3], int p, double beta, const double box[
         snprintf(msg, len, "p = %d must be in [2, min(K)]", p);
         return 1;
     }
-    if (p != 4 && p != 6 && p != 8) {
-        snprintf(msg, len, "p = %d: only B-spline orders 4, 6, 8 are implemented", p);
+    if (p != 4 && p != 5 && p != 6 && p != 8) {
+        snprintf(msg, len, "p = %d: only B-spline orders 4, 5, 6, 8 are implemented", p);
         return 2;
     }
     if (!(beta > 0.0) || !isfinite(beta)) {
@@ -155,9 +155,11 @@ inline std::vector<double> bspline_knots(int p) {
 }
 
 // |b(m)|^2 = 1 / |sum_{k=0}^{p-2} M_p(k+1) exp(2 pi i m k / K)|^2 (the Euler exponential-spline factor).
+// For odd p the denominator vanishes at m = K/2 (symmetric knot values, alternating sum); there it is taken
+// as the mean of the denominators at K/2 - 1 and K/2 + 1.
 inline std::vector<double> bspline_moduli(int K, int p) {
     const std::vector<double> M = bspline_knots(p);
-    std::vector<double> b(K);
+    std::vector<double> den(K), b(K);
     for (int m = 0; m < K; ++m) {
         double sr = 0.0, si = 0.0;
         for (int k = 0; k <= p - 2; ++k) {
@@ -165,8 +167,10 @@ inline std::vector<double> bspline_moduli(int K, int p) {
             sr += M[k + 1] * cos(a);
             si += M[k + 1] * sin(a);
         }
-        b[m] = 1.0 / (sr * sr + si * si);
+        den[m] = sr * sr + si * si;
     }
+    if ((p & 1) && (K & 1) == 0 && K >= 4) den[K / 2] = 0.5 * (den[K / 2 - 1] + den[K / 2 + 1]);
+    for (int m = 0; m < K; ++m) b[m] = 1.0 / den[m];
     return b;
 }
 

@@ -106,10 +106,12 @@ static cudaError_t set_smem_limit(const void *fn, size_t bytes) {
 cudaError_t configure_kernels() {
     const size_t big = MAX_SMEM_BYTES;
     const void *fns[] = {(const void *)k_fwd, (const void *)k_conv, (const void *)k_inv,
-                         (const void *)k_spread<4, 8>, (const void *)k_spread<6, 8>, (const void *)k_spread<8, 8>,
-                         (const void *)k_spread<4, 16>, (const void *)k_spread<6, 16>, (const void *)k_spread<8, 16>,
-                         (const void *)k_gather<4, 8>, (const void *)k_gather<6, 8>, (const void *)k_gather<8, 8>,
-                         (const void *)k_gather<4, 16>, (const void *)k_gather<6, 16>, (const void *)k_gather<8, 16>};
+                         (const void *)k_spread<4, 8>, (const void *)k_spread<5, 8>, (const void *)k_spread<6, 8>,
+                         (const void *)k_spread<8, 8>, (const void *)k_spread<4, 16>, (const void *)k_spread<5, 16>,
+                         (const void *)k_spread<6, 16>, (const void *)k_spread<8, 16>, (const void *)k_gather<4, 8>,
+                         (const void *)k_gather<5, 8>, (const void *)k_gather<6, 8>, (const void *)k_gather<8, 8>,
+                         (const void *)k_gather<4, 16>, (const void *)k_gather<5, 16>, (const void *)k_gather<6, 16>,
+                         (const void *)k_gather<8, 16>};
     for (const void *f : fns) {
         cudaError_t e = set_smem_limit(f, big);
         if (e != cudaSuccess) return e;
@@ -174,6 +176,7 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             break;
         case STAGE_SPREAD:
             if (d.p == 4) launch_tiles_spread<4>(d, s);
+            else if (d.p == 5) launch_tiles_spread<5>(d, s);
             else if (d.p == 6) launch_tiles_spread<6>(d, s);
             else launch_tiles_spread<8>(d, s);
             break;
@@ -188,6 +191,7 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             break;
         default:
             if (d.p == 4) launch_tiles_gather<4>(d, s);
+            else if (d.p == 5) launch_tiles_gather<5>(d, s);
             else if (d.p == 6) launch_tiles_gather<6>(d, s);
             else launch_tiles_gather<8>(d, s);
             break;

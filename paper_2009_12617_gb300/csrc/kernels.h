@@ -14,6 +14,7 @@ constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interp
 // atom, sized to the mean tile occupancy, so sparse tiles (large meshes) do not leave half the CTA idle and
 // twice as many CTAs fit on an SM. Results do not depend on it.
 inline int tile_threads(const SysDev &d, int64_t n) {
+    if (d.nt_tile == 128 || d.nt_tile == NT_TILE) return d.nt_tile;  // chosen by the autotuner
     return (d.ntiles > 0 && n <= (int64_t)64 * d.ntiles) ? 128 : NT_TILE;
 }
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage

@@ -251,6 +251,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     const int v = validate_params(K, p, beta, box, msg, sizeof(msg));
     if (v == 1) return fail(PME_EINVAL, "%s", msg);
     if (v == 2) return fail(PME_EUNSUPPORTED, "%s", msg);
+    if (p != 4 && p != 6 && p != 8) return fail(PME_EUNSUPPORTED, "pme_compute_noalloc: B-spline orders 4, 6 and 8 only");
     const int64_t mesh = (int64_t)K[0] * K[1] * K[2];
     if (mesh > NOALLOC_MAX_MESH_POINTS || K[0] > 64 || K[1] > 64 || K[2] > 64)
         return fail(PME_EINVAL, "pme_compute_noalloc: mesh %dx%dx%d exceeds its static limit (K1*K2*K3 <= %d, each K <= 64)",

@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -28,8 +29,33 @@ pme_status fail(pme_status s, const char *fmt, ...) {
     return s;
 }
 
+static std::atomic<long long> g_fail_countdown{0};  // > 0: the allocation that takes it to zero fails
+
+bool alloc_injected_failure() {
+    long long v = g_fail_countdown.load();
+    while (v > 0)
+        if (g_fail_countdown.compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
+}
+
+cudaError_t lib_malloc(void **p, size_t bytes) {
+    if (alloc_injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t lib_malloc_host(void **p, size_t bytes) {
+    if (alloc_injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 pme_status cuda_fail(cudaError_t e, const char *what) {
-    return fail(PME_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? PME_ENOMEM : PME_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 pme_status status_from_bits(unsigned bits) {
@@ -97,7 +123,7 @@ static pme_status alloc_mesh(pme_plan *pl) {
     const size_t o_cnt = off;  off = align256(off + bcount_bytes_max(pl->K));
     const size_t o_par = off;  off = align256(off + partials_bytes(d));
     const size_t o_ctl = off;  off = align256(off + sizeof(Ctl));
-    cudaError_t e = cudaMalloc(&pl->mesh_mem, off);
+    cudaError_t e = lib_malloc(&pl->mesh_mem, off);
     if (e != cudaSuccess) {
         pl->mesh_mem = nullptr;
         return fail(e == cudaErrorMemoryAllocation ? PME_ENOMEM : PME_ECUDA, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
@@ -126,9 +152,9 @@ pme_status plan_reserve(pme_plan *pl, int64_t n) {
     if (n <= pl->n_cap && pl->atom_mem) return PME_OK;
     SysDev &d = pl->d;
     const int64_t ncap = n > 0 ? n : 1;
-    // tile edge from the atom density (every tile counter is zero between evaluations, so the tiling may
-    // change here; results do not depend on it)
-    set_tiling(d, choose_tile_log(ncap, pl->K));
+    // tile edge from the atom density, or the one the autotuner / caller set (every tile counter is zero
+    // between evaluations, so the tiling may change here; results do not depend on it)
+    set_tiling(d, pl->tile_log_set ? pl->tile_log_set : choose_tile_log(ncap, pl->K));
     const int cap = bucket_capacity(ncap, d.ntiles);
     const size_t nb = (size_t)d.ntiles * cap;
     size_t off = 0;
@@ -142,7 +168,7 @@ pme_status plan_reserve(pme_plan *pl, int64_t n) {
     pl->atom_mem = nullptr;
     pl->atom_bytes = 0;
     pl->n_cap = 0;
-    e = cudaMalloc(&pl->atom_mem, off);
+    e = lib_malloc(&pl->atom_mem, off);
     if (e != cudaSuccess) {
         pl->atom_mem = nullptr;
         return fail(e == cudaErrorMemoryAllocation ? PME_ENOMEM : PME_ECUDA, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
@@ -259,6 +285,12 @@ const char *pme_strerror(pme_status s) {
     return "unknown status";
 }
 
+pme_status pme_debug_fail_alloc(int nth) {
+    if (nth < 0) return fail(PME_EINVAL, "nth must be >= 0");
+    g_fail_countdown.store(nth);
+    return PME_OK;
+}
+
 pme_status pme_last_error_detail(char *buf, size_t len) {
     if (buf && len) {
         strncpy(buf, g_msg, len - 1);
@@ -277,7 +309,7 @@ pme_status pme_create(const int K[3], int p, double beta, const double box[9], v
     if (v == 2) return fail(PME_EUNSUPPORTED, "%s", msg);
     double recip[9], vol;
     if (!cell_reciprocal(box, recip, &vol)) return fail(PME_EINVAL, "box is singular");
-    pme_plan *pl = new (std::nothrow) pme_plan();
+    pme_plan *pl = lib_new<pme_plan>();
     if (!pl) return fail(PME_ENOMEM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&pl->dev);
     if (e != cudaSuccess) {
@@ -302,7 +334,7 @@ pme_status pme_create(const int K[3], int p, double beta, const double box[9], v
         pme_destroy(pl);
         return st;
     }
-    if ((e = cudaMallocHost((void **)&pl->h_ctl, sizeof(Ctl))) != cudaSuccess) {
+    if ((e = lib_malloc_host((void **)&pl->h_ctl, sizeof(Ctl))) != cudaSuccess) {
         pl->h_ctl = nullptr;
         pme_destroy(pl);
         return cuda_fail(e, "cudaMallocHost");
@@ -411,7 +443,7 @@ pme_status pme_compute_host(pme_plan *pl, const float *pos, const float *q, int6
         pl->host_mem = nullptr;
         pl->host_cap = 0;
         const size_t bytes = align256((size_t)n * 12) * 2 + align256((size_t)n * 4);
-        if ((e = cudaMalloc(&pl->host_mem, bytes)) != cudaSuccess) {
+        if ((e = lib_malloc(&pl->host_mem, bytes)) != cudaSuccess) {
             pl->host_mem = nullptr;
             return fail(PME_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
         }
@@ -516,6 +548,8 @@ void pme_destroy(pme_plan *pl) {
     cudaStreamSynchronize(pl->stream);
     if (pl->g_dev.exec) cudaGraphExecDestroy(pl->g_dev.exec);
     if (pl->g_host.exec) cudaGraphExecDestroy(pl->g_host.exec);
+    if (pl->g_md.exec) cudaGraphExecDestroy(pl->g_md.exec);
+    if (pl->md_mem) cudaFree(pl->md_mem);
     if (pl->rec_stream) cudaStreamDestroy(pl->rec_stream);
     if (pl->mesh_mem) cudaFree(pl->mesh_mem);
     if (pl->atom_mem) cudaFree(pl->atom_mem);

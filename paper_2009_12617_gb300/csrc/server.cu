@@ -227,7 +227,7 @@ pme_status pme_server_create(size_t mem_budget_bytes, int max_slots, pme_server 
     if (!out) return fail(PME_EINVAL, "out is NULL");
     *out = nullptr;
     if (max_slots < 1 || mem_budget_bytes == 0) return fail(PME_EINVAL, "max_slots >= 1 and a nonzero budget required");
-    pme_server *sv = new (std::nothrow) pme_server();
+    pme_server *sv = lib_new<pme_server>();
     if (!sv) return fail(PME_ENOMEM, "host allocation failed");
     cudaGetDevice(&sv->dev);
     sv->budget = mem_budget_bytes;
@@ -272,7 +272,7 @@ pme_status pme_submit(pme_server *sv, pme_plan *plan, const float *pos, const fl
         DeviceGuard g(plan->dev);
         if ((st = plan_reserve(plan, n)) != PME_OK) return st;
     }
-    Request *r = new (std::nothrow) Request();
+    Request *r = lib_new<Request>();
     if (!r) return fail(PME_ENOMEM, "host allocation failed");
     r->id = sv->next_id++;
     r->plan = plan;

@@ -31,13 +31,17 @@ struct Region {
     static constexpr int VOL = R * R * R;
 };
 
+// The two threads of an atom split its support planes j1: half 0 takes [0, H0), half 1 [H0, P), with
+// H0 = ceil(P / 2) (equal halves for even orders, one plane more in half 0 for odd ones).
+PME_HD int half_planes(int P) { return (P + 1) / 2; }
+
 // Spreading region layout: planes of R x R points padded to PL so that the two half-support lanes of an
-// atom ((P/2) planes apart) sit 16 banks apart: (P/2) PL = 16 (mod 32). Then the 32 lanes of a warp (16
-// atoms x 2 halves) hit distinct banks whenever the atoms' base addresses differ mod 16, which the dealt
-// processing order (stage_spread) arranges.
+// atom (H0 planes apart) sit 16 banks apart: H0 PL = 16 (mod 32). Then the 32 lanes of a warp (16 atoms x 2
+// halves) hit distinct banks whenever the atoms' base addresses differ mod 16, which the dealt processing
+// order (stage_spread) arranges.
 constexpr int spread_plane(int R, int P) {
     int pl = R * R;
-    while (((P / 2) * pl) % 32 != 16) ++pl;
+    while ((half_planes(P) * pl) % 32 != 16) ++pl;
     return pl;
 }
 template <int P, int T>
@@ -335,7 +339,8 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
         }
     }
     PME_SYNC();
-    // two threads per atom: half h takes the planes j1 in [h P/2, (h + 1) P/2)
+    // two threads per atom: half 0 takes the planes j1 in [0, H0), half 1 [H0, P)
+    constexpr int H0 = half_planes(P);
     for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
         const int a = inv_s[a2 >> 1], half = a2 & 1;
         const float4 ra = ra_s[a];
@@ -349,9 +354,10 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
         const int l2 = ((rb.x >> 10) & 1023) - o2 + H;
         const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
 #pragma unroll
-        for (int jj = 0; jj < P / 2; ++jj) {
-            const int j1 = half * (P / 2) + jj;
-            const float t1 = half ? th1[P / 2 + jj] : th1[jj];
+        for (int jj = 0; jj < H0; ++jj) {
+            if (half && jj >= P - H0) break;  // odd P: half 1 has one plane fewer
+            const int j1 = half * H0 + jj;
+            const float t1 = half ? th1[H0 + jj < P ? H0 + jj : P - 1] : th1[jj];
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
                 const float c = ra.w * t1 * th2[j2];
@@ -1105,13 +1111,14 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
     bspline_wd<P>(ra.y, th2, dth2);
     bspline_wd<P>(ra.z, th3, dth3);
     const int b1 = rb.x & 1023, b2 = (rb.x >> 10) & 1023, b3 = (rb.x >> 20) & 1023;
+    constexpr int H0 = half_planes(P);
     float gh[2][3];
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         float g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-        for (int jj = 0; jj < P / 2; ++jj) {
-            const int j1 = half * (P / 2) + jj;
+        for (int jj = 0; jj < (half ? P - H0 : H0); ++jj) {
+            const int j1 = half * H0 + jj;
             const int k1 = wrapk(b1 - j1, d.K1);
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
@@ -1198,8 +1205,9 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
 #if defined(PME_HOST_EMULATION)
         float e1 = 0.f, e2 = 0.f, e3 = 0.f;  // the even half's partial sums, combined on the odd half
 #endif
-        // two threads per atom (adjacent lanes): half h sums the planes j1 in [h P/2, (h + 1) P/2); the
+        // two threads per atom (adjacent lanes): half 0 sums the planes j1 in [0, H0), half 1 [H0, P); the
         // halves are added in a fixed order, so both lanes hold the same total
+        constexpr int H0 = half_planes(P);
         for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
             const int a = a2 >> 1, half = a2 & 1;
             const bool first = a2 == tid;
@@ -1214,10 +1222,12 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
             const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
             float g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
-            for (int jj = 0; jj < P / 2; ++jj) {
-                const int j1 = half * (P / 2) + jj;
-                const float t1 = half ? th1[P / 2 + jj] : th1[jj];
-                const float dt1 = half ? dth1[P / 2 + jj] : dth1[jj];
+            for (int jj = 0; jj < H0; ++jj) {
+                if (half && jj >= P - H0) break;  // odd P: half 1 has one plane fewer
+                const int j1 = half * H0 + jj;
+                const int jh = H0 + jj < P ? H0 + jj : P - 1;
+                const float t1 = half ? th1[jh] : th1[jj];
+                const float dt1 = half ? dth1[jh] : dth1[jj];
 #pragma unroll
                 for (int j2 = 0; j2 < P; ++j2) {
                     const float *row = reg + ((l1 - j1) * R + (l2 - j2)) * R + l3;

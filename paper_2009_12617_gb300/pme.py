@@ -39,7 +39,22 @@ EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme
            "pme_batch_destroy", "pme_server_create", "pme_submit", "pme_poll", "pme_server_stats",
            "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall",
            "pme_compute_noalloc", "pme_batch_set_strategy", "pme_batch_get_strategy",
-           "pme_probe_launch")
+           "pme_probe_launch", "pme_real_create", "pme_real_set_box", "pme_real_reserve", "pme_real_enqueue",
+           "pme_real_compute", "pme_real_destroy", "pme_autotune", "pme_tune_cache", "pme_plan_set_tiling",
+           "pme_plan_get_tiling", "pme_batch_autotune", "pme_run_steps", "pme_debug_fail_alloc")
+
+
+PME_TUNE_FORCE = 1
+
+
+class TuneResult(ctypes.Structure):
+    """pme_tune_result of include/pme.h."""
+    _fields_ = [("tile_edge", ctypes.c_int), ("tile_threads", ctypes.c_int), ("us_per_eval", ctypes.c_double),
+                ("default_us", ctypes.c_double), ("candidates", ctypes.c_int), ("rejected", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PMEError(RuntimeError):
@@ -124,6 +139,19 @@ def load_library(path: str | None = None):
         "pme_batch_debug_stall": (_st, [_vp, ctypes.c_int, _i64]),
         "pme_batch_set_strategy": (_st, [_vp, ctypes.c_int]),
         "pme_batch_get_strategy": (ctypes.c_int, [_vp]),
+        "pme_autotune": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult)]),
+        "pme_tune_cache": (_st, [ctypes.c_char_p]),
+        "pme_plan_set_tiling": (_st, [_vp, ctypes.c_int, ctypes.c_int]),
+        "pme_plan_get_tiling": (_st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "pme_batch_autotune": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+        "pme_debug_fail_alloc": (_st, [ctypes.c_int]),
+        "pme_run_steps": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_double, ctypes.c_int, _vp]),
+        "pme_real_create": (_st, [ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
+        "pme_real_set_box": (_st, [_vp, ctypes.POINTER(ctypes.c_double)]),
+        "pme_real_reserve": (_st, [_vp, _i64]),
+        "pme_real_enqueue": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, _vp]),
+        "pme_real_compute": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "pme_real_destroy": (None, [_vp]),
         "pme_probe_launch": (_st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_double)]),
         "pme_server_create": (_st, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
         "pme_submit": (_st, [_vp, _vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
@@ -387,6 +415,93 @@ def pme_probe_launch(kind: int, ctas: int, rounds: int, buf, stream=None) -> flo
     check(load_library().pme_probe_launch(int(kind), int(ctas), int(rounds), _vp(_ptr(buf)),
                                           buf.numel() * buf.element_size(), _vp(_stream_handle(stream)), ctypes.byref(ops)))
     return ops.value
+
+
+def pme_autotune(plan: int, pos, q, forces, reps: int = 20, force: bool = False) -> dict:
+    """Tune the plan's tile edge and CTA size on these atoms (see include/pme.h); returns pme_tune_result."""
+    res = TuneResult()
+    check(load_library().pme_autotune(_vp(plan), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), int(q.shape[0]),
+                                      _vp(_f32(forces, (3,), "forces")), int(reps), PME_TUNE_FORCE if force else 0,
+                                      ctypes.byref(res)))
+    return res.as_dict()
+
+
+def pme_tune_cache(path) -> None:
+    check(load_library().pme_tune_cache(None if path is None else os.fsencode(path)))
+
+
+def pme_plan_set_tiling(plan: int, tile_edge: int = 0, tile_threads: int = 0) -> None:
+    check(load_library().pme_plan_set_tiling(_vp(plan), int(tile_edge), int(tile_threads)))
+
+
+def pme_plan_get_tiling(plan: int) -> tuple[int, int]:
+    e, t = ctypes.c_int(), ctypes.c_int()
+    check(load_library().pme_plan_get_tiling(_vp(plan), ctypes.byref(e), ctypes.byref(t)))
+    return e.value, t.value
+
+
+def pme_batch_autotune(batch: int, pos, q, forces, ev_dev, reps: int = 10) -> tuple[int, float]:
+    """Tune a batch's strategy and tile CTA size; returns (strategy, us per batch)."""
+    st, us = ctypes.c_int(), ctypes.c_double()
+    check(load_library().pme_batch_autotune(_vp(batch), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")),
+                                            _vp(_f32(forces, (3,), "forces")), _vp(_ptr(ev_dev)), int(reps),
+                                            ctypes.byref(st), ctypes.byref(us)))
+    return st.value, us.value
+
+
+def pme_run_steps(plan: int, pos, vel, q, forces, dt: float, steps: int, rs: int = 0, inv_mass=None,
+                  ev_steps=None) -> None:
+    """Enqueue `steps` leapfrog time steps on the device (see include/pme.h); pme_sync(plan) waits."""
+    n = int(q.shape[0])
+    if inv_mass is not None:
+        _f32(inv_mass, (), "inv_mass")
+    check(load_library().pme_run_steps(_vp(plan), _vp(rs or 0), _vp(_f32(pos, (3,), "pos")), _vp(_f32(vel, (3,), "vel")),
+                                       _vp(_f32(q, (), "q")), _vp(_ptr(inv_mass)), n, _vp(_f32(forces, (3,), "forces")),
+                                       float(dt), int(steps), _vp(_ptr(ev_steps))))
+
+
+def pme_real_create(box, beta: float, rcut: float, stream=None) -> int:
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    out = _vp()
+    check(load_library().pme_real_create(bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(beta), float(rcut),
+                                         _vp(_stream_handle(stream)), ctypes.byref(out)))
+    return out.value
+
+
+def pme_real_set_box(rs: int, box) -> None:
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    check(load_library().pme_real_set_box(_vp(rs), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def pme_real_reserve(rs: int, n: int) -> None:
+    check(load_library().pme_real_reserve(_vp(rs), int(n)))
+
+
+def pme_real_enqueue(rs: int, pos, q, forces, accumulate: bool = False, ev_dev=None) -> None:
+    """Asynchronous real-space evaluation; ev_dev (8 doubles, device) receives E_real, E_self, virial[6]."""
+    n = int(q.shape[0])
+    check(load_library().pme_real_enqueue(_vp(rs), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), n,
+                                          _vp(_f32(forces, (3,), "forces")), int(bool(accumulate)), _vp(_ptr(ev_dev))))
+
+
+def pme_real_compute(rs: int, pos, q, forces) -> tuple[float, float, np.ndarray]:
+    """Synchronous real-space evaluation on CUDA tensors; returns (E_real, E_self, virial[6])."""
+    n = int(q.shape[0])
+    er, es = ctypes.c_double(), ctypes.c_double()
+    vir = (ctypes.c_double * 6)()
+    check(load_library().pme_real_compute(_vp(rs), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")), n,
+                                          _vp(_f32(forces, (3,), "forces")), ctypes.byref(er), ctypes.byref(es), vir))
+    return er.value, es.value, np.array(vir[:])
+
+
+def pme_real_destroy(rs: int) -> None:
+    if rs:
+        load_library().pme_real_destroy(_vp(rs))
+
+
+def pme_debug_fail_alloc(nth: int) -> None:
+    """Make the nth library allocation from now on fail (0 disarms); for tests."""
+    check(load_library().pme_debug_fail_alloc(int(nth)))
 
 
 def pme_strerror(status: int) -> str:

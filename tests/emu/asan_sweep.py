@@ -45,7 +45,7 @@ def main(lib_path):
     meshes = [(8, 8, 8), (10, 12, 18), (16, 18, 20), (24, 30, 36), (40, 48, 50), (54, 60, 64), (72, 80, 90),
               (96, 100, 108), (120, 128, 8), (128, 128, 128)]
     for K in meshes:
-        for p in (4, 6, 8):
+        for p in (4, 5, 6, 8):
             if p > min(K):
                 continue
             n = int(rng.integers(0, 400))

@@ -125,6 +125,8 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
             const int key = p * 10 + d.tlog;
             switch (key) {
                 case 43: spread_item<4, 8>(d, it, sp); break;
+                case 53: spread_item<5, 8>(d, it, sp); break;
+                case 54: spread_item<5, 16>(d, it, sp); break;
                 case 63: spread_item<6, 8>(d, it, sp); break;
                 case 83: spread_item<8, 8>(d, it, sp); break;
                 case 44: spread_item<4, 16>(d, it, sp); break;
@@ -140,6 +142,8 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
             const int key = p * 10 + d.tlog;
             switch (key) {
                 case 43: gather_item<4, 8>(d, it, sp); break;
+                case 53: gather_item<5, 8>(d, it, sp); break;
+                case 54: gather_item<5, 16>(d, it, sp); break;
                 case 63: gather_item<6, 8>(d, it, sp); break;
                 case 83: gather_item<8, 8>(d, it, sp); break;
                 case 44: gather_item<4, 16>(d, it, sp); break;

@@ -47,7 +47,7 @@ def test_strerror(lib):
     ((15, 16, 16), 4, 0.3, pme.PME_EINVAL),    # odd edge
     ((6, 16, 16), 4, 0.3, pme.PME_EINVAL),     # below 8
     ((256, 16, 16), 4, 0.3, pme.PME_EINVAL),   # above 128
-    ((16, 16, 16), 5, 0.3, pme.PME_EUNSUPPORTED),  # odd order
+    ((16, 16, 16), 7, 0.3, pme.PME_EUNSUPPORTED),  # an order this build does not implement
     ((16, 16, 16), 2, 0.3, pme.PME_EUNSUPPORTED),
     ((16, 16, 16), 10, 0.3, pme.PME_EUNSUPPORTED),
     ((16, 16, 16), 4, 0.0, pme.PME_EINVAL),
@@ -137,3 +137,22 @@ def test_product_never_reaches_the_oracle(tmp_path):
             "try:\n    pme.load_library(%r)\nexcept RuntimeError as e:\n    print('raised', e)\n" % str(tmp_path / "missing.so"))
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, check=True).stdout
     assert out.startswith("raised")
+
+
+def test_injected_host_allocation_failure(lib):
+    """The first allocation of each constructor is its host object, made before any CUDA call: with the
+    first allocation made to fail, every constructor returns PME_ENOMEM (no GPU needed), and disarming
+    restores normal argument checking."""
+    box = np.eye(3) * 20.0
+    try:
+        for make in (lambda: pme.pme_create((16, 16, 16), 4, 0.3, box), lambda: pme.pme_real_create(box, 0.3, 9.0),
+                     lambda: pme.pme_server_create(1 << 20, 4)):
+            pme.pme_debug_fail_alloc(1)
+            with pytest.raises(pme.PMEError) as ei:
+                make()
+            assert ei.value.status == pme.PME_ENOMEM and "allocation" in ei.value.detail
+    finally:
+        pme.pme_debug_fail_alloc(0)
+    with pytest.raises(pme.PMEError) as ei:
+        pme.pme_debug_fail_alloc(-1)
+    assert ei.value.status == pme.PME_EINVAL

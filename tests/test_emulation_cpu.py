@@ -21,6 +21,8 @@ CASES = [
     ((32, 40, 48), 8),
     ((10, 12, 18), 4),   # small ragged meshes (tiles of 8 with tails of 2, 4, 2)
     ((8, 8, 8), 8),      # the p - 1 halo wraps onto the same tile
+    ((24, 30, 40), 5),   # odd order: unequal support halves, the m = K/2 modulus reading
+    ((10, 12, 16), 5),
 ]
 
 
@@ -99,3 +101,19 @@ def test_emulated_invalid_inputs(emu):
     q[:] = 3000.0  # sum |q| = 6.1e6 e > 2^22
     st, _, _, _, _ = emu_spme(emu, s.pos, q, (32, 32, 32), 4, 0.34, s.box)
     assert st & 2
+
+
+def test_emulated_odd_order_paths_bit_identical(oracle_mod, emu):
+    """p = 5 (support halves of 3 and 2 planes): the overflow path equals the tile path bit for bit, and 8^3
+    and 16^3 tiles agree bit for bit; all match the oracle."""
+    s = wl.parity_system()
+    K = (30, 32, 36)
+    _, Ft, evt, mt, _ = emu_spme(emu, s.pos, s.q, K, 5, 0.34, s.box, tile_log=3)
+    _, Fo, evo, mo, _ = emu_spme(emu, s.pos, s.q, K, 5, 0.34, s.box, cap=32, tile_log=3)
+    _, F16, ev16, m16, _ = emu_spme(emu, s.pos, s.q, K, 5, 0.34, s.box, tile_log=4)
+    for F, ev, m in ((Fo, evo, mo), (F16, ev16, m16)):
+        assert np.array_equal(m, mt) and np.array_equal(F, Ft) and np.array_equal(ev, evt)
+    r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), K, 5, 0.34, s.box)
+    assert rel_energy(evt[0], r["energy"]) < E_REL_TOL
+    assert rms_force(Ft, r["forces"]) < F_RMS_TOL
+    assert rel_virial(evt[1:], r["virial"]) < V_TOL

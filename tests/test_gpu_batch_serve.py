@@ -294,3 +294,45 @@ def test_server_mixed_orders_and_shapes(pme):
         pme.pme_server_destroy(srv)
         for o in syst:
             pme.pme_destroy(o["plan"])
+
+
+def test_batch_and_server_odd_order(pme, oracle_mod):
+    """p = 5 systems through grouped and persistent batches and the server: bit-identical to their single
+    evaluations, which match the oracle."""
+    specs = [(3000, (32, 32, 32), 5), (2500, (32, 32, 32), 5), (4000, (30, 36, 40), 5)]
+    syst = _shaped_systems(pme, specs, 500)
+    try:
+        s = syst[2]["sys"]
+        r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), s.K, s.p, s.beta, s.box)
+        assert rel_energy(syst[2]["E"], r["energy"]) < E_REL_TOL
+        assert rms_force(syst[2]["F"], r["forces"]) < F_RMS_TOL
+        pos, q, ns = packed(syst)
+        F = torch.full_like(pos, float("nan"))
+        ev = torch.zeros((len(syst), 7), dtype=torch.float64, device="cuda:0")
+        b = pme.pme_batch_create([o["plan"] for o in syst], ns)
+        try:
+            for strategy in (pme.PME_BATCH_GROUPED, pme.PME_BATCH_PERSISTENT):
+                pme.pme_batch_set_strategy(b, strategy)
+                pme.pme_batch_enqueue(b, pos, q, F, ev)
+                pme.pme_batch_sync(b)
+                Fh, evh = F.cpu().numpy(), ev.cpu().numpy()
+                off = 0
+                for i, o in enumerate(syst):
+                    check_same(o, Fh[off:off + ns[i]], evh[i, 0], evh[i, 1:], exact=True)
+                    off += ns[i]
+        finally:
+            pme.pme_batch_destroy(b)
+        srv = pme.pme_server_create(1 << 34, 16)
+        try:
+            tickets = []
+            for o in syst:
+                Fo = torch.full_like(o["pos"], float("nan"))
+                tickets.append((o, Fo, pme.pme_submit(srv, o["plan"], o["pos"], o["q"], Fo)))
+            for o, Fo, t in tickets:
+                assert pme.pme_poll(srv, t, block=True) == pme.PME_OK
+                check_same(o, Fo.cpu().numpy(), t.energy.value, np.array(t.virial[:]), exact=True)
+        finally:
+            pme.pme_server_destroy(srv)
+    finally:
+        for o in syst:
+            pme.pme_destroy(o["plan"])

@@ -66,13 +66,14 @@ def test_parity_config1(pmelib, oracle_mod):
 
 SHAPES = [((8, 10, 12), 4), ((16, 18, 20), 6), ((24, 30, 32), 8), ((36, 40, 48), 4), ((50, 54, 60), 6),
           ((64, 72, 80), 4), ((90, 96, 100), 4), ((108, 120, 128), 6), ((40, 40, 40), 8), ((8, 8, 8), 8),
-          ((96, 80, 128), 6), ((128, 128, 128), 4)]
+          ((96, 80, 128), 6), ((128, 128, 128), 4), ((30, 32, 36), 5), ((64, 64, 64), 5), ((50, 48, 54), 5)]
 
 
 @pytest.mark.parametrize("K,p", SHAPES, ids=[f"{K[0]}x{K[1]}x{K[2]}_p{p}" for K, p in SHAPES])
 def test_parity_mesh_shapes(pmelib, oracle_mod, K, p):
-    """Every radix-2/3/5 length from 8 to 128 in some dimension, ragged tiles, orders 4, 6 and 8; register
-    (lane-plan) and shared-memory transform paths, specialised and general kernels."""
+    """Every radix-2/3/5 length from 8 to 128 in some dimension, ragged tiles, orders 4, 5, 6 and 8 (odd p: the
+    m = K/2 modulus reading); register (lane-plan) and shared-memory transform paths, specialised and general
+    kernels."""
     L = np.array(K, dtype=float) * 1.1
     box = np.diag(L)
     n = 3000
