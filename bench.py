@@ -971,11 +971,13 @@ def leg_serving(args, sampler, dist, n_req: int = 4000):
 
 
 def leg_large(args, sampler, dist=None):
-    """Precision study at the largest mesh: 262144 water-like atoms, 137.9 A, 128^3, p = 6. Time per
-    evaluation (CUDA graph replays) and the energy / RMS-force / virial error of the FP32 path against the
-    FP64 oracle on the same inputs."""
+    """Precision study at the largest mesh: 262144 water-like atoms, 137.9 A, 128^3, p = 6. For each influence
+    path (FP32 register FFTs along k1; the same transforms as split-BF16 matrix products on the tensor cores):
+    time per evaluation (CUDA graph replays), per-stage times, and the energy / RMS-force / virial error
+    against the FP64 oracle on the same inputs."""
     import torch
 
+    import oracle
     from paper_2009_12617_gb300 import pme
     from paper_2009_12617_gb300 import workloads as wl
 
@@ -983,43 +985,68 @@ def leg_large(args, sampler, dist=None):
     s = wl.large_system(seed=3)
     stream = torch.cuda.Stream(dev)
     plan = pme.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        ref = oracle.spme(s.pos.astype(np.float64), s.q.astype(np.float64), s.K, s.p, s.beta, s.box)
+    finally:
+        oracle.set_threads(1)
+
+    def errs(E, V, F):
+        F = np.asarray(F, dtype=np.float64)
+        return {"rel_energy_error": float(abs(E - ref["energy"]) / abs(ref["energy"])),
+                "rms_force_error": float(np.sqrt(np.mean((F - ref["forces"]) ** 2) / np.mean(ref["forces"] ** 2))),
+                "rel_virial_error": float(np.max(np.abs(np.asarray(V) - ref["virial"])) / np.max(np.abs(ref["virial"])))}
+
+    out = {}
     try:
         pos = torch.from_numpy(s.pos).to(dev)
         q = torch.from_numpy(s.q).to(dev)
         F = torch.empty_like(pos)
-        E, V = pme.pme_compute(plan, pos, q, F)
         pme.pme_reserve(plan, s.n)
-        ev = torch.zeros(7, dtype=torch.float64, device=dev)
-        with torch.cuda.stream(stream):
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=stream):
-                pme.pme_enqueue(plan, pos, q, F, ev)
-            for _ in range(5):
-                g.replay()
-            st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 200
-            t0 = time.time()
-            st.record(stream)
-            for _ in range(reps):
-                g.replay()
-            en.record(stream)
-            torch.cuda.synchronize(dev)
-            sampler.window(t0, time.time())
-        us = 1000.0 * st.elapsed_time(en) / reps
-        stages = pme.pme_profile_stages(plan, pos, q, F, reps=20)
-        acc = errors_vs_oracle(E, V, F.cpu().numpy(), s)
+        for path, name in ((pme.PME_INFLUENCE_FP32, "fp32"), (pme.PME_INFLUENCE_TENSOR, "tensor")):
+            pme.pme_set_influence_path(plan, path)
+            E, V = pme.pme_compute(plan, pos, q, F)
+            Fh = F.cpu().numpy()
+            ev = torch.zeros(7, dtype=torch.float64, device=dev)
+            with torch.cuda.stream(stream):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    pme.pme_enqueue(plan, pos, q, F, ev)
+                for _ in range(5):
+                    g.replay()
+                st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 200
+                t0 = time.time()
+                st.record(stream)
+                for _ in range(reps):
+                    g.replay()
+                en.record(stream)
+                torch.cuda.synchronize(dev)
+                sampler.window(t0, time.time())
+            pme.pme_sync(plan)
+            del g
+            us = 1000.0 * st.elapsed_time(en) / reps
+            stages = pme.pme_profile_stages(plan, pos, q, F, reps=20)
+            out[name] = {"us_per_eval": round(us, 2), "stage_us": {k: round(v, 2) for k, v in stages.items()},
+                         **errs(E, V, Fh)}
+        out["fp32"]["path"] = "FP32 register FFTs along k1 (int64 fixed-point charge mesh, double-float energy sums)"
+        out["tensor"]["path"] = ("k1 transforms as tcgen05 matrix products, operands split into three BF16 terms, "
+                                 "six term products, main and correction products in separate FP32 accumulators")
+        ff = out["fp32"]
         return {"large_grid": {
             "workload": "262144 water-like atoms (87380 triplets + 2 pairs), cubic 137.9 A, 128^3, p=6, beta=0.34/A",
-            "us_per_eval": round(us, 2), "stage_us": {k: round(v, 2) for k, v in stages.items()},
-            "path": "FP32 mesh arithmetic (int64 fixed-point charge mesh, double-float energy sums)",
-            **{k: acc[k] for k in ("rel_energy_error", "rms_force_error", "rel_virial_error")}}}
+            "us_per_eval": ff["us_per_eval"], "stage_us": ff["stage_us"], "path": ff["path"],
+            **{k: ff[k] for k in ("rel_energy_error", "rms_force_error", "rel_virial_error")},
+            "tensor_core_path": out["tensor"]}}
     finally:
         pme.pme_destroy(plan)
 
 
 def leg_profile(args, sampler, dist=None):
     """A short fixed sequence for ncu captures: 10 evaluations of the 65536-atom 64^3 p=4 box, then 5 of the
-    262144-atom 128^3 p=6 box, eager launches on device arrays (six stage kernels each, in stage order)."""
+    262144-atom 128^3 p=6 box, then 3 more of that box with the tensor-core influence stage; eager launches on
+    device arrays (six stage kernels each, in stage order)."""
     import torch
 
     from paper_2009_12617_gb300 import pme
@@ -1027,9 +1054,12 @@ def leg_profile(args, sampler, dist=None):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     out = {}
-    for name, s, reps in (("headline", wl.headline_system(seed=2), 10), ("large", wl.large_system(seed=3), 5)):
+    for name, s, reps in (("headline", wl.headline_system(seed=2), 10), ("large", wl.large_system(seed=3), 5),
+                          ("large_tensor", wl.large_system(seed=3), 3)):
         plan = pme.pme_create(s.K, s.p, s.beta, s.box)
         try:
+            if name == "large_tensor":
+                pme.pme_set_influence_path(plan, pme.PME_INFLUENCE_TENSOR)
             pos = torch.from_numpy(s.pos).to(dev)
             q = torch.from_numpy(s.q).to(dev)
             F = torch.empty_like(pos)

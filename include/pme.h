@@ -158,6 +158,22 @@ pme_status pme_set_launch_mode(int mode);
 
 /* Paper: Sec. V-C (which problem sizes fit in on-chip memory and which need HBM); here the figure the
  * serving loop admits requests by. */
+/* Paper: Sec. VI lists reduced precision among the future work. How the influence stage (the k1 transforms
+ * around the Green's-function multiply) computes, for single-system evaluations of this plan
+ * (pme_compute, pme_enqueue, pme_compute_host, pme_profile_stages, pme_run_steps; batches and the server
+ * always use the FP32 stage):
+ *   PME_INFLUENCE_FP32   (default) 128-point FFTs in FP32 registers;
+ *   PME_INFLUENCE_TENSOR the transforms as dense matrix products on the tensor cores (tcgen05, BF16 inputs,
+ *                        FP32 accumulation), every operand split into three BF16 terms (about 24 bits),
+ *                        the six term products above 2^-24 kept; K1 = 128 only (else PME_EUNSUPPORTED).
+ * Both give the same results within FP32 rounding; the energy, virial and forces stay within the tolerances
+ * against the FP64 reference. The first switch to the tensor path uploads a 192 KB matrix image.
+ * Synchronous with respect to the plan stream. */
+enum { PME_INFLUENCE_FP32 = 0, PME_INFLUENCE_TENSOR = 1 };
+pme_status pme_set_influence_path(pme_plan *plan, int path);
+/* The plan's influence path, or -1 for a NULL plan. */
+int pme_get_influence_path(const pme_plan *plan);
+
 /* Device bytes the plan holds right now (mesh, tables, per-atom scratch). */
 size_t pme_plan_device_bytes(const pme_plan *plan);
 

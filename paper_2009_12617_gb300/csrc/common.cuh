@@ -146,6 +146,8 @@ struct SysDev {
     int lane_slab, lane_conv;    // slab stages / influence stage take the register path (1) or not (0)
     int pdl_late;                // when a stage kernel triggers its successor's launch (PdlScope, pdl.cuh)
     int nt_tile;                 // spread / force CTA threads (128 or 256) chosen by the tuner; 0: density rule
+    const void *tc_w;            // non-null: single-system launches run the influence stage on the tensor
+                                 // cores with this DFT-matrix image (K1 = 128; batches keep the FP32 stage)
     float kinv[3];               // 1 / K_alpha
     // u_alpha = sum_j r_j C[j][alpha], C[j][alpha] = K_alpha a*_alpha[j], as an unevaluated float sum
     // chi + clo (about 48 significant bits), index 3*j + alpha.

@@ -124,7 +124,7 @@ cudaError_t configure_kernels() {
     }
     PME_CUBIC_KS(PME_CFG_K)
 #undef PME_CFG_K
-    return cudaSuccess;
+    return configure_tc_kernel();
 }
 
 // The specialised kernel for the system's plans, or the general one.
@@ -169,7 +169,15 @@ static void launch_tiles_gather(const SysDev &d, cudaStream_t s) {
     else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 3), s, d, STAGE_GATHER);
 }
 
-void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
+void launch_stage(const SysDev &d0, int stage, cudaStream_t s) {
+    // with the tensor-core influence stage, every stage of the evaluation sees its tile count as the number
+    // of influence items (the inverse stage's level-1 reduction reads that many partials)
+    SysDev dt;
+    if (d0.tc_w) {
+        dt = d0;
+        dt.nconv = tc_tiles(d0);
+    }
+    const SysDev &d = d0.tc_w ? dt : d0;
     switch (stage) {
         case STAGE_BIN:
             launch_pdl(k_bin, d.nbin > 0 ? d.nbin : 1, NT_BIN, smem_bin(NT_BIN), s, d, STAGE_BIN);
@@ -184,7 +192,13 @@ void launch_stage(const SysDev &d, int stage, cudaStream_t s) {
             launch_pdl(fwd_kernel(d), d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d, STAGE_FWD);
             break;
         case STAGE_CONV:
-            launch_pdl(conv_kernel(d), d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d, STAGE_CONV);
+            if (d.tc_w) {
+                SysDev dp = d;
+                dp.pdl_late = pdl_when(g_launch_mode, STAGE_CONV);
+                launch_conv_tc(dp, d.tc_w, s);
+            } else {
+                launch_pdl(conv_kernel(d), d.nconv, NT_CONV, smem_conv(d.K1, NT_CONV), s, d, STAGE_CONV);
+            }
             break;
         case STAGE_INV:
             launch_pdl(inv_kernel(d), d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d, STAGE_INV);

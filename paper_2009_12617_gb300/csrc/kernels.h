@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
 
 #include "common.cuh"
 
@@ -57,6 +60,14 @@ cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ct
 
 // Enqueue one stage kernel of system d.
 void launch_stage(const SysDev &d, int stage, cudaStream_t s);
+
+// Tensor-core influence stage (tc_dft.cu): kernel set-up, tiles per evaluation, launch, and the DFT-matrix
+// image (three BF16 terms of the real and imaginary parts, both K halves, 128-byte swizzled K-major rows).
+cudaError_t configure_tc_kernel();
+int tc_tiles(const SysDev &d);
+cudaError_t launch_conv_tc(const SysDev &d, const void *w_img, cudaStream_t s);
+void make_tc_w_image(std::vector<uint8_t> &img);
+constexpr size_t TC_W_IMAGE_BYTES = 2 * 6 * 128 * 128;
 
 // Enqueue the six stage kernels of one evaluation of system d on stream s.
 cudaError_t launch_pipeline(const SysDev &d, cudaStream_t s, const DebugTaps *taps = nullptr);

@@ -192,6 +192,7 @@ SysDev plan_descriptor(const pme_plan *pl, const float *pos, const float *q, int
     d.q = q;
     d.forces = forces;
     d.ev = ev_dev ? ev_dev : pl->d.ctl->ev;
+    d.tc_w = pl->influence_path == PME_INFLUENCE_TENSOR ? pl->tc_w : nullptr;
     return d;
 }
 
@@ -529,6 +530,33 @@ pme_status pme_profile_stages(pme_plan *pl, const float *pos, const float *q, in
     return collect_status(pl, false);
 }
 
+pme_status pme_set_influence_path(pme_plan *pl, int path) {
+    if (!pl) return fail(PME_EINVAL, "plan is NULL");
+    if (path != PME_INFLUENCE_FP32 && path != PME_INFLUENCE_TENSOR)
+        return fail(PME_EINVAL, "path must be PME_INFLUENCE_FP32 or PME_INFLUENCE_TENSOR");
+    if (path == PME_INFLUENCE_TENSOR && pl->K[0] != 128)
+        return fail(PME_EUNSUPPORTED, "the tensor-core influence stage needs K1 = 128 (K1 is %d)", pl->K[0]);
+    DeviceGuard g(pl->dev);
+    if (path == PME_INFLUENCE_TENSOR && !pl->tc_w) {
+        std::vector<uint8_t> img;
+        make_tc_w_image(img);
+        cudaError_t e = lib_malloc(&pl->tc_w, img.size());
+        if (e != cudaSuccess) {
+            pl->tc_w = nullptr;
+            return cuda_fail(e, "cudaMalloc(DFT-matrix image)");
+        }
+        if ((e = cudaMemcpy(pl->tc_w, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy(DFT-matrix image)");
+    }
+    cudaError_t e = cudaStreamSynchronize(pl->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    pl->influence_path = path;
+    ++pl->gen;  // recorded graphs hold the other stage
+    return PME_OK;
+}
+
+int pme_get_influence_path(const pme_plan *pl) { return pl ? pl->influence_path : -1; }
+
 pme_status pme_set_launch_mode(int mode) {
     if (mode < 0 || mode > 3) return fail(PME_EINVAL, "launch mode must be 0, 1, 2 or 3");
     set_launch_mode(mode);
@@ -550,6 +578,7 @@ void pme_destroy(pme_plan *pl) {
     if (pl->g_host.exec) cudaGraphExecDestroy(pl->g_host.exec);
     if (pl->g_md.exec) cudaGraphExecDestroy(pl->g_md.exec);
     if (pl->md_mem) cudaFree(pl->md_mem);
+    if (pl->tc_w) cudaFree(pl->tc_w);
     if (pl->rec_stream) cudaStreamDestroy(pl->rec_stream);
     if (pl->mesh_mem) cudaFree(pl->mesh_mem);
     if (pl->atom_mem) cudaFree(pl->atom_mem);

@@ -29,6 +29,8 @@ struct pme_plan {
     pme::Ctl *h_ctl_dev = nullptr;  // its device-side (mapped) address, or null
     unsigned long long gen = 0;     // bumped whenever the kernels' arguments change (box, tiling)
     int tile_log_set = 0;           // tile edge 2^tile_log_set chosen by the autotuner or the caller (0: default)
+    int influence_path = 0;         // PME_INFLUENCE_FP32 or PME_INFLUENCE_TENSOR (single-system launches)
+    void *tc_w = nullptr;           // DFT-matrix image of the tensor-core influence stage (allocated on demand)
     int tuned_apt = -1000;          // atoms-per-tile class the current tiling was tuned for (-1000: none)
     // Repeated synchronous calls replay a CUDA graph of the whole call, recorded (on a private stream, as
     // the plan stream may not be capturable) once the same arguments come twice in a row: one for device

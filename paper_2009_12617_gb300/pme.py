@@ -41,10 +41,13 @@ EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme
            "pme_compute_noalloc", "pme_batch_set_strategy", "pme_batch_get_strategy",
            "pme_probe_launch", "pme_real_create", "pme_real_set_box", "pme_real_reserve", "pme_real_enqueue",
            "pme_real_compute", "pme_real_destroy", "pme_autotune", "pme_tune_cache", "pme_plan_set_tiling",
-           "pme_plan_get_tiling", "pme_batch_autotune", "pme_run_steps", "pme_debug_fail_alloc")
+           "pme_plan_get_tiling", "pme_batch_autotune", "pme_run_steps", "pme_debug_fail_alloc",
+           "pme_set_influence_path", "pme_get_influence_path")
 
 
 PME_TUNE_FORCE = 1
+PME_INFLUENCE_FP32 = 0
+PME_INFLUENCE_TENSOR = 1
 
 
 class TuneResult(ctypes.Structure):
@@ -145,6 +148,8 @@ def load_library(path: str | None = None):
         "pme_plan_get_tiling": (_st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "pme_batch_autotune": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "pme_debug_fail_alloc": (_st, [ctypes.c_int]),
+        "pme_set_influence_path": (_st, [_vp, ctypes.c_int]),
+        "pme_get_influence_path": (ctypes.c_int, [_vp]),
         "pme_run_steps": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_double, ctypes.c_int, _vp]),
         "pme_real_create": (_st, [ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
         "pme_real_set_box": (_st, [_vp, ctypes.POINTER(ctypes.c_double)]),
@@ -497,6 +502,14 @@ def pme_real_compute(rs: int, pos, q, forces) -> tuple[float, float, np.ndarray]
 def pme_real_destroy(rs: int) -> None:
     if rs:
         load_library().pme_real_destroy(_vp(rs))
+
+
+def pme_set_influence_path(plan: int, path: int) -> None:
+    check(load_library().pme_set_influence_path(_vp(plan), int(path)))
+
+
+def pme_get_influence_path(plan: int) -> int:
+    return int(load_library().pme_get_influence_path(_vp(plan)))
 
 
 def pme_debug_fail_alloc(nth: int) -> None:
