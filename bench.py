@@ -673,7 +673,8 @@ def main():
             torch.cuda.set_device(dist.local)
             sampler = ClockSampler(dist.local)
             out = {}
-            table = {"batched": leg_batched, "serving": leg_serving, "large": leg_large, "profile": leg_profile}
+            table = {"batched": leg_batched, "serving": leg_serving, "large": leg_large, "profile": leg_profile,
+                     "slab": leg_slab}
             for name in args.legs.split(","):
                 out.update(table[name](args, sampler, dist))
             out["clocks"] = sampler.summary()
@@ -1043,6 +1044,75 @@ def leg_large(args, sampler, dist=None):
         pme.pme_destroy(plan)
 
 
+def leg_slab(args, sampler, dist):
+    """Strong scaling of one system over the ranks (only with several ranks): the 65536-atom 64^3 box divided
+    into k1 slabs, one per GPU (pme_slab_*), with the two corner turns as NCCL all-to-alls and the force and
+    energy sums as all-reduces through torch.distributed, all on each rank's stream. Microseconds per
+    evaluation of the one system (max over ranks) and the error of the summed result against the oracle."""
+    if dist.world < 2:
+        return {}
+    import datetime
+
+    import torch
+    import torch.distributed as tdist
+
+    from paper_2009_12617_gb300 import pme
+    from paper_2009_12617_gb300 import workloads as wl
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = tdist.new_group(backend="nccl", timeout=datetime.timedelta(seconds=120))
+    s = wl.headline_system(seed=2)
+    stream = torch.cuda.Stream(dev)
+    slab = pme.pme_slab_create(s.K, s.p, s.beta, s.box, dist.world, dist.rank, stream=stream)
+    try:
+        lay = pme.pme_slab_layout(slab)
+        B = lay["block_values"]
+        pos = torch.from_numpy(s.pos).to(dev)
+        q = torch.from_numpy(s.q).to(dev)
+        send = torch.zeros(dist.world * B * 2, dtype=torch.float32, device=dev)
+        recv, send2, recv2 = torch.zeros_like(send), torch.zeros_like(send), torch.zeros_like(send)
+        F = torch.zeros_like(pos)
+        ev = torch.zeros(7, dtype=torch.float64, device=dev)
+
+        def step():
+            pme.pme_slab_stage1(slab, pos, q, send)
+            tdist.all_to_all_single(recv, send, group=g)
+            pme.pme_slab_stage2(slab, recv, send2, ev)
+            tdist.all_to_all_single(recv2, send2, group=g)
+            pme.pme_slab_stage3(slab, recv2, pos, q, F)
+            tdist.all_reduce(F, group=g)
+            tdist.all_reduce(ev, group=g)
+
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 200
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                step()
+            torch.cuda.synchronize(dev)
+            dist.barrier()
+            t0 = time.time()
+            st.record(stream)
+            for _ in range(reps):
+                step()
+            en.record(stream)
+            torch.cuda.synchronize(dev)
+            dist.barrier()
+            sampler.window(t0, time.time())
+        pme.pme_slab_sync(slab)
+        us = dist.max(1000.0 * st.elapsed_time(en) / reps)
+        out = {"slab_decomposition": {
+            "workload": "one 65536-atom water-like box, 64^3, p=4, divided into k1 slabs over the ranks; corner turns "
+                        "and force / energy sums by NCCL through torch.distributed",
+            "ranks": dist.world, "us_per_eval": round(us, 2), "planes_rank0": list(lay["planes"]),
+            "block_values": B}}
+        if dist.rank == 0:
+            evh = ev.cpu().numpy()
+            out["slab_decomposition"]["accuracy"] = errors_vs_oracle(float(evh[0]), evh[1:], F.cpu().numpy(), s)
+        return out
+    finally:
+        pme.pme_slab_destroy(slab)
+
+
 def leg_profile(args, sampler, dist=None):
     """A short fixed sequence for ncu captures: 10 evaluations of the 65536-atom 64^3 p=4 box, then 5 of the
     262144-atom 128^3 p=6 box, then 3 more of that box with the tensor-core influence stage; eager launches on
@@ -1075,8 +1145,8 @@ def leg_profile(args, sampler, dist=None):
 
 
 def _extras():
-    """Batched, served and largest-mesh legs."""
-    return [leg_batched, leg_serving, leg_large]
+    """Batched, served and largest-mesh legs, and the slab decomposition when there are several ranks."""
+    return [leg_batched, leg_serving, leg_large, leg_slab]
 
 
 if __name__ == "__main__":

@@ -280,6 +280,44 @@ pme_status pme_real_compute(pme_real *rs, const float *pos, const float *q, int6
 void pme_real_destroy(pme_real *rs);
 
 /* ------------------------------------------------------------------------------------------------------ */
+/* One system over several ranks: slab decomposition with two corner turns                                 */
+
+/* Paper: Sec. III-A "FFT", III-C and IV-C: the mesh is divided into slabs, each transformed independently;
+ * an all-to-all "corner turn" regroups the data so that every pipeline holds full pencils for the
+ * Green's-function multiply, and a second one returns it; atoms that affect several pipelines are processed
+ * by each of them (Sec. III-A "Charge Spreading"). Here rank r of nranks owns a contiguous range of mesh
+ * planes along k1 and of influence-stage columns (pme_slab_layout); one evaluation is
+ *   pme_slab_stage1 -> all-to-all -> pme_slab_stage2 -> all-to-all -> pme_slab_stage3,
+ * then the caller sums the ranks' forces and energy / virial partials. The all-to-alls are the caller's
+ * (for example torch.distributed.all_to_all_single over NCCL): send and recv are DEVICE buffers of nranks
+ * equal blocks of block_values complex FP32 values (2 floats each), block s of send going to rank s and block
+ * r of recv coming from rank r. Every call enqueues on the rank's stream and returns without waiting;
+ * nothing waits on another rank. Results equal the undivided evaluation within FP32 rounding (the force
+ * and energy sums are split across ranks). */
+typedef struct pme_slab pme_slab;
+
+/* Rank `rank` of `nranks` for mesh K, order p, beta, cell box (pme_create rules), on cuda_stream. Returns
+ * PME_EUNSUPPORTED when the mesh cannot give every rank a plane and an influence item. */
+pme_status pme_slab_create(const int K[3], int p, double beta, const double box[9], int nranks, int rank,
+                           void *cuda_stream, pme_slab **out);
+/* The rank's planes [planes[0], planes[1]) and half-spectrum columns [columns[0], columns[1]) (c = m2 (K3/2 + 1)
+ * + m3), and the complex values per exchange block; any pointer may be NULL. */
+pme_status pme_slab_layout(const pme_slab *slab, int *planes, int *columns, int64_t *block_values);
+/* Stage 1 on DEVICE pos (n x 3) and q (n), all atoms of the system on every rank: binning, spreading into the
+ * own planes, forward slab transforms of those planes, and the first exchange's send blocks. */
+pme_status pme_slab_stage1(pme_slab *slab, const float *pos, const float *q, int64_t n, float *send);
+/* Stage 2: the first exchange's recv blocks in; the influence stage on the own columns; this rank's partial
+ * (E, virial[6]) to ev_dev (DEVICE, 7 doubles; NULL keeps it internal); the second exchange's send blocks. */
+pme_status pme_slab_stage2(pme_slab *slab, const float *recv, float *send, double *ev_dev);
+/* Stage 3: the second exchange's recv blocks in; inverse slab transforms of the own planes; forces (DEVICE,
+ * n x 3, overwritten) = the part of every atom's force from the own planes (same pos, q, n as stage 1). */
+pme_status pme_slab_stage3(pme_slab *slab, const float *recv, const float *pos, const float *q, int64_t n,
+                           float *forces);
+/* Wait for the rank's stream and report (and clear) device-side errors. */
+pme_status pme_slab_sync(pme_slab *slab);
+void pme_slab_destroy(pme_slab *slab);
+
+/* ------------------------------------------------------------------------------------------------------ */
 /* Multi-step loop on the device                                                                           */
 
 /* Paper: Sec. III runs multiple timesteps on the accelerators with no host communication beyond

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libpme_gb300.so"
-SOURCES = ["kernels.cu", "group.cu", "batch.cu", "plan.cu", "server.cu", "noalloc.cu", "probe.cu", "realspace.cu", "tune.cu", "md.cu", "tc_dft.cu"]
+SOURCES = ["kernels.cu", "group.cu", "batch.cu", "plan.cu", "server.cu", "noalloc.cu", "probe.cu", "realspace.cu", "tune.cu", "md.cu", "tc_dft.cu", "slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

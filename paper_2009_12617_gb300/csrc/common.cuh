@@ -146,6 +146,8 @@ struct SysDev {
     int lane_slab, lane_conv;    // slab stages / influence stage take the register path (1) or not (0)
     int pdl_late;                // when a stage kernel triggers its successor's launch (PdlScope, pdl.cuh)
     int nt_tile;                 // spread / force CTA threads (128 or 256) chosen by the tuner; 0: density rule
+    int item0;                   // first work item of the slab / influence stage launches (slab decomposition)
+    int k1_lo, k1_hi;            // spreading writes only the mesh planes k1_lo <= k1 < k1_hi (slab decomposition)
     const void *tc_w;            // non-null: single-system launches run the influence stage on the tensor
                                  // cores with this DFT-matrix image (K1 = 128; batches keep the FP32 stage)
     float kinv[3];               // 1 / K_alpha

@@ -120,6 +120,9 @@ inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const d
     d.K3 = K[2];
     d.H3 = K[2] / 2 + 1;
     d.p = p;
+    d.item0 = 0;
+    d.k1_lo = 0;
+    d.k1_hi = K[0];
     set_tiling(d, TILE_MIN_LOG);
     choose_fft_paths(d, LANE_FFT_DEFAULT);
     for (int a = 0; a < 3; ++a) d.kinv[a] = 1.0f / (float)K[a];
@@ -216,6 +219,51 @@ inline void make_influence(const int K[3], int p, double beta, const double reci
                 o.z = (float)g;
                 o.w = (float)gp;
             }
+}
+
+// Slab decomposition of one system over P ranks (the paper's distributed FFT, Sec. III-A "FFT", III-C):
+// rank r owns the mesh planes [plane0[r], plane0[r+1]) along k1 for spreading and the slab transforms, and
+// the influence-stage work items [item0[r], item0[r+1]), which cover the half-spectrum columns (m2, m3)
+// flattened as c = m2 H3 + m3 in [col0[r], col0[r+1]). The two corner turns move, between every pair
+// (r, s), the block of r's planes x s's columns: at most maxS x maxW complex values.
+constexpr int SLAB_MAX_RANKS = 64;
+struct SlabLayout {
+    int P;
+    int plane0[SLAB_MAX_RANKS + 1], item0[SLAB_MAX_RANKS + 1], col0[SLAB_MAX_RANKS + 1];
+    int maxS, maxW;
+};
+
+// First half-spectrum column of influence-stage item i (items cover consecutive columns).
+inline int conv_item_col(const SysDev &d, int i) {
+    const int ncol = d.K2 * d.H3;
+    if (i >= d.nconv) return ncol;
+    int c;
+    if (d.lane_conv) {
+        c = i * (CONV_UNITS / plan_L(d.lp_k1));
+    } else {
+        const int m2 = i / d.nchunk3, ch = i - m2 * d.nchunk3;
+        c = m2 * d.H3 + ch * CONV_COLS;
+    }
+    return c < ncol ? c : ncol;
+}
+
+// Even split of the planes and of the influence items; false when a rank would own no plane or no item.
+inline bool make_slab_layout(const SysDev &d, int P, SlabLayout &L) {
+    if (P < 1 || P > SLAB_MAX_RANKS || P > d.K1 || P > d.nconv) return false;
+    L.P = P;
+    L.maxS = L.maxW = 0;
+    for (int r = 0; r <= P; ++r) {
+        L.plane0[r] = (int)((int64_t)r * d.K1 / P);
+        L.item0[r] = (int)((int64_t)r * d.nconv / P);
+        L.col0[r] = conv_item_col(d, L.item0[r]);
+    }
+    for (int r = 0; r < P; ++r) {
+        const int S = L.plane0[r + 1] - L.plane0[r], W = L.col0[r + 1] - L.col0[r];
+        if (S < 1 || W < 1) return false;
+        L.maxS = S > L.maxS ? S : L.maxS;
+        L.maxW = W > L.maxW ? W : L.maxW;
+    }
+    return true;
 }
 
 // Bucket capacity per tile for n atoms: twice the mean occupancy plus a margin, a multiple of 32.

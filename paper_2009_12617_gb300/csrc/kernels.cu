@@ -33,19 +33,19 @@ __global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
 __global__ void __launch_bounds__(NT_SLAB) k_fwd(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late);
-    stage_fwd(d, blockIdx.x, smem);
+    stage_fwd(d, d.item0 + blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_CONV) k_conv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late);
-    stage_conv(d, blockIdx.x, smem);
+    stage_conv(d, d.item0 + blockIdx.x, smem);
 }
 
 __global__ void __launch_bounds__(NT_SLAB) k_inv(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late);
-    stage_inv(d, blockIdx.x, smem);
+    stage_inv(d, d.item0 + blockIdx.x, smem);
 }
 
 // Slab and influence kernels specialised for the lane plans of the cubic meshes of PME_CUBIC_KS (kernels.h);
@@ -56,21 +56,21 @@ template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_fwd_p(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late);
-    stage_fwd<PR, PC>(d, blockIdx.x, smem);
+    stage_fwd<PR, PC>(d, d.item0 + blockIdx.x, smem);
 }
 
 template <int P1>
 __global__ void __launch_bounds__(NT_CONV) k_conv_p(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late);
-    stage_conv<P1>(d, blockIdx.x, smem);
+    stage_conv<P1>(d, d.item0 + blockIdx.x, smem);
 }
 
 template <int PR, int PC>
 __global__ void __launch_bounds__(NT_SLAB) k_inv_p(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     PdlScope pdl(d.pdl_late);
-    stage_inv<PR, PC>(d, blockIdx.x, smem);
+    stage_inv<PR, PC>(d, d.item0 + blockIdx.x, smem);
 }
 
 template <int P, int T>
@@ -208,6 +208,26 @@ void launch_stage(const SysDev &d0, int stage, cudaStream_t s) {
             else if (d.p == 5) launch_tiles_gather<5>(d, s);
             else if (d.p == 6) launch_tiles_gather<6>(d, s);
             else launch_tiles_gather<8>(d, s);
+            break;
+    }
+}
+
+void launch_stage_items(const SysDev &d0, int stage, int first, int count, cudaStream_t s) {
+    SysDev d = d0;
+    d.item0 = first;
+    if (count < 1) return;
+    switch (stage) {
+        case STAGE_FWD:
+            launch_pdl(fwd_kernel(d), count, NT_SLAB, smem_slab(d.K2, d.K3), s, d, STAGE_FWD);
+            break;
+        case STAGE_CONV:
+            launch_pdl(conv_kernel(d), count, NT_CONV, smem_conv(d.K1, NT_CONV), s, d, STAGE_CONV);
+            break;
+        case STAGE_INV:
+            launch_pdl(inv_kernel(d), count, NT_SLAB, smem_inv(d.K2, d.K3), s, d, STAGE_INV);
+            break;
+        default:
+            launch_stage(d0, stage, s);
             break;
     }
 }

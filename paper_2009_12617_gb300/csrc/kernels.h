@@ -60,6 +60,9 @@ cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ct
 
 // Enqueue one stage kernel of system d.
 void launch_stage(const SysDev &d, int stage, cudaStream_t s);
+// The forward, influence or inverse stage over its work items [first, first + count) only (a rank's planes or
+// columns in the slab decomposition).
+void launch_stage_items(const SysDev &d, int stage, int first, int count, cudaStream_t s);
 
 // Tensor-core influence stage (tc_dft.cu): kernel set-up, tiles per evaluation, launch, and the DFT-matrix
 // image (three BF16 terms of the real and imaginary parts, both K halves, 128-byte swizzled K-major rows).

@@ -231,6 +231,7 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
 #pragma unroll
     for (int j1 = 0; j1 < P; ++j1) {
         const int k1 = wrapk(b1 - j1, d.K1);
+        if (k1 < d.k1_lo || k1 >= d.k1_hi) continue;  // another rank's planes (slab decomposition)
 #pragma unroll
         for (int j2 = 0; j2 < P; ++j2) {
             const int k2 = wrapk(b2 - j2, d.K2);
@@ -385,6 +386,7 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
             const int h = hi[i], l = lo[i];
             if ((h | l) == 0) continue;
             const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2);
+            if (k1 < d.k1_lo || k1 >= d.k1_hi) continue;  // another rank's planes (slab decomposition)
             red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
         }
     }
@@ -586,6 +588,37 @@ PME_DEV void stage_conv_smem(const SysDev &d, int item, void *smem) {
         for (int lane = 1; lane < 16; ++lane) s = df_add(s, red2[c * 16 + lane]);
         part[(size_t)item * 8 + c] = s;
     }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Slab decomposition helpers (the corner turns of the paper's distributed 3D FFT, Sec. III-A "FFT"): copy
+// the block of planes [pa, pb) x columns [ca, cb) of the half spectrum to or from a packed buffer
+// (row k1 - pa of width cb - ca), with thread t of nth covering elements t, t + nth, ...
+
+PME_DEV void slab_pack(const float2 *spec, int ncol, int pa, int pb, int ca, int cb, float2 *dst, int t, int nth) {
+    const int w = cb - ca, tot = (pb - pa) * w;
+    for (int i = t; i < tot; i += nth) {
+        const int k = i / w, c = i - k * w;
+        dst[i] = ldcg(spec + (size_t)(pa + k) * ncol + ca + c);
+    }
+}
+PME_DEV void slab_unpack(float2 *spec, int ncol, int pa, int pb, int ca, int cb, const float2 *src, int t, int nth) {
+    const int w = cb - ca, tot = (pb - pa) * w;
+    for (int i = t; i < tot; i += nth) {
+        const int k = i / w, c = i - k * w;
+        spec[(size_t)(pa + k) * ncol + ca + c] = ldcg(src + i);
+    }
+}
+
+// The energy and virial partial of the influence items [i0, i1) (this rank's columns), summed in order in
+// double-float: out[c] for the 7 components (E, then Pi xx yy zz xy xz yz). Thread t < 7 sums component t.
+PME_DEV void slab_energy(const SysDev &d, int i0, int i1, double *out, int t) {
+    if (t >= 7) return;
+    const DF *part = (const DF *)d.partials;
+    DF s;
+    s.hi = s.lo = 0.f;
+    for (int i = i0; i < i1; ++i) s = df_add(s, part[(size_t)i * 8 + t]);
+    out[t] = (double)s.hi + (double)s.lo;
 }
 
 // Energy and virial of the whole system, in two fixed-order levels off the critical path. Level 1 (inverse

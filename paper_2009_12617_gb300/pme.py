@@ -42,7 +42,8 @@ EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme
            "pme_probe_launch", "pme_real_create", "pme_real_set_box", "pme_real_reserve", "pme_real_enqueue",
            "pme_real_compute", "pme_real_destroy", "pme_autotune", "pme_tune_cache", "pme_plan_set_tiling",
            "pme_plan_get_tiling", "pme_batch_autotune", "pme_run_steps", "pme_debug_fail_alloc",
-           "pme_set_influence_path", "pme_get_influence_path")
+           "pme_set_influence_path", "pme_get_influence_path", "pme_slab_create", "pme_slab_layout",
+           "pme_slab_stage1", "pme_slab_stage2", "pme_slab_stage3", "pme_slab_sync", "pme_slab_destroy")
 
 
 PME_TUNE_FORCE = 1
@@ -149,6 +150,13 @@ def load_library(path: str | None = None):
         "pme_batch_autotune": (_st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
         "pme_debug_fail_alloc": (_st, [ctypes.c_int]),
         "pme_set_influence_path": (_st, [_vp, ctypes.c_int]),
+        "pme_slab_create": (_st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+        "pme_slab_layout": (_st, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64)]),
+        "pme_slab_stage1": (_st, [_vp, _vp, _vp, _i64, _vp]),
+        "pme_slab_stage2": (_st, [_vp, _vp, _vp, _vp]),
+        "pme_slab_stage3": (_st, [_vp, _vp, _vp, _vp, _i64, _vp]),
+        "pme_slab_sync": (_st, [_vp]),
+        "pme_slab_destroy": (None, [_vp]),
         "pme_get_influence_path": (ctypes.c_int, [_vp]),
         "pme_run_steps": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_double, ctypes.c_int, _vp]),
         "pme_real_create": (_st, [ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
@@ -510,6 +518,44 @@ def pme_set_influence_path(plan: int, path: int) -> None:
 
 def pme_get_influence_path(plan: int) -> int:
     return int(load_library().pme_get_influence_path(_vp(plan)))
+
+
+def pme_slab_create(K, p: int, beta: float, box, nranks: int, rank: int, stream=None) -> int:
+    Kc = (ctypes.c_int * 3)(*[int(k) for k in K])
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(9)
+    out = _vp()
+    check(load_library().pme_slab_create(Kc, int(p), float(beta), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         int(nranks), int(rank), _vp(_stream_handle(stream)), ctypes.byref(out)))
+    return out.value
+
+
+def pme_slab_layout(slab: int) -> dict:
+    pl, cl, b = (ctypes.c_int * 2)(), (ctypes.c_int * 2)(), _i64()
+    check(load_library().pme_slab_layout(_vp(slab), pl, cl, ctypes.byref(b)))
+    return {"planes": (pl[0], pl[1]), "columns": (cl[0], cl[1]), "block_values": b.value}
+
+
+def pme_slab_stage1(slab: int, pos, q, send) -> None:
+    check(load_library().pme_slab_stage1(_vp(slab), _vp(_f32(pos, (3,), "pos")), _vp(_f32(q, (), "q")),
+                                         int(q.shape[0]), _vp(_ptr(send))))
+
+
+def pme_slab_stage2(slab: int, recv, send, ev_dev=None) -> None:
+    check(load_library().pme_slab_stage2(_vp(slab), _vp(_ptr(recv)), _vp(_ptr(send)), _vp(_ptr(ev_dev))))
+
+
+def pme_slab_stage3(slab: int, recv, pos, q, forces) -> None:
+    check(load_library().pme_slab_stage3(_vp(slab), _vp(_ptr(recv)), _vp(_f32(pos, (3,), "pos")),
+                                         _vp(_f32(q, (), "q")), int(q.shape[0]), _vp(_f32(forces, (3,), "forces"))))
+
+
+def pme_slab_sync(slab: int) -> int:
+    return check(load_library().pme_slab_sync(_vp(slab)))
+
+
+def pme_slab_destroy(slab: int) -> None:
+    if slab:
+        load_library().pme_slab_destroy(_vp(slab))
 
 
 def pme_debug_fail_alloc(nth: int) -> None:

@@ -56,20 +56,15 @@ static void gather_item(const SysDev &d, int it, void *sp) {
     }
 }
 
-extern "C" {
-
-// One or more evaluations (repeat >= 1, same inputs) of the emulated pipeline. Outputs: forces (n*3),
-// ev[7], and optionally the fixed-point mesh as spread (grid_out, K1*K2*K3 int64) and phi (K1*K2*K3).
-// Returns the device status bits of the last evaluation, or -1 / -2 for invalid / unsupported input.
-int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p, double beta, const double box[9],
-             int cap_override, int repeat, float *forces, double *ev, long long *grid_out, float *phi_out,
-             int tile_log) {
+// The emulated resident state of one system (as pme_create + pme_reserve build it on the device).
+// Returns 0, or -1 / -2 for invalid / unsupported input.
+static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta, const double box[9], int cap_override,
+                     int tile_log) {
     char msg[256];
     int v = validate_params(K, p, beta, box, msg, sizeof(msg));
     if (v) return -v;
     double recip[9], vol;
     if (!cell_reciprocal(box, recip, &vol)) return -1;
-    EmuState s;
     memset(&s.d, 0, sizeof(s.d));
     memset(&s.ctl, 0, sizeof(s.ctl));
     SysDev &d = s.d;
@@ -111,6 +106,21 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     d.ova = s.ova.data();
     d.ovb = s.ovb.data();
     d.cap = cap;
+    return 0;
+}
+
+extern "C" {
+
+// One or more evaluations (repeat >= 1, same inputs) of the emulated pipeline. Outputs: forces (n*3),
+// ev[7], and optionally the fixed-point mesh as spread (grid_out, K1*K2*K3 int64) and phi (K1*K2*K3).
+// Returns the device status bits of the last evaluation, or -1 / -2 for invalid / unsupported input.
+int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p, double beta, const double box[9],
+             int cap_override, int repeat, float *forces, double *ev, long long *grid_out, float *phi_out,
+             int tile_log) {
+    EmuState s;
+    const int rc = emu_setup(s, n, K, p, beta, box, cap_override, tile_log);
+    if (rc) return rc;
+    SysDev &d = s.d;
     d.n = (int)n;
     d.nbin = (int)((n + BIN_CHUNK - 1) / BIN_CHUNK);
     d.pos = pos;
@@ -162,6 +172,129 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     for (unsigned long long g : s.grid) clean = clean && g == 0;
     if (!clean) status |= 0x100u;
     return (int)status;
+}
+
+
+// Slab decomposition (the library's pme_slab_* calls), one rank of P: the same stage bodies with the rank's
+// plane window and item ranges, the corner-turn blocks packed and unpacked by the library's own helpers.
+struct EmuSlab {
+    EmuState s;
+    SlabLayout L;
+    int rank = 0;
+};
+
+static void emu_spread_all(EmuState &s, int p) {
+    SysDev &d = s.d;
+    void *sp = s.smem.data();
+    for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
+        switch (p * 10 + d.tlog) {
+            case 43: spread_item<4, 8>(d, it, sp); break;
+            case 53: spread_item<5, 8>(d, it, sp); break;
+            case 63: spread_item<6, 8>(d, it, sp); break;
+            case 83: spread_item<8, 8>(d, it, sp); break;
+            case 44: spread_item<4, 16>(d, it, sp); break;
+            case 54: spread_item<5, 16>(d, it, sp); break;
+            case 64: spread_item<6, 16>(d, it, sp); break;
+            default: spread_item<8, 16>(d, it, sp); break;
+        }
+    }
+}
+
+static void emu_gather_all(EmuState &s, int p) {
+    SysDev &d = s.d;
+    void *sp = s.smem.data();
+    for (int it = 0; it < d.ntiles + OVF_ITEMS; ++it) {
+        switch (p * 10 + d.tlog) {
+            case 43: gather_item<4, 8>(d, it, sp); break;
+            case 53: gather_item<5, 8>(d, it, sp); break;
+            case 63: gather_item<6, 8>(d, it, sp); break;
+            case 83: gather_item<8, 8>(d, it, sp); break;
+            case 44: gather_item<4, 16>(d, it, sp); break;
+            case 54: gather_item<5, 16>(d, it, sp); break;
+            case 64: gather_item<6, 16>(d, it, sp); break;
+            default: gather_item<8, 16>(d, it, sp); break;
+        }
+    }
+}
+
+void *emu_slab_create(int64_t n, const int K[3], int p, double beta, const double box[9], int P, int rank) {
+    EmuSlab *e = new EmuSlab();
+    if (emu_setup(e->s, n, K, p, beta, box, 0, 0) != 0 || !make_slab_layout(e->s.d, P, e->L) || rank < 0 || rank >= P) {
+        delete e;
+        return nullptr;
+    }
+    e->rank = rank;
+    e->s.d.k1_lo = e->L.plane0[rank];
+    e->s.d.k1_hi = e->L.plane0[rank + 1];
+    return e;
+}
+
+void emu_slab_destroy(void *h) { delete (EmuSlab *)h; }
+
+// block_values, and the rank's planes and columns
+int64_t emu_slab_layout(void *h, int *planes, int *cols) {
+    EmuSlab *e = (EmuSlab *)h;
+    planes[0] = e->L.plane0[e->rank];
+    planes[1] = e->L.plane0[e->rank + 1];
+    cols[0] = e->L.col0[e->rank];
+    cols[1] = e->L.col0[e->rank + 1];
+    return (int64_t)e->L.maxS * e->L.maxW;
+}
+
+int emu_slab_stage1(void *h, int64_t n, const float *pos, const float *q, float *send) {
+    EmuSlab *e = (EmuSlab *)h;
+    SysDev &d = e->s.d;
+    const int r = e->rank, p = d.p, ncol = d.K2 * d.H3;
+    d.n = (int)n;
+    d.nbin = (int)((n + BIN_CHUNK - 1) / BIN_CHUNK);
+    d.pos = pos;
+    d.q = q;
+    void *sp = e->s.smem.data();
+    for (int it = 0; it < (d.nbin > 0 ? d.nbin : 1); ++it) stage_bin(d, it, sp);
+    emu_spread_all(e->s, p);
+    for (int k1 = e->L.plane0[r]; k1 < e->L.plane0[r + 1]; ++k1) stage_fwd(d, k1, sp);
+    float2 *buf = (float2 *)send;
+    for (int s = 0; s < e->L.P; ++s)
+        slab_pack(d.spec, ncol, e->L.plane0[r], e->L.plane0[r + 1], e->L.col0[s], e->L.col0[s + 1],
+                  buf + (size_t)s * e->L.maxS * e->L.maxW, 0, 1);
+    return (int)e->s.ctl.status;
+}
+
+int emu_slab_stage2(void *h, const float *recv, float *send, double *ev7) {
+    EmuSlab *e = (EmuSlab *)h;
+    SysDev &d = e->s.d;
+    const int r = e->rank, ncol = d.K2 * d.H3;
+    void *sp = e->s.smem.data();
+    const float2 *in = (const float2 *)recv;
+    for (int s = 0; s < e->L.P; ++s)
+        slab_unpack(d.spec, ncol, e->L.plane0[s], e->L.plane0[s + 1], e->L.col0[r], e->L.col0[r + 1],
+                    in + (size_t)s * e->L.maxS * e->L.maxW, 0, 1);
+    for (int it = e->L.item0[r]; it < e->L.item0[r + 1]; ++it) stage_conv(d, it, sp);
+    for (int c = 0; c < 7; ++c) slab_energy(d, e->L.item0[r], e->L.item0[r + 1], ev7, c);
+    float2 *out = (float2 *)send;
+    for (int s = 0; s < e->L.P; ++s)
+        slab_pack(d.spec, ncol, e->L.plane0[s], e->L.plane0[s + 1], e->L.col0[r], e->L.col0[r + 1],
+                  out + (size_t)s * e->L.maxS * e->L.maxW, 0, 1);
+    return 0;
+}
+
+int emu_slab_stage3(void *h, const float *recv, float *forces) {
+    EmuSlab *e = (EmuSlab *)h;
+    SysDev &d = e->s.d;
+    const int r = e->rank, ncol = d.K2 * d.H3;
+    void *sp = e->s.smem.data();
+    const float2 *in = (const float2 *)recv;
+    for (int s = 0; s < e->L.P; ++s)
+        slab_unpack(d.spec, ncol, e->L.plane0[r], e->L.plane0[r + 1], e->L.col0[s], e->L.col0[s + 1],
+                    in + (size_t)s * e->L.maxS * e->L.maxW, 0, 1);
+    for (int k1 = e->L.plane0[r]; k1 < e->L.plane0[r + 1]; ++k1) stage_inv(d, k1, sp);
+    d.forces = forces;
+    d.ev = e->s.ctl.ev;
+    emu_gather_all(e->s, d.p);
+    e->s.ctl.novf = 0;
+    const unsigned st = e->s.ctl.status;
+    e->s.ctl.status = 0;
+    return (int)st;
 }
 
 }  // extern "C"
