@@ -539,11 +539,58 @@ def run_ours(args, dist: Dist):
 
 
 def run_e2e(pme, plan, s, steps: int):
-    """pme_compute_host on page-locked host buffers, every step: positions and charges move host -> device
-    (read by the binning kernel over the CPU-GPU link), the evaluation runs, forces, energy and virial move
-    device -> host (written by the library's copy kernel); the call returns once they are in host memory."""
+    """End to end through the library's host-array calls on page-locked buffers, every step: positions and
+    charges move host -> device (read by the binning kernel over the CPU-GPU link), the evaluation runs, and
+    forces, energy and virial move device -> host (written by the library's copy kernel).
+    value: pme_enqueue_host with two buffer sets in flight (the host waits for step i - 2, reads its result,
+    writes step i's positions and enqueues it), host clock over all steps; synchronous: pme_compute_host,
+    one call and one wait per step."""
     import torch
 
+    stream = torch.cuda.Stream()
+    L = float(s.box[0, 0])
+    frames = [s.pos.astype(np.float32)]
+    for f in range(7):
+        frames.append(wl_jitter(frames[-1], L, 900, f))
+    bufs = []
+    for _ in range(2):
+        P = torch.empty((s.n, 3), dtype=torch.float32).pin_memory().numpy()
+        Q = torch.empty(s.n, dtype=torch.float32).pin_memory().numpy()
+        F = torch.empty((s.n, 3), dtype=torch.float32).pin_memory().numpy()
+        R = torch.empty(8, dtype=torch.float64).pin_memory().numpy()
+        Q[:] = s.q
+        bufs.append((P, Q, F, R))
+    e2e_plan = pme.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
+    try:
+        def run(nsteps):
+            events = [None, None]
+            energy = 0.0
+            for i in range(nsteps + 2):
+                slot = i % 2
+                if events[slot] is not None:
+                    events[slot].synchronize()
+                    P, Q, F, R = bufs[slot]
+                    if R[7] != 0.0:
+                        raise RuntimeError(f"device status {R[7]} in step {i - 2}")
+                    energy += R[0]  # the step's result, read on the host
+                if i >= nsteps:
+                    continue
+                P, Q, F, R = bufs[slot]
+                P[:] = frames[i % len(frames)]
+                pme.pme_enqueue_host(e2e_plan, P, Q, F, R)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                events[slot] = ev
+            return energy
+
+        run(10)  # records the two argument sets' graphs
+        t0 = time.perf_counter()
+        run(steps)
+        dt = time.perf_counter() - t0
+        t_end = time.time()
+    finally:
+        pme.pme_destroy(e2e_plan)
+    # synchronous, for comparison
     pos_h = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
     q_h = torch.empty(s.n, dtype=torch.float32).pin_memory()
     f_h = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
@@ -552,14 +599,23 @@ def run_e2e(pme, plan, s, steps: int):
     P, Q, F = pos_h.numpy(), q_h.numpy(), f_h.numpy()
     for _ in range(5):
         pme.pme_compute_host(plan, P, Q, F)
-    t0 = time.perf_counter()
+    t1 = time.perf_counter()
     for _ in range(steps):
         pme.pme_compute_host(plan, P, Q, F)
-    dt = time.perf_counter() - t0
+    dts = time.perf_counter() - t1
     return {"value": round(1e6 * dt / steps, 3), "unit": UNIT, "h2d_bytes_per_step": s.n * 16,
-            "d2h_bytes_per_step": s.n * 12 + 7 * 8, "steps": steps,
-            "how": "synchronous pme_compute_host per step on page-locked numpy arrays, host clock"}, \
-        (time.time() - dt, time.time())
+            "d2h_bytes_per_step": s.n * 12 + 8 * 8, "steps": steps,
+            "how": "pme_enqueue_host on two page-locked buffer sets in flight (wait for step i-2, read its energy, "
+                   "write step i's positions, enqueue), host clock",
+            "synchronous_us": round(1e6 * dts / steps, 3),
+            "synchronous_how": "pme_compute_host per step (one call and one wait), host clock"}, \
+        (t_end - dt, t_end)
+
+
+def wl_jitter(pos, L, seed, step):
+    from paper_2009_12617_gb300 import workloads as wl
+
+    return wl.jitter(pos, L, seed, step).astype(np.float32)
 
 
 def cpu_baseline(target_seconds: float = 12.0):

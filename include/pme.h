@@ -136,6 +136,18 @@ pme_status pme_sync(pme_plan *plan);
 pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                             double *energy, double *virial);
 
+/* Paper: Sec. III (many timesteps without host round trips) with the host application of Fig. "MDOverview":
+ * the asynchronous form of pme_compute_host. pos, q, forces (n x 3) and result (8 doubles) must all be
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister), else PME_EINVAL. Enqueues the evaluation on
+ * the plan stream and returns: the binning kernel reads positions and charges in host memory, and one copy
+ * kernel writes the forces and result[0..6] = (energy, virial[6]) and result[7] = the device status bits
+ * (0: no error) into host memory when the stream gets there. Each call may use its own arrays, so a caller
+ * can keep several evaluations in flight (double buffering) and wait on the plan stream for the oldest. The
+ * first call with an argument set records the evaluation as a CUDA graph; the four most recent sets are kept
+ * and replayed. The arrays must stay allocated and unchanged until the evaluation has completed. */
+pme_status pme_enqueue_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
+                            double *result);
+
 /* Paper: Sec. V-B and V-C, which time the stages of the pipeline separately (Table IV brackets the forward
  * and inverse FFTs with timestamps). */
 /* Per-stage device time: runs reps evaluations, each stage kernel bracketed by CUDA events on the plan

@@ -234,7 +234,8 @@ void launch_stage_items(const SysDev &d0, int stage, int first, int count, cudaS
 
 // Forces from device memory to page-locked host memory (coalesced 16-byte stores where both addresses
 // allow) and the control block to its host copy: the last step of an evaluation on host arrays.
-__global__ void __launch_bounds__(256) k_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl) {
+__global__ void __launch_bounds__(256) k_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl,
+                                                  double *res8) {
     pdl_wait();
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
     if (((((size_t)src) | ((size_t)dst)) & 15) == 0) {
@@ -244,11 +245,14 @@ __global__ void __launch_bounds__(256) k_copy_out(const float *src, float *dst, 
     } else {
         for (long long i = tid; i < nf; i += nth) dst[i] = __ldcg(src + i);
     }
-    if (blockIdx.x == 0 && threadIdx.x < sizeof(Ctl) / 4)
+    if (hctl && blockIdx.x == 0 && threadIdx.x < sizeof(Ctl) / 4)
         ((unsigned *)hctl)[threadIdx.x] = __ldcg((const unsigned *)ctl + threadIdx.x);
+    if (res8 && blockIdx.x == 0 && threadIdx.x < 8)  // energy, virial[6], status bits
+        res8[threadIdx.x] = threadIdx.x < 7 ? __ldcg(ctl->ev + threadIdx.x) : (double)__ldcg(&ctl->status);
 }
 
-cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl, cudaStream_t s) {
+cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl, cudaStream_t s,
+                            double *res8) {
     long long blocks = (nf / 4 + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 1216) blocks = 1216;  // 152 SMs x 8
@@ -261,7 +265,7 @@ cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ct
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = g_launch_mode ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_copy_out, src, dst, nf, ctl, hctl);
+    return cudaLaunchKernelEx(&cfg, k_copy_out, src, dst, nf, ctl, hctl, res8);
 }
 
 cudaError_t launch_pipeline(const SysDev &d, cudaStream_t s, const DebugTaps *taps) {

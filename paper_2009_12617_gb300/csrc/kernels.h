@@ -54,9 +54,11 @@ struct DebugTaps {
 enum Stage { STAGE_BIN = 0, STAGE_SPREAD, STAGE_FWD, STAGE_CONV, STAGE_INV, STAGE_GATHER, NUM_STAGES };
 
 // Enqueue the copy of nf floats from device memory to page-locked host memory (dst: its device-side
-// address) and of the control block ctl to its host copy hctl (device-side address), after the work before
-// it on s.
-cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl, cudaStream_t s);
+// address), of the control block ctl to its host copy hctl (device-side address; may be null) and, when
+// res8 (device-side address of page-locked memory) is given, of energy, virial and status bits to res8[0..7],
+// after the work before it on s.
+cudaError_t launch_copy_out(const float *src, float *dst, long long nf, const Ctl *ctl, Ctl *hctl, cudaStream_t s,
+                            double *res8 = nullptr);
 
 // Enqueue one stage kernel of system d.
 void launch_stage(const SysDev &d, int stage, cudaStream_t s);

@@ -232,6 +232,24 @@ static void *device_view(const void *p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Device staging for host-array calls (positions, forces, charges), at least n atoms.
+static pme_status ensure_host_staging(pme_plan *pl, int64_t n) {
+    if (n <= pl->host_cap && pl->host_mem) return PME_OK;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (pl->host_mem) cudaFree(pl->host_mem);
+    pl->host_mem = nullptr;
+    pl->host_cap = 0;
+    const int64_t m = n > 0 ? n : 1;
+    const size_t bytes = align256((size_t)m * 12) * 2 + align256((size_t)m * 4);
+    if ((e = lib_malloc(&pl->host_mem, bytes)) != cudaSuccess) {
+        pl->host_mem = nullptr;
+        return fail(PME_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    pl->host_cap = m;
+    return PME_OK;
+}
+
 // Enqueue the call described by key through graph g: replay it if it was recorded for these arguments,
 // record it now if the previous call (seen) had the same arguments, else enqueue directly. enqueue(stream)
 // issues the call's work on a stream.
@@ -431,6 +449,66 @@ pme_status pme_compute_debug(pme_plan *pl, const float *pos, const float *q, int
     return PME_OK;
 }
 
+pme_status pme_enqueue_host(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *result) {
+    pme_status st = check_atoms(pl, pos, q, n, forces);
+    if (st) return st;
+    if (!result) return fail(PME_EINVAL, "result must be non-NULL");
+    DeviceGuard g(pl->dev);
+    if ((st = plan_reserve(pl, n)) != PME_OK) return st;
+    if ((st = ensure_host_staging(pl, n)) != PME_OK) return st;
+    const float *mpos = n > 0 ? (const float *)device_view(pos) : nullptr;
+    const float *mq = n > 0 ? (const float *)device_view(q) : nullptr;
+    float *mfor = n > 0 ? (float *)device_view(forces) : nullptr;
+    double *mres = (double *)device_view(result);
+    if (!mres || (n > 0 && (!mpos || !mq || !mfor)))
+        return fail(PME_EINVAL, "pme_enqueue_host needs page-locked pos, q, forces and result (cudaHostAlloc / cudaHostRegister)");
+    float *dfor = (float *)((char *)pl->host_mem + align256((size_t)pl->host_cap * 12));
+    const SysDev d = plan_descriptor(pl, mpos, mq, n, dfor, nullptr);
+    pme_plan::EvalGraph key;
+    key.pos = pos;
+    key.q = q;
+    key.forces = forces;
+    key.atoms = pl->atom_mem;
+    key.staging = pl->host_mem;
+    key.result = result;
+    key.n = n;
+    key.mode = launch_mode();
+    key.gen = pl->gen;
+    cudaError_t e;
+    for (pme_plan::EvalGraph &gr : pl->g_async)
+        if (gr.exec && gr.same(key)) {
+            if ((e = cudaGraphLaunch(gr.exec, pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+            return PME_OK;
+        }
+    // first use of these arguments: record the evaluation and the copy kernel as a graph (on the private
+    // stream, so the plan stream may itself be capturing or busy), then launch it
+    if (!pl->rec_stream && (e = cudaStreamCreateWithFlags(&pl->rec_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    if ((e = cudaStreamBeginCapture(pl->rec_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t r = launch_pipeline(d, pl->rec_stream);
+    if (r == cudaSuccess) r = launch_copy_out(dfor, mfor, (long long)n * 3, pl->d.ctl, nullptr, pl->rec_stream, mres);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(pl->rec_stream, &graph);
+    if (r != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(r != cudaSuccess ? r : e, "recording the evaluation");
+    }
+    pme_plan::EvalGraph &slot = pl->g_async[pl->g_async_next];
+    pl->g_async_next = (pl->g_async_next + 1) % 4;
+    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+    slot = key;
+    slot.exec = nullptr;
+    e = cudaGraphInstantiate(&slot.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        slot.exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if ((e = cudaGraphLaunch(slot.exec, pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return PME_OK;
+}
+
 pme_status pme_compute_host(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *energy,
                             double *virial) {
     pme_status st = check_atoms(pl, pos, q, n, forces);
@@ -438,18 +516,7 @@ pme_status pme_compute_host(pme_plan *pl, const float *pos, const float *q, int6
     DeviceGuard g(pl->dev);
     cudaError_t e;
     if ((st = plan_reserve(pl, n)) != PME_OK) return st;
-    if (n > pl->host_cap) {
-        if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-        if (pl->host_mem) cudaFree(pl->host_mem);
-        pl->host_mem = nullptr;
-        pl->host_cap = 0;
-        const size_t bytes = align256((size_t)n * 12) * 2 + align256((size_t)n * 4);
-        if ((e = lib_malloc(&pl->host_mem, bytes)) != cudaSuccess) {
-            pl->host_mem = nullptr;
-            return fail(PME_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
-        }
-        pl->host_cap = n;
-    }
+    if ((st = ensure_host_staging(pl, n)) != PME_OK) return st;
     char *b = (char *)pl->host_mem;
     float *dpos = (float *)b, *dfor = (float *)(b + align256((size_t)pl->host_cap * 12));
     float *dq = (float *)(b + 2 * align256((size_t)pl->host_cap * 12));
@@ -577,6 +644,8 @@ void pme_destroy(pme_plan *pl) {
     if (pl->g_dev.exec) cudaGraphExecDestroy(pl->g_dev.exec);
     if (pl->g_host.exec) cudaGraphExecDestroy(pl->g_host.exec);
     if (pl->g_md.exec) cudaGraphExecDestroy(pl->g_md.exec);
+    for (pme_plan::EvalGraph &gr : pl->g_async)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (pl->md_mem) cudaFree(pl->md_mem);
     if (pl->tc_w) cudaFree(pl->tc_w);
     if (pl->rec_stream) cudaStreamDestroy(pl->rec_stream);

@@ -37,16 +37,19 @@ struct pme_plan {
     // arrays (pme_compute) and one for page-locked host arrays (pme_compute_host).
     struct EvalGraph {
         cudaGraphExec_t exec = nullptr;
-        const void *pos = nullptr, *q = nullptr, *forces = nullptr, *atoms = nullptr, *staging = nullptr;
+        const void *pos = nullptr, *q = nullptr, *forces = nullptr, *atoms = nullptr, *staging = nullptr,
+                   *result = nullptr;
         int64_t n = -1;
         int mode = -1;
         unsigned long long gen = ~0ull;
         bool same(const EvalGraph &o) const {
             return pos == o.pos && q == o.q && forces == o.forces && atoms == o.atoms && staging == o.staging &&
-                   n == o.n && mode == o.mode && gen == o.gen;
+                   result == o.result && n == o.n && mode == o.mode && gen == o.gen;
         }
     };
     EvalGraph g_dev, g_host, seen_dev, seen_host;  // recorded graphs, and the previous call's arguments
+    EvalGraph g_async[4];           // recorded graphs of pme_enqueue_host, most recent argument sets
+    int g_async_next = 0;
     cudaStream_t rec_stream = nullptr;
     // multi-step loop (pme_run_steps): step counter and real-space energies, and the recorded graph of one
     // chunk of steps for the last argument set

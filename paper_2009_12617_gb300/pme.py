@@ -43,7 +43,8 @@ EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme
            "pme_real_compute", "pme_real_destroy", "pme_autotune", "pme_tune_cache", "pme_plan_set_tiling",
            "pme_plan_get_tiling", "pme_batch_autotune", "pme_run_steps", "pme_debug_fail_alloc",
            "pme_set_influence_path", "pme_get_influence_path", "pme_slab_create", "pme_slab_layout",
-           "pme_slab_stage1", "pme_slab_stage2", "pme_slab_stage3", "pme_slab_sync", "pme_slab_destroy")
+           "pme_slab_stage1", "pme_slab_stage2", "pme_slab_stage3", "pme_slab_sync", "pme_slab_destroy",
+           "pme_enqueue_host")
 
 
 PME_TUNE_FORCE = 1
@@ -132,6 +133,7 @@ def load_library(path: str | None = None):
         "pme_reserve": (_st, [_vp, _i64]),
         "pme_sync": (_st, [_vp]),
         "pme_compute_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "pme_enqueue_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
         "pme_profile_stages": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pme_set_launch_mode": (_st, [ctypes.c_int]),
         "pme_plan_device_bytes": (ctypes.c_size_t, [_vp]),
@@ -273,6 +275,18 @@ def pme_reserve(plan: int, n: int) -> None:
 
 def pme_sync(plan: int) -> None:
     check(load_library().pme_sync(_vp(plan)))
+
+
+def pme_enqueue_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray, result: np.ndarray) -> None:
+    """Asynchronous evaluation on page-locked numpy arrays (pos (n,3), q (n,), forces (n,3) float32; result (8,)
+    float64 receives energy, virial[6] and the status bits when the plan stream completes the evaluation)."""
+    for name, a, dt in (("pos", pos, np.float32), ("q", q, np.float32), ("forces", forces, np.float32),
+                        ("result", result, np.float64)):
+        if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be a contiguous {np.dtype(dt).name} array")
+    n = int(q.shape[0])
+    check(load_library().pme_enqueue_host(_vp(plan), _vp(_addr(pos)), _vp(_addr(q)), n, _vp(_addr(forces)),
+                                          _vp(_addr(result))))
 
 
 def pme_compute_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray | None = None):

@@ -352,3 +352,55 @@ def test_headline_trajectory_every_100th_frame(pmelib, oracle_mod):
             cur = wl.jitter(cur, L, 77, f)
     finally:
         pmelib.pme_destroy(plan)
+
+
+def test_enqueue_host_double_buffered(pmelib):
+    """pme_enqueue_host on two sets of page-locked arrays kept in flight alternately: every frame's forces,
+    energy, virial and status equal the synchronous host-array call's bit for bit; pageable arrays are
+    refused."""
+    s = wl.parity_system()
+    n = s.n
+    L = float(s.box[0, 0])
+    frames = [s.pos.astype(np.float32)]
+    for step in range(9):
+        frames.append(wl.jitter(frames[-1], L, 19, step).astype(np.float32))
+    bufs = []
+    for _ in range(2):
+        P = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+        Q = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+        F = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+        R = torch.empty(8, dtype=torch.float64).pin_memory().numpy()
+        Q[:] = s.q
+        bufs.append((P, Q, F, R))
+    stream = torch.cuda.Stream()
+    plan = pmelib.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
+    ref = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+    try:
+        events = [None, None]
+        got = [None] * len(frames)
+        for i, fr in enumerate(frames + [None, None]):
+            slot = i % 2
+            if events[slot] is not None:  # the evaluation of frame i - 2 is done: read it
+                events[slot].synchronize()
+                P, Q, F, R = bufs[slot]
+                got[i - 2] = (F.copy(), R.copy())
+            if fr is None:
+                continue
+            P, Q, F, R = bufs[slot]
+            P[:] = fr
+            R[:] = np.nan
+            pmelib.pme_enqueue_host(plan, P, Q, F, R)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            events[slot] = ev
+        pmelib.pme_sync(plan)
+        for i, fr in enumerate(frames):
+            F2, E2, V2 = pmelib.pme_compute_host(ref, fr.copy(), s.q.copy())
+            F, R = got[i]
+            assert R[7] == 0.0 and R[0] == E2 and np.array_equal(R[1:7], V2) and np.array_equal(F, F2), i
+        with pytest.raises(pmelib.PMEError) as ei:
+            pmelib.pme_enqueue_host(plan, frames[0].copy(), s.q.copy(), np.empty((n, 3), np.float32), np.zeros(8))
+        assert ei.value.status == pmelib.PME_EINVAL
+    finally:
+        pmelib.pme_destroy(ref)
+        pmelib.pme_destroy(plan)
