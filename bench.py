@@ -434,6 +434,29 @@ def run_ours(args, dist: Dist):
         modes[f"{name}_us_per_eval"] = round(1000.0 * start.elapsed_time(end) / nm, 3)
         del gm
     pme.pme_set_launch_mode(2)  # the library default
+    # slab-split sweep: the forward / inverse slab stages on 2 or 4 CTAs per slab (thread-block clusters;
+    # the default, one CTA per slab, is the headline)
+    for cs in (2, 4):
+        pme.pme_set_slab_split(cs)
+        gm = []
+        with torch.cuda.stream(stream):
+            for f in range(100):
+                gg = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gg, stream=stream):
+                    pme.pme_enqueue(plan, frames[f], q, forces, ev)
+                gm.append(gg)
+            for i in range(20):
+                gm[i % 100].replay()
+            torch.cuda.synchronize(dev)
+            nm = min(args.steps, 2000)
+            start.record(stream)
+            for i in range(nm):
+                gm[i % 100].replay()
+            end.record(stream)
+            torch.cuda.synchronize(dev)
+        modes[f"slab_split_{cs}_us_per_eval"] = round(1000.0 * start.elapsed_time(end) / nm, 3)
+        del gm
+    pme.pme_set_slab_split(1)  # the library default
     pme.pme_sync(plan)
     result["config"].update(modes)
 
@@ -542,52 +565,76 @@ def run_e2e(pme, plan, s, steps: int):
     """End to end through the library's host-array calls on page-locked buffers, every step: positions and
     charges move host -> device (read by the binning kernel over the CPU-GPU link), the evaluation runs, and
     forces, energy and virial move device -> host (written by the library's copy kernel).
-    value: pme_enqueue_host with two buffer sets in flight (the host waits for step i - 2, reads its result,
-    writes step i's positions and enqueues it), host clock over all steps; synchronous: pme_compute_host,
-    one call and one wait per step."""
+    value: pme_enqueue_host with two steps in flight (the host waits for step i - 2, reads its result and
+    enqueues step i), host clock over all steps; host_writes_positions_us: the same with the host copying the
+    positions of each step into page-locked memory first; synchronous: pme_compute_host, one call and one wait
+    per step."""
     import torch
 
     stream = torch.cuda.Stream()
     L = float(s.box[0, 0])
     frames = [s.pos.astype(np.float32)]
-    for f in range(7):
+    for f in range(3):
         frames.append(wl_jitter(frames[-1], L, 900, f))
-    bufs = []
-    for _ in range(2):
-        P = torch.empty((s.n, 3), dtype=torch.float32).pin_memory().numpy()
-        Q = torch.empty(s.n, dtype=torch.float32).pin_memory().numpy()
-        F = torch.empty((s.n, 3), dtype=torch.float32).pin_memory().numpy()
-        R = torch.empty(8, dtype=torch.float64).pin_memory().numpy()
-        Q[:] = s.q
-        bufs.append((P, Q, F, R))
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype).pin_memory().numpy()
+
+    # four page-locked position frames (prepared before the timed region), one charge array, two force/result
+    # sets: step i reads frame i % 4 and writes set i % 2, so four argument sets cycle (one cached graph each)
+    P_frames = [pinned((s.n, 3), torch.float32) for _ in frames]
+    for P, fr in zip(P_frames, frames):
+        P[:] = fr
+    Q = pinned(s.n, torch.float32)
+    Q[:] = s.q
+    outs = [(pinned((s.n, 3), torch.float32), pinned(8, torch.float64)) for _ in range(2)]
     e2e_plan = pme.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
     try:
-        def run(nsteps):
-            events = [None, None]
+        def run(nsteps, host_writes):
+            """host_writes: the host copies step i's frame into a working position array of its slot before
+            enqueueing (as an integrator writing its new positions would), instead of cycling prepared frames."""
+            events = [torch.cuda.Event(), torch.cuda.Event()]
             energy = 0.0
             for i in range(nsteps + 2):
                 slot = i % 2
-                if events[slot] is not None:
+                if i >= 2:
                     events[slot].synchronize()
-                    P, Q, F, R = bufs[slot]
+                    R = outs[slot][1]
                     if R[7] != 0.0:
                         raise RuntimeError(f"device status {R[7]} in step {i - 2}")
                     energy += R[0]  # the step's result, read on the host
                 if i >= nsteps:
                     continue
-                P, Q, F, R = bufs[slot]
-                P[:] = frames[i % len(frames)]
+                F, R = outs[slot]
+                if host_writes:
+                    P = P_frames[slot]
+                    P[:] = frames[i % len(frames)]
+                else:
+                    P = P_frames[i % len(P_frames)]
                 pme.pme_enqueue_host(e2e_plan, P, Q, F, R)
-                ev = torch.cuda.Event()
-                ev.record(stream)
-                events[slot] = ev
+                events[slot].record(stream)
             return energy
 
-        run(10)  # records the two argument sets' graphs
+        run(10, False)  # records the argument sets' graphs
         t0 = time.perf_counter()
-        run(steps)
+        run(steps, False)
         dt = time.perf_counter() - t0
         t_end = time.time()
+        run(10, True)
+        t0 = time.perf_counter()
+        run(steps, True)
+        dt_w = time.perf_counter() - t0
+        # device time of the same steps enqueued back to back (CUDA events on the plan stream, no host
+        # waits): what the two-in-flight loop converges to when the host keeps ahead
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nd = min(steps, 2000)
+        st.record(stream)
+        for i in range(nd):
+            F, R = outs[i % 2]
+            pme.pme_enqueue_host(e2e_plan, P_frames[i % len(P_frames)], Q, F, R)
+        en.record(stream)
+        en.synchronize()
+        dev_us = 1000.0 * st.elapsed_time(en) / nd
     finally:
         pme.pme_destroy(e2e_plan)
     # synchronous, for comparison
@@ -605,8 +652,13 @@ def run_e2e(pme, plan, s, steps: int):
     dts = time.perf_counter() - t1
     return {"value": round(1e6 * dt / steps, 3), "unit": UNIT, "h2d_bytes_per_step": s.n * 16,
             "d2h_bytes_per_step": s.n * 12 + 8 * 8, "steps": steps,
-            "how": "pme_enqueue_host on two page-locked buffer sets in flight (wait for step i-2, read its energy, "
-                   "write step i's positions, enqueue), host clock",
+            "how": "pme_enqueue_host with two steps in flight on page-locked arrays (wait for step i-2, read its "
+                   "energy and status, enqueue step i on prepared position frame i % 4), host clock",
+            "device_us_per_step": round(dev_us, 3),
+            "device_how": "the same steps enqueued back to back, CUDA events on the plan stream",
+            "host_writes_positions_us": round(1e6 * dt_w / steps, 3),
+            "host_writes_how": "the same, the host copying each step's 786 KB of positions into the slot's "
+                               "page-locked array before enqueueing it",
             "synchronous_us": round(1e6 * dts / steps, 3),
             "synchronous_how": "pme_compute_host per step (one call and one wait), host clock"}, \
         (t_end - dt, t_end)

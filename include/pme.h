@@ -168,6 +168,16 @@ pme_status pme_profile_stages(pme_plan *plan, const float *pos, const float *q, 
  * values. */
 pme_status pme_set_launch_mode(int mode);
 
+/* Paper: Sec. III-A ("FFT"): each slab of the 3D transform is a 2D transform of one mesh plane; the paper
+ * gives each slab a pipeline. Here: how many CTAs (SMs) transform one slab in the forward (fwd_ctas) and
+ * in the inverse (inv_ctas) slab stage of single-system evaluations (process-wide, for launches issued
+ * afterwards): 1, or 2 / 4 CTAs forming a thread-block cluster that exchanges its intermediate rows or
+ * columns through distributed shared memory. Meshes with K2 = K3 in {32, 64, 128} have the 2-CTA kernels,
+ * K2 = K3 = 64 the 4-CTA ones; other meshes keep one CTA per slab. The default is 1 and 1: split slabs
+ * measured slower in the pipelined evaluation (their stage alone can be faster). Results are bitwise the
+ * same for every value. Returns PME_EINVAL for other values. */
+pme_status pme_set_slab_split(int fwd_ctas, int inv_ctas);
+
 /* Paper: Sec. V-C (which problem sizes fit in on-chip memory and which need HBM); here the figure the
  * serving loop admits requests by. */
 /* Paper: Sec. VI lists reduced precision among the future work. How the influence stage (the k1 transforms
@@ -215,12 +225,12 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
 
 /* Paper: Sec. IV-A and Table III size the FFT and spreading pipelines to each problem size on the FPGA; the
  * GPU counterpart is choosing, per mesh and atom density, the spreading / force-interpolation tile edge
- * (8^3 or 16^3 mesh points) and CTA size (128 or 256 threads). Every such choice gives bit-identical results
- * (an exact integer charge mesh; each atom's force summed over its support in a fixed order), so tuning
- * changes only speed. */
+ * (8^3 or 16^3 mesh points) and CTA size (128 or 256 threads; 256 or 512 with 16^3 tiles). Every such choice
+ * gives bit-identical results (an exact integer charge mesh; each atom's force summed over its support in a
+ * fixed order), so tuning changes only speed. */
 typedef struct {
     int tile_edge;       /* chosen tile edge (8 or 16 mesh points) */
-    int tile_threads;    /* chosen spread / force CTA size (128 or 256) */
+    int tile_threads;    /* chosen spread / force CTA size (128, 256, or 512 with 16^3 tiles) */
     double us_per_eval;  /* its time per evaluation (0 when taken from the cache) */
     double default_us;   /* the default configuration's time (0 when taken from the cache) */
     int candidates;      /* configurations tried */
@@ -242,9 +252,10 @@ pme_status pme_autotune(pme_plan *plan, const float *pos, const float *q, int64_
  * choices in memory only. Process-wide. */
 pme_status pme_tune_cache(const char *path);
 
-/* Set the plan's tile edge (0 = default, 8 or 16) and spread / force CTA size (0 = by atom density, 128 or
- * 256) by hand; the current configuration is reported by pme_plan_get_tiling. Batches built on the plan pick
- * the change up at their next pme_batch_enqueue. */
+/* Set the plan's tile edge (0 = default: 16 where the 16^3 tiling has at least two tiles per SM and about
+ * 256 atoms per tile or more, else 8) and spread / force CTA size (0 = by atom density, 128 or 256, or 512
+ * with tile edge 16) by hand; the current configuration is reported by pme_plan_get_tiling. Batches built on
+ * the plan pick the change up at their next pme_batch_enqueue. */
 pme_status pme_plan_set_tiling(pme_plan *plan, int tile_edge, int tile_threads);
 pme_status pme_plan_get_tiling(const pme_plan *plan, int *tile_edge, int *tile_threads);
 

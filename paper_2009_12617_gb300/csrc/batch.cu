@@ -386,7 +386,7 @@ static pme_status batch_record_grouped(pme_batch *b, const float *pos, const flo
     return PME_OK;
 }
 
-// Group the systems by mesh shape and order (and tile edge); returns false if grouping is not possible.
+// Group the systems by mesh shape, order and tile edge (a group shares its kernels and CTA shape).
 static bool batch_make_groups(pme_batch *b) {
     const int nsys = (int)b->sys.size();
     std::vector<int> idx(nsys);
@@ -400,7 +400,6 @@ static bool batch_make_groups(pme_batch *b) {
     b->groups.clear();
     for (int i = 0; i < nsys; ++i) {
         const SysDev &d = b->sys[idx[i]];
-        if (d.tlog != 3) return false;
         if (i == 0 || key(idx[i]) != key(idx[i - 1])) b->groups.push_back({i, 0, 0});
         pme_batch::Group &g = b->groups.back();
         ++g.count;

@@ -50,11 +50,14 @@ constexpr int MAX_K = 128;
 // Tile counters sit on separate 128-byte lines so the binning atomics spread over the L2 slices.
 constexpr int BCOUNT_STRIDE = 32;
 // Shared-memory accumulation splits each fixed-point contribution v into hi = rn(v / 2^20) and
-// lo = rn(v - hi 2^20) in [-2^19, 2^19], summed in two int32 arrays with native 32-bit atomics. With at
-// most CAP_MAX atoms per tile and |q| <= Q_TILE_MAX (|v| <= 2^41), neither sum can overflow; atoms with
-// larger charges take the 64-bit global path instead.
+// lo = rn(v - hi 2^20) in [-2^19, 2^19], summed in two int32 arrays with native 32-bit atomics. A B-spline
+// weight of order >= 4 is at most 2/3, so with |q| <= Q_TILE_MAX every |v| <= 2 (2/3)^3 2^40 < 2^39, |hi|
+// <= 2^19; with at most 1024 atoms per tile neither sum reaches 2^30. Atoms with larger charges take the
+// 64-bit global path instead. Bucket capacity per tile: at most CAP_MAX (8^3 tiles) or CAP_MAX16 (16^3).
 constexpr float Q_TILE_MAX = 2.0f;
 constexpr int CAP_MAX = 512;
+constexpr int CAP_MAX16 = 1024;
+constexpr int cap_max_for(int tlog) { return tlog >= 4 ? CAP_MAX16 : CAP_MAX; }
 // Columns m3 per influence-stage work item (shared-memory transform path).
 constexpr int CONV_COLS = 8;
 // Lane plans of the register-resident transforms: plan c has length LANE_L[c] * LANE_E[c], L lanes of

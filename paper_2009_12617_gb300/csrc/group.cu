@@ -28,14 +28,14 @@ __global__ void __launch_bounds__(NT_BIN) k_bin_g(GroupArgs a) {
     if (item < sd.nbin) stage_bin(sd, item, smem);
 }
 
-template <int P>
-__global__ void __launch_bounds__(NT_TILE) k_spread_g(GroupArgs a) {
+template <int P, int T>
+__global__ void __launch_bounds__(tile_nt_bound(T)) k_spread_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
-    spread_clear<P, 8>(smem);  // before the wait: shared memory only
+    spread_clear<P, T>(smem);  // before the wait: shared memory only
     PdlScope pdl(a.late);
     const int item = group_load(a, sd);
-    stage_spread<P, 8>(sd, item, smem, true);
+    stage_spread<P, T>(sd, item, smem, true);
 }
 
 template <int PR, int PC>
@@ -65,14 +65,26 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv_g(GroupArgs a) {
     stage_inv<PR, PC>(sd, item, smem);
 }
 
-template <int P>
-__global__ void __launch_bounds__(NT_TILE) k_gather_g(GroupArgs a) {
+template <int P, int T>
+__global__ void __launch_bounds__(tile_nt_bound(T)) k_gather_g(GroupArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SysDev sd;
     PdlScope pdl(a.late);
     const int item = group_load(a, sd);
-    stage_gather<P, 8>(sd, item, smem);
+    stage_gather<P, T>(sd, item, smem);
 }
+
+// The spread / force kernels of a group: order p, tile edge 2^tlog.
+template <int T>
+static void (*spread_g_t(int p))(GroupArgs) {
+    return p == 4 ? k_spread_g<4, T> : (p == 5 ? k_spread_g<5, T> : (p == 6 ? k_spread_g<6, T> : k_spread_g<8, T>));
+}
+template <int T>
+static void (*gather_g_t(int p))(GroupArgs) {
+    return p == 4 ? k_gather_g<4, T> : (p == 5 ? k_gather_g<5, T> : (p == 6 ? k_gather_g<6, T> : k_gather_g<8, T>));
+}
+static void (*spread_g(const SysDev &d))(GroupArgs) { return d.tlog == 4 ? spread_g_t<16>(d.p) : spread_g_t<8>(d.p); }
+static void (*gather_g(const SysDev &d))(GroupArgs) { return d.tlog == 4 ? gather_g_t<16>(d.p) : gather_g_t<8>(d.p); }
 
 static cudaError_t set_limit(const void *fn) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -80,10 +92,14 @@ static cudaError_t set_limit(const void *fn) {
 }
 
 cudaError_t configure_group_kernels() {
-    const void *fns[] = {(const void *)k_bin_g,          (const void *)k_spread_g<4>,        (const void *)k_spread_g<5>,
-                         (const void *)k_spread_g<6>,    (const void *)k_spread_g<8>,        (const void *)k_fwd_g<-1, -1>,
-                         (const void *)k_conv_g<-1>,     (const void *)k_inv_g<-1, -1>,      (const void *)k_gather_g<4>,
-                         (const void *)k_gather_g<5>,    (const void *)k_gather_g<6>,        (const void *)k_gather_g<8>};
+    const void *fns[] = {(const void *)k_bin_g, (const void *)k_fwd_g<-1, -1>, (const void *)k_conv_g<-1>,
+                         (const void *)k_inv_g<-1, -1>};
+    for (int p : {4, 5, 6, 8})
+        for (const void *f : {(const void *)spread_g_t<8>(p), (const void *)spread_g_t<16>(p),
+                              (const void *)gather_g_t<8>(p), (const void *)gather_g_t<16>(p)}) {
+            cudaError_t e = set_limit(f);
+            if (e != cudaSuccess) return e;
+        }
     for (const void *f : fns) {
         cudaError_t e = set_limit(f);
         if (e != cudaSuccess) return e;
@@ -166,15 +182,15 @@ cudaError_t launch_group_chain(const SysDev *sys_dev, int nsys, const SysDev &pr
         switch (stage) {
             case STAGE_BIN: e = launch_ex(k_bin_g, grid, NT_BIN, smem_bin(NT_BIN), s, a); break;
             case STAGE_SPREAD:
-                e = launch_ex(d.p == 4 ? k_spread_g<4> : (d.p == 5 ? k_spread_g<5> : (d.p == 6 ? k_spread_g<6> : k_spread_g<8>)), grid,
-                              (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK), smem_spread(d.p, 3), s, a);
+                e = launch_ex(spread_g(d), grid, (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK),
+                              smem_spread(d.p, d.tlog), s, a);
                 break;
             case STAGE_FWD: e = launch_ex(fwd_g(d), grid, NT_SLAB, smem_slab(d.K2, d.K3), s, a); break;
             case STAGE_CONV: e = launch_ex(conv_g(d), grid, NT_CONV, smem_conv(d.K1, NT_CONV), s, a); break;
             case STAGE_INV: e = launch_ex(inv_g(d), grid, NT_SLAB, smem_inv(d.K2, d.K3), s, a); break;
             default:
-                e = launch_ex(d.p == 4 ? k_gather_g<4> : (d.p == 5 ? k_gather_g<5> : (d.p == 6 ? k_gather_g<6> : k_gather_g<8>)), grid,
-                              (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK), smem_gather_all(d.p, 3), s, a);
+                e = launch_ex(gather_g(d), grid, (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK),
+                              smem_gather_all(d.p, d.tlog), s, a);
                 break;
         }
         if (e != cudaSuccess) return e;

@@ -79,13 +79,15 @@ inline void set_tiling(SysDev &d, int tlog) {
     d.ntiles = d.nt1 * d.nt2 * d.nt3;
 }
 
-// Tile edge for n atoms. 8^3 tiles measured faster than 16^3 on GB300 even where they hold few atoms
-// (128^3 at p = 6: 187 vs 331 us per evaluation): many light CTAs hide latency better than few heavy ones,
-// and fuller tiles overflow the bucket cap on small meshes. So the edge is 8; 16 stays available (results
-// do not depend on it).
-inline int choose_tile_log(int64_t n, const int K[3]) {
-    (void)n;
-    (void)K;
+// Tile edge for n atoms on a GPU with `sms` SMs. 16^3 tiles halve the halo each tile adds to the global
+// mesh (a region of (16 + p - 1)^3 points per 4096 instead of (8 + p - 1)^3 per 512) and hold enough atoms
+// per residue class for the dealt order to avoid shared-memory bank conflicts, but there are 8 times fewer
+// of them. They pay when there are still at least two per SM and they hold about 256 atoms or more (128^3,
+// 262144 atoms, p = 6: 144 vs 151 us per evaluation on GB300); otherwise 8^3 tiles (many light CTAs) are
+// faster. Results do not depend on the edge.
+inline int choose_tile_log(int64_t n, const int K[3], int sms) {
+    const int64_t t16 = (int64_t)((K[0] + 15) / 16) * ((K[1] + 15) / 16) * ((K[2] + 15) / 16);
+    if (sms > 0 && t16 >= 2 * (int64_t)sms && n >= 256 * t16) return TILE_MAX_LOG;
     return TILE_MIN_LOG;
 }
 
@@ -266,14 +268,16 @@ inline bool make_slab_layout(const SysDev &d, int P, SlabLayout &L) {
     return true;
 }
 
-// Bucket capacity per tile for n atoms: twice the mean occupancy plus a margin, a multiple of 32.
-// Atoms beyond it go to the overflow list (handled by global-memory paths), so this only tunes speed.
-inline int bucket_capacity(int64_t n, int ntiles) {
+// Bucket capacity per tile for n atoms in tiles of edge 2^tlog: twice the mean occupancy plus a margin, a
+// multiple of 32, at most cap_max_for(tlog). Atoms beyond it go to the overflow list (handled by
+// global-memory paths), so this only tunes speed.
+inline int bucket_capacity(int64_t n, int ntiles, int tlog) {
+    const int cmax = cap_max_for(tlog);
     const double mean = (double)n / (double)ntiles;
     const double want = 2.0 * mean + 32.0;
-    int cap = want > (double)CAP_MAX ? CAP_MAX : (int)want;
+    int cap = want > (double)cmax ? cmax : (int)want;
     cap = (cap + 31) / 32 * 32;
-    return cap < 32 ? 32 : (cap > CAP_MAX ? CAP_MAX : cap);
+    return cap < 32 ? 32 : (cap > cmax ? cmax : cap);
 }
 
 // Bytes of the padded tile-counter array and of the influence-stage partials.

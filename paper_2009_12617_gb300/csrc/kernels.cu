@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(NT_BIN) k_bin(SysDev d) {
 }
 
 template <int P, int T>
-__global__ void __launch_bounds__(NT_TILE) k_spread(SysDev d) {
+__global__ void __launch_bounds__(tile_nt_bound(T)) k_spread(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     // before the wait: shared memory and kernel parameters only
     spread_clear<P, T>(smem);
@@ -73,8 +73,38 @@ __global__ void __launch_bounds__(NT_SLAB) k_inv_p(SysDev d) {
     stage_inv<PR, PC>(d, d.item0 + blockIdx.x, smem);
 }
 
+// Slab kernels with each slab split over a thread-block cluster of CS CTAs (slab d.item0 + blockIdx.x / CS,
+// cluster rank blockIdx.x mod CS), for K2 = K3 = K. They keep the one-CTA kernels' lane plans (the same
+// transforms in the same order, so the same bits), with fewer transforms per CTA.
+template <int K, int CS>
+struct SlabSplit {
+    static constexpr int H3 = K / 2 + 1;
+    static constexpr int PR = Cubic<K>::PR, PC = Cubic<K>::PC;
+    static constexpr int units(int c, int ntr) { return ((ntr + 32 / plan_L(c) - 1) / (32 / plan_L(c))) * 32; }
+    static constexpr int NT_FWD = units(PR, K / CS) > units(PC, (H3 + CS - 1) / CS) ? units(PR, K / CS)
+                                                                                       : units(PC, (H3 + CS - 1) / CS);
+    static constexpr int NT_INV = NT_FWD + 64;  // two spare warps for the side work
+    static_assert(PR >= 0 && PC >= 0 && NT_INV <= 1024, "split slab plans");
+};
+
+template <int K, int CS>
+__global__ void __launch_bounds__(SlabSplit<K, CS>::NT_FWD) k_fwd_c(SysDev d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late);
+    const int c = (int)cg::this_cluster().block_rank();
+    stage_fwd_cluster<SlabSplit<K, CS>::PR, SlabSplit<K, CS>::PC, CS>(d, d.item0 + blockIdx.x / CS, c, smem);
+}
+
+template <int K, int CS>
+__global__ void __launch_bounds__(SlabSplit<K, CS>::NT_INV) k_inv_c(SysDev d) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PdlScope pdl(d.pdl_late);
+    const int c = (int)cg::this_cluster().block_rank();
+    stage_inv_cluster<SlabSplit<K, CS>::PR, SlabSplit<K, CS>::PC, CS>(d, d.item0 + blockIdx.x / CS, c, smem);
+}
+
 template <int P, int T>
-__global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
+__global__ void __launch_bounds__(tile_nt_bound(T)) k_gather(SysDev d) {
     extern __shared__ __align__(16) unsigned char smem[];
     int org[3] = {0, 0, 0};  // before the wait: kernel parameters only
     if ((int)blockIdx.x < d.ntiles) tile_origin(d, blockIdx.x, org[0], org[1], org[2]);
@@ -83,7 +113,7 @@ __global__ void __launch_bounds__(NT_TILE) k_gather(SysDev d) {
 }
 
 static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
-                       const SysDev &d0, int stage) {
+                       const SysDev &d0, int stage, unsigned cluster = 1) {
     SysDev d = d0;
     d.pdl_late = pdl_when(g_launch_mode, stage);
     cudaLaunchConfig_t cfg = {};
@@ -91,12 +121,57 @@ static void launch_pdl(void (*kernel)(SysDev), unsigned grid, unsigned block, si
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[2];
+    unsigned na = 0;
+    if (cluster > 1) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = cluster;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (g_launch_mode) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = g_launch_mode ? 1 : 0;
+    cfg.numAttrs = na;
     cudaLaunchKernelEx(&cfg, kernel, d);
+}
+
+// CTAs per slab of the forward and the inverse slab stages (thread-block clusters), process-wide.
+static int g_slab_split[2] = {1, 1};  // split slabs measured slower in the pipelined evaluation
+int set_slab_split(int fwd_ctas, int inv_ctas) {
+    for (int c : {fwd_ctas, inv_ctas})
+        if (c != 1 && c != 2 && c != 4) return -1;
+    g_slab_split[0] = fwd_ctas;
+    g_slab_split[1] = inv_ctas;
+    return 0;
+}
+int slab_split(int inverse) { return g_slab_split[inverse ? 1 : 0]; }
+
+// The split slab kernels instantiated: cubic meshes K, clusters of CS CTAs.
+#define PME_SPLIT_KS(X) X(32, 2) X(64, 2) X(64, 4) X(128, 2)
+
+// Launches the split forward (fwd = true) or inverse slab kernel for the items [d.item0, d.item0 + count)
+// if the mesh has one for the current split, else returns false.
+static bool launch_split_slab(const SysDev &d, bool fwd, int count, cudaStream_t s) {
+    const int cs = g_slab_split[fwd ? 0 : 1];
+    if (cs == 1 || !d.lane_slab || d.K2 != d.K3) return false;
+#define PME_SPLIT_LAUNCH(K, CS)                                                                                  \
+    if (d.K2 == K && cs == CS) {                                                                                 \
+        if (fwd)                                                                                                 \
+            launch_pdl(k_fwd_c<K, CS>, (unsigned)(count * CS), SlabSplit<K, CS>::NT_FWD, smem_slab(K, K), s, d, \
+                       STAGE_FWD, CS);                                                                           \
+        else                                                                                                     \
+            launch_pdl(k_inv_c<K, CS>, (unsigned)(count * CS), SlabSplit<K, CS>::NT_INV, smem_inv(K, K), s, d,  \
+                       STAGE_INV, CS);                                                                           \
+        return true;                                                                                             \
+    }
+    PME_SPLIT_KS(PME_SPLIT_LAUNCH)
+#undef PME_SPLIT_LAUNCH
+    return false;
 }
 
 static cudaError_t set_smem_limit(const void *fn, size_t bytes) {
@@ -124,6 +199,13 @@ cudaError_t configure_kernels() {
     }
     PME_CUBIC_KS(PME_CFG_K)
 #undef PME_CFG_K
+#define PME_CFG_SPLIT(K, CS)                                                                \
+    for (const void *f : {(const void *)k_fwd_c<K, CS>, (const void *)k_inv_c<K, CS>}) {   \
+        cudaError_t e = set_smem_limit(f, big);                                             \
+        if (e != cudaSuccess) return e;                                                     \
+    }
+    PME_SPLIT_KS(PME_CFG_SPLIT)
+#undef PME_CFG_SPLIT
     return configure_tc_kernel();
 }
 
@@ -189,7 +271,8 @@ void launch_stage(const SysDev &d0, int stage, cudaStream_t s) {
             else launch_tiles_spread<8>(d, s);
             break;
         case STAGE_FWD:
-            launch_pdl(fwd_kernel(d), d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d, STAGE_FWD);
+            if (!launch_split_slab(d, true, d.K1, s))
+                launch_pdl(fwd_kernel(d), d.K1, NT_SLAB, smem_slab(d.K2, d.K3), s, d, STAGE_FWD);
             break;
         case STAGE_CONV:
             if (d.tc_w) {
@@ -201,7 +284,8 @@ void launch_stage(const SysDev &d0, int stage, cudaStream_t s) {
             }
             break;
         case STAGE_INV:
-            launch_pdl(inv_kernel(d), d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d, STAGE_INV);
+            if (!launch_split_slab(d, false, d.K1, s))
+                launch_pdl(inv_kernel(d), d.K1, NT_SLAB, smem_inv(d.K2, d.K3), s, d, STAGE_INV);
             break;
         default:
             if (d.p == 4) launch_tiles_gather<4>(d, s);

@@ -12,12 +12,17 @@ namespace pme {
 
 constexpr int NT_BIN = 128;    // threads per CTA for binning (BIN_CHUNK atoms per CTA)
 constexpr int NT_SLAB = SLAB_THREADS;  // threads per CTA for the forward / inverse slab FFT stages
-constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interpolation (two per atom), at most
+constexpr int NT_TILE = 256;   // threads per CTA for spreading and force interpolation (two per atom), at most,
+constexpr int NT_TILE16 = 512; // with 8^3 / 16^3 tiles
+PME_HD int tile_nt_bound(int T) { return T >= 16 ? NT_TILE16 : NT_TILE; }
 // Spread / gather CTA size for a system whose binned atoms number about n_bins * BIN_CHUNK: two threads per
-// atom, sized to the mean tile occupancy, so sparse tiles (large meshes) do not leave half the CTA idle and
-// twice as many CTAs fit on an SM. Results do not depend on it.
+// atom, sized to the mean tile occupancy, so sparse 8^3 tiles (large meshes) do not leave half the CTA idle
+// and twice as many CTAs fit on an SM; 16^3 tiles (hundreds of atoms each) take 512. Results do not depend
+// on it.
 inline int tile_threads(const SysDev &d, int64_t n) {
-    if (d.nt_tile == 128 || d.nt_tile == NT_TILE) return d.nt_tile;  // chosen by the autotuner
+    if (d.nt_tile == 128 || d.nt_tile == NT_TILE || (d.nt_tile == NT_TILE16 && d.tlog >= 4))
+        return d.nt_tile;  // chosen by the autotuner or the caller
+    if (d.tlog >= 4) return NT_TILE16;
     return (d.ntiles > 0 && n <= (int64_t)64 * d.ntiles) ? 128 : NT_TILE;
 }
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
@@ -41,6 +46,13 @@ int launch_mode();
 // become resident during them (measured 30.6 vs 31.1 us per 64^3 evaluation); released early, the other
 // stages' successors were slower or no faster (their CTAs then land unevenly on the SMs).
 int pdl_when(int mode, int stage);
+
+// CTAs per slab of the single-system forward and inverse slab stages: 1, or 2 / 4 (a thread-block cluster
+// per slab exchanging its intermediate rows / columns through distributed shared memory; meshes with
+// K2 = K3 in {32, 64, 128} at 2, 64 at 4, others keep one CTA). Process-wide, default 1; affects launches
+// issued afterwards. Returns -1 for other values. Results are bitwise the same for every value.
+int set_slab_split(int fwd_ctas, int inv_ctas);
+int slab_split(int inverse);
 
 // Raise the dynamic shared-memory limit of the large-footprint kernels (once per device).
 cudaError_t configure_kernels();

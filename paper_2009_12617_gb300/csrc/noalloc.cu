@@ -276,7 +276,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     choose_fft_paths(d, false);
     const size_t K1 = K[0], K2 = K[1], K3 = K[2], H3 = d.H3, Nh = K3 / 2;
     const int64_t ncap = n > 0 ? n : 1;
-    const int cap = bucket_capacity(ncap, d.ntiles);
+    const int cap = bucket_capacity(ncap, d.ntiles, d.tlog);
     size_t off = 0;
     const size_t o_ctl = off;  off = al256(off + sizeof(Ctl));
     const size_t o_cnt = off;  off = al256(off + bcount_bytes(d.ntiles));

@@ -154,8 +154,8 @@ pme_status plan_reserve(pme_plan *pl, int64_t n) {
     const int64_t ncap = n > 0 ? n : 1;
     // tile edge from the atom density, or the one the autotuner / caller set (every tile counter is zero
     // between evaluations, so the tiling may change here; results do not depend on it)
-    set_tiling(d, pl->tile_log_set ? pl->tile_log_set : choose_tile_log(ncap, pl->K));
-    const int cap = bucket_capacity(ncap, d.ntiles);
+    set_tiling(d, pl->tile_log_set ? pl->tile_log_set : choose_tile_log(ncap, pl->K, pl->sms));
+    const int cap = bucket_capacity(ncap, d.ntiles, d.tlog);
     const size_t nb = (size_t)d.ntiles * cap;
     size_t off = 0;
     const size_t o_bka = off; off = align256(off + nb * 16);
@@ -338,6 +338,10 @@ pme_status pme_create(const int K[3], int p, double beta, const double box[9], v
     if ((e = ensure_configured(pl->dev)) != cudaSuccess) {
         delete pl;
         return cuda_fail(e, "configure kernels");
+    }
+    if ((e = cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, pl->dev)) != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
     }
     pl->stream = (cudaStream_t)cuda_stream;
     memcpy(pl->K, K, sizeof(pl->K));
@@ -627,6 +631,11 @@ int pme_get_influence_path(const pme_plan *pl) { return pl ? pl->influence_path 
 pme_status pme_set_launch_mode(int mode) {
     if (mode < 0 || mode > 3) return fail(PME_EINVAL, "launch mode must be 0, 1, 2 or 3");
     set_launch_mode(mode);
+    return PME_OK;
+}
+
+pme_status pme_set_slab_split(int fwd_ctas, int inv_ctas) {
+    if (set_slab_split(fwd_ctas, inv_ctas) != 0) return fail(PME_EINVAL, "slab split must be 1, 2 or 4 CTAs");
     return PME_OK;
 }
 

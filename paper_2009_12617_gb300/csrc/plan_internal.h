@@ -10,6 +10,7 @@
 
 struct pme_plan {
     int dev = 0;
+    int sms = 0;  // SMs of the device (tile edge choice)
     cudaStream_t stream = nullptr;
     int K[3] = {0, 0, 0};
     int p = 0;

@@ -49,6 +49,7 @@ struct SpreadLayout {
     static constexpr int R = T + P - 1;
     static constexpr int PL = spread_plane(R, P);
     static constexpr int VOLP = R * PL;
+    static constexpr int CAP = cap_max_for(T >= 16 ? 4 : 3);  // record slots
 };
 
 // ---------------------------------------------------------------------------------------------------------
@@ -59,11 +60,12 @@ inline size_t smem_tile_region(int p, int tlog) {
     const size_t r = (size_t)(1 << tlog) + p - 1;
     return r * r * r;
 }
-// split accumulators over the padded region (2 x R PL ints), the tile's records (CAP_MAX x (float4 + int2)),
-// the dealt order's keys and inverse (CAP_MAX ints each) and 16 residue counters
+// split accumulators over the padded region (2 x R PL ints), the tile's records (cap x (float4 + int2)),
+// the dealt order's keys and inverse (cap ints each) and 16 residue counters; cap = cap_max_for(tlog)
 inline size_t smem_spread(int p, int tlog) {
     const int r = (1 << tlog) + p - 1;
-    return (size_t)2 * r * spread_plane(r, p) * sizeof(int) + (size_t)CAP_MAX * (16 + 8 + 4 + 4) + 16 * sizeof(unsigned);
+    return (size_t)2 * r * spread_plane(r, p) * sizeof(int) + (size_t)cap_max_for(tlog) * (16 + 8 + 4 + 4) +
+           16 * sizeof(unsigned);
 }
 inline size_t smem_gather(int p, int tlog) { return smem_tile_region(p, tlog) * sizeof(float); }
 // Two K2 x H3 buffers (the register path uses one, with rows padded by up to 15), then the twiddles.
@@ -235,12 +237,13 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
 #pragma unroll
         for (int j2 = 0; j2 < P; ++j2) {
             const int k2 = wrapk(b2 - j2, d.K2);
-            const float c = ra.w * th1[j1] * th2[j2];
+            // the fixed-point scale (a power of two) applied to the row factor: rn(c 2^40 th3) = rn(c th3) 2^40
+            const float c = ra.w * th1[j1] * th2[j2] * FIX_SCALE;
             unsigned long long *row = d.grid + ((size_t)k1 * d.K2 + k2) * d.K3;
 #pragma unroll
             for (int j3 = 0; j3 < P; ++j3) {
                 // rn(v) directly in 64 bits: the same integer as the tile path's split, for any |q| < 2^22
-                red_add_u64(row + wrapk(b3 - j3, d.K3), (unsigned long long)f2ll_rn(c * th3[j3] * FIX_SCALE));
+                red_add_u64(row + wrapk(b3 - j3, d.K3), (unsigned long long)f2ll_rn(c * th3[j3]));
             }
         }
     }
@@ -261,10 +264,11 @@ struct SpreadSmem {
         hi = (int *)smem;
         lo = hi + VOLP;
         ra_s = (float4 *)(lo + VOLP);
-        rb_s = (int2 *)(ra_s + CAP_MAX);
-        key_s = (int *)(rb_s + CAP_MAX);
-        inv_s = key_s + CAP_MAX;
-        bins = (unsigned *)(inv_s + CAP_MAX);
+        constexpr int CAP = SpreadLayout<P, T>::CAP;
+        rb_s = (int2 *)(ra_s + CAP);
+        key_s = (int *)(rb_s + CAP);
+        inv_s = key_s + CAP;
+        bins = (unsigned *)(inv_s + CAP);
     }
 };
 
@@ -361,12 +365,14 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
             const float t1 = half ? th1[H0 + jj < P ? H0 + jj : P - 1] : th1[jj];
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
-                const float c = ra.w * t1 * th2[j2];
+                // scaled row factor: rn(c 2^40 th3) = rn(c th3) 2^40 (a power of two; |v| < 2^62, and values
+                // small enough for the scaling to matter round to 0 either way), one multiply per point
+                const float c = ra.w * t1 * th2[j2] * FIX_SCALE;
                 const int row = (l1 - j1) * PL + (l2 - j2) * R + l3;
 #pragma unroll
                 for (int j3 = 0; j3 < P; ++j3) {
                     int h, l;
-                    fix_split(c * th3[j3] * FIX_SCALE, h, l);
+                    fix_split(c * th3[j3], h, l);
                     atomic_add_i32(hi + row - j3, h);
                     atomic_add_i32(lo + row - j3, l);
                 }
@@ -743,6 +749,10 @@ PME_DEV void stage_inv_smem(const SysDev &d, int k1, void *smem) {
 }
 
 #if defined(PME_LANE_FFT)
+}  // namespace pme
+#include <cooperative_groups.h>
+namespace pme {
+namespace cg = cooperative_groups;
 // ---------------------------------------------------------------------------------------------------------
 // Register path of a3 - a5 (lane plans, fft.cuh): each transform runs in the registers of L lanes of one
 // warp, reading its points straight from global memory (or from the slab buffer in shared memory) and
@@ -767,16 +777,29 @@ PME_DEV int lane_units(int ntr) {
     return ((ntr + T - 1) / T) * 32;
 }
 
+// Where a slab pass stores its intermediate results: the CTA's own slab buffer and, when a slab is split
+// over a cluster of NB CTAs, the same offset in the other CTAs' buffers (distributed shared memory), so that
+// every CTA of the cluster holds the whole intermediate slab for the second pass.
+template <int NB>
+struct SlabDst {
+    float2 *buf[NB];
+    PME_DEV void put(int i, float2 v) const {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) buf[c][i] = v;
+    }
+};
+
 // a3 rows: the packed real row k2 (z[n] = Q[2n] + i Q[2n+1], K3/2 = L E points) from the int64 mesh; the
-// K3/2-point transform goes to row k2 of Z (row stride zs).
-template <int L, int E>
-PME_DEV void fwd_rows_lane(const SysDev &d, int k1, float2 *Z, int zs) {
-    const int K2 = d.K2, total = lane_units<L>(K2);
+// K3/2-point transform goes to row k2 of Z (row stride zs). Rows [t0, t0 + nt).
+template <int L, int E, int NB>
+PME_DEV void fwd_rows_lane(const SysDev &d, int k1, const SlabDst<NB> &Z, int zs, int t0, int nt) {
+    const int K2 = d.K2, total = lane_units<L>(nt);
     for (int u = PME_TID; u < total; u += PME_NTH) {
         int t, j;
         lane_unit<L>(u, t, j);
-        const bool ok = t < K2;
-        const ulonglong2 *g = (const ulonglong2 *)(d.grid + ((size_t)k1 * K2 + (ok ? t : 0)) * d.K3);
+        const bool ok = t < nt;
+        t += t0;
+        const ulonglong2 *g = (const ulonglong2 *)(d.grid + ((size_t)k1 * K2 + (ok ? t : t0)) * d.K3);
         ulonglong2 w[E];
 #pragma unroll
         for (int n = 0; n < E; ++n) w[n] = ldcg(g + j + L * n);
@@ -788,23 +811,25 @@ PME_DEV void fwd_rows_lane(const SysDev &d, int k1, float2 *Z, int zs) {
         if (ok) {
             const int r = lane_rev<L>(j);
 #pragma unroll
-            for (int k = 0; k < E; ++k) Z[t * zs + k + E * r] = v[k];
+            for (int k = 0; k < E; ++k) Z.put(t * zs + k + E * r, v[k]);
         }
     }
 }
 
 // a3 columns: the split X[m] = E[m] + W_K3^m O[m] of row transforms Z (E, O as in the shared-memory path)
 // fused into the loads of column m3, then the K2-point transform along k2 into the half spectrum. tw3
-// (K3/2 + 1 entries) and tw2 (K2 entries) are shared-memory copies.
+// (K3/2 + 1 entries) and tw2 (K2 entries) are shared-memory copies. Columns [m0, m0 + nm).
 template <int L, int E>
-PME_DEV void fwd_cols_lane(const SysDev &d, int k1, const float2 *Z, int zs, const float2 *tw3, const float2 *tw2) {
-    const int K2 = d.K2, H3 = d.H3, Nh = d.K3 / 2, total = lane_units<L>(H3);
+PME_DEV void fwd_cols_lane(const SysDev &d, int k1, const float2 *Z, int zs, const float2 *tw3, const float2 *tw2,
+                           int m0, int nm) {
+    const int K2 = d.K2, H3 = d.H3, Nh = d.K3 / 2, total = lane_units<L>(nm);
     float2 *out = d.spec + (size_t)k1 * K2 * H3;
     for (int u = PME_TID; u < total; u += PME_NTH) {
         int m, j;
         lane_unit<L>(u, m, j);
-        const bool ok = m < H3;
-        const int mm = ok ? m : 0;
+        const bool ok = m < nm;
+        m += m0;
+        const int mm = ok ? m : m0;
         const LaneTw<L, E> tw = lane_tw<L, E, false>(tw2, j);
         const float2 w3 = tw3[mm];
         const int ia = mm == Nh ? 0 : mm, ib = mm == 0 ? 0 : Nh - mm;
@@ -826,16 +851,18 @@ PME_DEV void fwd_cols_lane(const SysDev &d, int k1, const float2 *Z, int zs, con
     }
 }
 
-// a5 columns: inverse K2-point transforms of column m3 of the half spectrum into Y (row stride ys).
-template <int L, int E>
-PME_DEV void inv_cols_lane(const SysDev &d, int k1, float2 *Y, int ys) {
-    const int K2 = d.K2, H3 = d.H3, total = lane_units<L>(H3);
+// a5 columns: inverse K2-point transforms of column m3 of the half spectrum into Y (row stride ys). Columns
+// [m0, m0 + nm).
+template <int L, int E, int NB>
+PME_DEV void inv_cols_lane(const SysDev &d, int k1, const SlabDst<NB> &Y, int ys, int m0, int nm) {
+    const int K2 = d.K2, H3 = d.H3, total = lane_units<L>(nm);
     const float2 *in = d.spec + (size_t)k1 * K2 * H3;
     for (int u = PME_TID; u < total; u += PME_NTH) {
         int m, j;
         lane_unit<L>(u, m, j);
-        const bool ok = m < H3;
-        const int mm = ok ? m : 0;
+        const bool ok = m < nm;
+        m += m0;
+        const int mm = ok ? m : m0;
         float2 v[E];
 #pragma unroll
         for (int n = 0; n < E; ++n) v[n] = ldcg(in + (size_t)(j + L * n) * H3 + mm);
@@ -844,23 +871,25 @@ PME_DEV void inv_cols_lane(const SysDev &d, int k1, float2 *Y, int ys) {
         if (ok) {
             const int r = lane_rev<L>(j);
 #pragma unroll
-            for (int k = 0; k < E; ++k) Y[(k + E * r) * ys + m] = v[k];
+            for (int k = 0; k < E; ++k) Y.put((k + E * r) * ys + m, v[k]);
         }
     }
 }
 
 // a5 rows: the merge Z[m] = (X[m] + conj X[Nh-m]) + i (X[m] - conj X[Nh-m]) exp(+2 pi i m / K3) fused into
 // the loads, then the inverse K3/2-point transform, whose real / imaginary parts are phi at even / odd k3.
-// twh (K3/2 entries) and tw3 (K3/2 + 1) are shared-memory copies.
+// twh (K3/2 entries) and tw3 (K3/2 + 1) are shared-memory copies. Rows [t0, t0 + nt).
 template <int L, int E>
-PME_DEV void inv_rows_lane(const SysDev &d, int k1, const float2 *Y, int ys, const float2 *twh, const float2 *tw3) {
-    const int K2 = d.K2, Nh = d.K3 / 2, total = lane_units<L>(K2);
+PME_DEV void inv_rows_lane(const SysDev &d, int k1, const float2 *Y, int ys, const float2 *twh, const float2 *tw3,
+                           int t0, int nt) {
+    const int K2 = d.K2, Nh = d.K3 / 2, total = lane_units<L>(nt);
     float2 *out = (float2 *)(d.phi + (size_t)k1 * K2 * d.K3);
     for (int u = PME_TID; u < total; u += PME_NTH) {
         int t, j;
         lane_unit<L>(u, t, j);
-        const bool ok = t < K2;
-        const float2 *x = Y + (ok ? t : 0) * ys;
+        const bool ok = t < nt;
+        t += t0;
+        const float2 *x = Y + (ok ? t : t0) * ys;
         const LaneTw<L, E> tw = lane_tw<L, E, false>(twh, j);
         float2 v[E];
 #pragma unroll
@@ -988,12 +1017,13 @@ PME_DEV void stage_fwd_lane(const SysDev &d, int k1, void *smem) {
     const int tid = PME_TID;
     const float2 a = tid <= Nh ? __ldg(d.tw3 + tid) : make_float2(0.f, 0.f);
     const float2 b = tid < d.K2 ? __ldg(d.tw2 + tid) : make_float2(0.f, 0.f);
+    const SlabDst<1> Zd = {{Z}};
     if constexpr (PR >= 0) {
-        fwd_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Z, zs);
+        fwd_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Zd, zs, 0, d.K2);
     } else {
         switch (d.lp_rows) {
 #define PME_ROWS(c, L, E) \
-    case c: fwd_rows_lane<L, E>(d, k1, Z, zs); break;
+    case c: fwd_rows_lane<L, E>(d, k1, Zd, zs, 0, d.K2); break;
             PME_LANE_CASES(PME_ROWS)
 #undef PME_ROWS
         }
@@ -1004,11 +1034,11 @@ PME_DEV void stage_fwd_lane(const SysDev &d, int k1, void *smem) {
     for (int i = tid + PME_NTH; i < d.K2; i += PME_NTH) tw2[i] = d.tw2[i];
     PME_SYNC();
     if constexpr (PC >= 0) {
-        fwd_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Z, zs, tw3, tw2);
+        fwd_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Z, zs, tw3, tw2, 0, d.H3);
     } else {
         switch (d.lp_cols) {
 #define PME_COLS(c, L, E) \
-    case c: fwd_cols_lane<L, E>(d, k1, Z, zs, tw3, tw2); break;
+    case c: fwd_cols_lane<L, E>(d, k1, Z, zs, tw3, tw2, 0, d.H3); break;
             PME_LANE_CASES(PME_COLS)
 #undef PME_COLS
         }
@@ -1029,12 +1059,13 @@ PME_DEV void stage_inv_lane(const SysDev &d, int k1, void *smem) {
     const int cu = plan_col_units(d.lp_cols, d.H3);
     if (PME_NTH - cu >= 32) inv_side_work(d, k1, cu, PME_NTH - cu);
     else inv_side_work(d, k1, 0, PME_NTH);
+    const SlabDst<1> Yd = {{Y}};
     if constexpr (PC >= 0) {
-        inv_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Y, ys);
+        inv_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Yd, ys, 0, d.H3);
     } else {
         switch (d.lp_cols) {
 #define PME_COLS(c, L, E) \
-    case c: inv_cols_lane<L, E>(d, k1, Y, ys); break;
+    case c: inv_cols_lane<L, E>(d, k1, Yd, ys, 0, d.H3); break;
             PME_LANE_CASES(PME_COLS)
 #undef PME_COLS
         }
@@ -1045,15 +1076,91 @@ PME_DEV void stage_inv_lane(const SysDev &d, int k1, void *smem) {
     for (int i = tid + PME_NTH; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
     PME_SYNC();
     if constexpr (PR >= 0) {
-        inv_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Y, ys, twh, tw3);
+        inv_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Y, ys, twh, tw3, 0, d.K2);
     } else {
         switch (d.lp_rows) {
 #define PME_ROWS(c, L, E) \
-    case c: inv_rows_lane<L, E>(d, k1, Y, ys, twh, tw3); break;
+    case c: inv_rows_lane<L, E>(d, k1, Y, ys, twh, tw3, 0, d.K2); break;
             PME_LANE_CASES(PME_ROWS)
 #undef PME_ROWS
         }
     }
+}
+
+// Slab k1 split over a cluster of CS CTAs (rank c of the cluster), plans PR / PC at compile time: each
+// CTA transforms rows [c K2 / CS, (c + 1) K2 / CS) and stores them into every CTA's slab buffer (distributed
+// shared memory), the cluster barrier makes them visible, then each CTA transforms its share of the
+// columns. With the plans of the one-CTA kernel these are the same transforms and stores as
+// stage_fwd_lane, so the results are bitwise the same; a slab takes CS SMs instead of one.
+PME_DEV void split_range(int n, int c, int cs, int &a, int &cnt) {
+    const int per = (n + cs - 1) / cs;
+    a = imin(n, c * per);
+    cnt = imin(n, a + per) - a;
+}
+
+template <int PR, int PC, int CS>
+PME_DEV void stage_fwd_cluster(const SysDev &d, int k1, int c, void *smem) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int Nh = d.K3 / 2, zs = stride_col_reader(Nh, PC);
+    float2 *Z = (float2 *)smem;
+    float2 *tw3 = Z + d.K2 * zs;
+    float2 *tw2 = tw3 + Nh + 1;
+    const int tid = PME_TID;
+    const float2 a = tid <= Nh ? __ldg(d.tw3 + tid) : make_float2(0.f, 0.f);
+    const float2 b = tid < d.K2 ? __ldg(d.tw2 + tid) : make_float2(0.f, 0.f);
+    if (k1 == 0 && c == 0 && tid == 0) d.ctl->novf = 0u;  // spreading (its last reader) has finished
+    SlabDst<CS> Zd;
+#pragma unroll
+    for (int q = 0; q < CS; ++q) Zd.buf[q] = cl.map_shared_rank(Z, (unsigned)((c + q) % CS));
+    int t0, nt, m0, nm;
+    split_range(d.K2, c, CS, t0, nt);
+    split_range(d.H3, c, CS, m0, nm);
+    fwd_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E, CS>(d, k1, Zd, zs, t0, nt);
+    if (tid <= Nh) tw3[tid] = a;
+    if (tid < d.K2) tw2[tid] = b;
+    for (int i = tid + PME_NTH; i <= Nh; i += PME_NTH) tw3[i] = d.tw3[i];
+    for (int i = tid + PME_NTH; i < d.K2; i += PME_NTH) tw2[i] = d.tw2[i];
+    cl.sync();  // every row of Z, from every CTA of the cluster; no remote access after this point
+    fwd_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E>(d, k1, Z, zs, tw3, tw2, m0, nm);
+}
+
+// Inverse slab k1 split the same way: columns first (stored into every CTA's buffer), the cluster barrier,
+// then each CTA's rows. The side work (zeroing the mesh plane, the level-1 energy reduction) is divided
+// among the CTAs and runs on the warps the column pass leaves free (else before it).
+template <int PR, int PC, int CS>
+PME_DEV void stage_inv_cluster(const SysDev &d, int k1, int c, void *smem) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int Nh = d.K3 / 2, ys = stride_row_reader(d.H3, PR);
+    float2 *Y = (float2 *)smem;
+    float2 *twh = Y + d.K2 * ys;
+    float2 *tw3 = twh + Nh;
+    const int tid = PME_TID, nth = PME_NTH;
+    const float2 a = tid < Nh ? __ldg(d.tw3h + tid) : make_float2(0.f, 0.f);
+    const float2 b = tid <= Nh ? __ldg(d.tw3 + tid) : make_float2(0.f, 0.f);
+    int t0, nt, m0, nm;
+    split_range(d.K2, c, CS, t0, nt);
+    split_range(d.H3, c, CS, m0, nm);
+    {
+        const int cu = lane_units<PlanLE<PC>::L>(nm);
+        const int s0 = nth - cu >= 32 ? cu : 0, ns = nth - s0, st = tid - s0;
+        if (st >= 0) {
+            if (c == 0) reduce_level1(d, k1, st, ns);
+            ulonglong2 *g = (ulonglong2 *)(d.grid + (size_t)k1 * d.K2 * d.K3);
+            int z0, nz;
+            split_range(d.K2 * d.K3 / 2, c, CS, z0, nz);
+            for (int i = st; i < nz; i += ns) g[z0 + i] = make_ulonglong2(0ull, 0ull);
+        }
+    }
+    SlabDst<CS> Yd;
+#pragma unroll
+    for (int q = 0; q < CS; ++q) Yd.buf[q] = cl.map_shared_rank(Y, (unsigned)((c + q) % CS));
+    inv_cols_lane<PlanLE<PC>::L, PlanLE<PC>::E, CS>(d, k1, Yd, ys, m0, nm);
+    if (tid < Nh) twh[tid] = a;
+    if (tid <= Nh) tw3[tid] = b;
+    for (int i = tid + nth; i < Nh; i += nth) twh[i] = d.tw3h[i];
+    for (int i = tid + nth; i <= Nh; i += nth) tw3[i] = d.tw3[i];
+    cl.sync();  // every column of Y, from every CTA of the cluster; no remote access after this point
+    inv_rows_lane<PlanLE<PR>::L, PlanLE<PR>::E>(d, k1, Y, ys, twh, tw3, t0, nt);
 }
 
 template <int P1>
@@ -1153,6 +1260,7 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
         for (int jj = 0; jj < (half ? P - H0 : H0); ++jj) {
             const int j1 = half * H0 + jj;
             const int k1 = wrapk(b1 - j1, d.K1);
+            float a = 0.f, b = 0.f, c = 0.f;  // plane sums, as in the tile path
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
                 const int k2 = wrapk(b2 - j2, d.K2);
@@ -1164,10 +1272,13 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
                     s = fmaf(th3[j3], ph, s);
                     ds = fmaf(dth3[j3], ph, ds);
                 }
-                g1 = fmaf(dth1[j1] * th2[j2], s, g1);
-                g2 = fmaf(th1[j1] * dth2[j2], s, g2);
-                g3 = fmaf(th1[j1] * th2[j2], ds, g3);
+                a = fmaf(th2[j2], s, a);
+                b = fmaf(dth2[j2], s, b);
+                c = fmaf(th2[j2], ds, c);
             }
+            g1 = fmaf(dth1[j1], a, g1);
+            g2 = fmaf(th1[j1], b, g2);
+            g3 = fmaf(th1[j1], c, g3);
         }
         gh[half][0] = g1;
         gh[half][1] = g2;
@@ -1261,6 +1372,9 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
                 const int jh = H0 + jj < P ? H0 + jj : P - 1;
                 const float t1 = half ? th1[jh] : th1[jj];
                 const float dt1 = half ? dth1[jh] : dth1[jj];
+                // per plane: a = sum_j2 th2 S, b = sum_j2 dth2 S, c = sum_j2 th2 dS over the rows' sums
+                // S = sum_j3 th3 phi, dS = sum_j3 dth3 phi; then the plane's weight (one multiply-add each)
+                float a = 0.f, b = 0.f, c = 0.f;
 #pragma unroll
                 for (int j2 = 0; j2 < P; ++j2) {
                     const float *row = reg + ((l1 - j1) * R + (l2 - j2)) * R + l3;
@@ -1271,10 +1385,13 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
                         s = fmaf(th3[j3], ph, s);
                         ds = fmaf(dth3[j3], ph, ds);
                     }
-                    g1 = fmaf(dt1 * th2[j2], s, g1);
-                    g2 = fmaf(t1 * dth2[j2], s, g2);
-                    g3 = fmaf(t1 * th2[j2], ds, g3);
+                    a = fmaf(th2[j2], s, a);
+                    b = fmaf(dth2[j2], s, b);
+                    c = fmaf(th2[j2], ds, c);
                 }
+                g1 = fmaf(dt1, a, g1);
+                g2 = fmaf(t1, b, g2);
+                g3 = fmaf(t1, c, g3);
             }
 #if defined(PME_HOST_EMULATION)
             if (!half) {

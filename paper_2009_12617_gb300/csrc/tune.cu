@@ -110,7 +110,8 @@ static void load_cache_locked() {
             t.tile_edge = (int)te;
             t.tile_threads = (int)tt;
             t.us = us;
-            if ((t.tile_edge == 8 || t.tile_edge == 16) && (t.tile_threads == 128 || t.tile_threads == 256))
+            if ((t.tile_edge == 8 || t.tile_edge == 16) &&
+                (t.tile_threads == 128 || t.tile_threads == 256 || (t.tile_threads == 512 && t.tile_edge == 16)))
                 g_entries.push_back(t);
         }
         s = e + 1;
@@ -258,8 +259,8 @@ pme_status pme_tune_cache(const char *path) {
 pme_status pme_plan_set_tiling(pme_plan *pl, int tile_edge, int tile_threads) {
     if (!pl) return fail(PME_EINVAL, "plan is NULL");
     if (tile_edge != 0 && tile_edge != 8 && tile_edge != 16) return fail(PME_EINVAL, "tile_edge must be 0, 8 or 16");
-    if (tile_threads != 0 && tile_threads != 128 && tile_threads != 256)
-        return fail(PME_EINVAL, "tile_threads must be 0, 128 or 256");
+    if (tile_threads != 0 && tile_threads != 128 && tile_threads != 256 && !(tile_threads == 512 && tile_edge == 16))
+        return fail(PME_EINVAL, "tile_threads must be 0, 128 or 256 (or 512 with tile_edge 16)");
     DeviceGuard g(pl->dev);
     const int tlog = tile_edge == 16 ? 4 : (tile_edge == 8 ? 3 : 0);
     return plan_retile(pl, tlog, tile_threads, pl->n_cap);
@@ -289,13 +290,13 @@ pme_status pme_autotune(pme_plan *pl, const float *pos, const float *q, int64_t 
         return PME_OK;
     }
     // candidates: the default first (its results are the reference bits), then every other combination
-    const int tdef = pl->tile_log_set ? pl->tile_log_set : choose_tile_log(n > 0 ? n : 1, pl->K);
+    const int tdef = pl->tile_log_set ? pl->tile_log_set : choose_tile_log(n > 0 ? n : 1, pl->K, pl->sms);
     if ((st = plan_retile(pl, tdef, 0, n)) != PME_OK) return st;
     const int ntdef = tile_threads(pl->d, n);
     struct Cand { int tlog, nt; double us; bool same; };
     std::vector<Cand> cands = {{tdef, ntdef, 0.0, true}};
     for (int tlog : {3, 4})
-        for (int nt : {128, 256})
+        for (int nt : {tlog == 3 ? 128 : NT_TILE, tlog == 3 ? NT_TILE : NT_TILE16})
             if (!(tlog == tdef && nt == ntdef)) cands.push_back({tlog, nt, 0.0, false});
     std::vector<float> F0((size_t)(n > 0 ? n : 1) * 3), F1(F0.size());
     double ev0[7], ev1[7];

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "PME_OK", 1: "PME_EINVAL", 2: "PME_EUNSUPPORTED", 3: "PME_ENO
 
 # every symbol include/pme.h declares
 EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme_enqueue", "pme_reserve", "pme_sync", "pme_compute_host",
-           "pme_profile_stages", "pme_set_launch_mode", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
+           "pme_profile_stages", "pme_set_launch_mode", "pme_set_slab_split", "pme_plan_device_bytes", "pme_destroy", "pme_batch_create", "pme_batch_enqueue", "pme_batch_sync",
            "pme_batch_destroy", "pme_server_create", "pme_submit", "pme_poll", "pme_server_stats",
            "pme_server_destroy", "pme_strerror", "pme_last_error_detail", "pme_batch_debug_stall",
            "pme_compute_noalloc", "pme_batch_set_strategy", "pme_batch_get_strategy",
@@ -136,6 +136,7 @@ def load_library(path: str | None = None):
         "pme_enqueue_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
         "pme_profile_stages": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pme_set_launch_mode": (_st, [ctypes.c_int]),
+        "pme_set_slab_split": (_st, [ctypes.c_int, ctypes.c_int]),
         "pme_plan_device_bytes": (ctypes.c_size_t, [_vp]),
         "pme_destroy": (None, [_vp]),
         "pme_batch_create": (_st, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp, ctypes.POINTER(_vp)]),
@@ -322,6 +323,12 @@ def pme_set_launch_mode(mode: int) -> None:
     """0 plain; programmatic dependent launch triggered 1 at kernel entry, 2 (default) at CTA exit (the influence
     stage: right after its own wait), 3 right after each kernel's own wait."""
     check(load_library().pme_set_launch_mode(int(mode)))
+
+
+def pme_set_slab_split(fwd_ctas: int, inv_ctas: int | None = None) -> None:
+    """CTAs (a thread-block cluster) per slab of the forward and the inverse slab stage: 1, 2 or 4 each
+    (inv_ctas defaults to fwd_ctas)."""
+    check(load_library().pme_set_slab_split(int(fwd_ctas), int(fwd_ctas if inv_ctas is None else inv_ctas)))
 
 
 def pme_plan_device_bytes(plan: int) -> int:

@@ -80,10 +80,10 @@ static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta,
     make_twiddles(K[1], K[1], s.tw.data() + K1);
     make_twiddles((int)Nh, (int)Nh, s.tw.data() + K1 + K2);
     make_twiddles(K[2], (int)Nh + 1, s.tw.data() + K1 + K2 + Nh);
-    set_tiling(d, tile_log > 0 ? tile_log : choose_tile_log(n > 0 ? n : 1, K));
+    set_tiling(d, tile_log > 0 ? tile_log : choose_tile_log(n > 0 ? n : 1, K, 0));
     s.bcount.assign(bcount_bytes(d.ntiles) / sizeof(unsigned), 0u);
     s.partials.assign(partials_bytes(d) / sizeof(double), 0.0);
-    const int cap = cap_override > 0 ? cap_override : bucket_capacity(n > 0 ? n : 1, d.ntiles);
+    const int cap = cap_override > 0 ? cap_override : bucket_capacity(n > 0 ? n : 1, d.ntiles, d.tlog);
     s.bka.resize((size_t)d.ntiles * cap);
     s.bkb.resize((size_t)d.ntiles * cap);
     s.ova.resize(n > 0 ? n : 1);

@@ -123,6 +123,46 @@ def test_parity_full_size_large(pmelib, oracle_mod):
         pmelib.pme_destroy(plan)
 
 
+SPLIT_CASES = [("parity", (1, 2)), ("headline", (1, 2, 4)), ("large", (1, 2))]
+
+
+@pytest.mark.parametrize("name,splits", SPLIT_CASES, ids=[c[0] for c in SPLIT_CASES])
+def test_slab_split_bit_identical(pmelib, name, splits):
+    """The slab stages split over clusters of 2 or 4 CTAs (distributed shared memory) give the one-CTA
+    results bit for bit: forces, energy, virial and the potential mesh (32^3, 64^3 p=4, 128^3 p=6); a
+    forward / inverse mix too."""
+    s = {"parity": wl.parity_system, "headline": wl.headline_system, "large": wl.large_system}[name]()
+    out = []
+    try:
+        for cs in splits:
+            pmelib.pme_set_slab_split(cs)
+            plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+            try:
+                out.append(gpu_eval(pmelib, plan, s.pos, s.q, s.K, taps=True))
+            finally:
+                pmelib.pme_destroy(plan)
+    finally:
+        pmelib.pme_set_slab_split(1)
+    for o in out[1:]:
+        assert o["energy"] == out[0]["energy"]
+        assert np.array_equal(o["virial"], out[0]["virial"])
+        assert np.array_equal(o["forces"], out[0]["forces"])
+        assert np.array_equal(o["phi"], out[0]["phi"])
+        assert np.array_equal(o["mesh"], out[0]["mesh"])
+    pmelib.pme_set_slab_split(2, 1)
+    try:
+        plan = pmelib.pme_create(s.K, s.p, s.beta, s.box)
+        try:
+            o = gpu_eval(pmelib, plan, s.pos, s.q, s.K)
+        finally:
+            pmelib.pme_destroy(plan)
+    finally:
+        pmelib.pme_set_slab_split(1)
+    assert o["energy"] == out[0]["energy"] and np.array_equal(o["forces"], out[0]["forces"])
+    with pytest.raises(Exception):
+        pmelib.pme_set_slab_split(3)
+
+
 def test_mesh_bit_exact_repeat_and_permutation(pmelib):
     """The int64 charge mesh is bit-identical over repeated runs and any input order; so is everything
     downstream (no floating-point atomics anywhere)."""

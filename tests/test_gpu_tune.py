@@ -43,8 +43,8 @@ def _noncubic():
 
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_every_tiling_candidate_is_bit_identical(pme, oracle_mod, name):
-    """Tile edges 8 and 16, CTA sizes 128 and 256: energy, virial and forces equal the default's bit for bit;
-    the default matches the oracle."""
+    """Tile edges 8 and 16, CTA sizes 128 and 256 (and 512 with 16^3 tiles): energy, virial and forces equal
+    the default's bit for bit; the default matches the oracle."""
     s = SYSTEMS[name]()
     P, Q = _dev(s)
     plan = pme.pme_create(s.K, s.p, s.beta, s.box)
@@ -52,7 +52,7 @@ def test_every_tiling_candidate_is_bit_identical(pme, oracle_mod, name):
         F0 = torch.empty_like(P)
         E0, V0 = pme.pme_compute(plan, P, Q, F0)
         for edge in (8, 16):
-            for nt in (128, 256):
+            for nt in ((128, 256) if edge == 8 else (128, 256, 512)):
                 pme.pme_plan_set_tiling(plan, edge, nt)
                 assert pme.pme_plan_get_tiling(plan) == (edge, nt)
                 F = torch.full_like(P, float("nan"))
@@ -80,7 +80,7 @@ def test_autotune_picks_and_persists(pme, tmp_path):
             F = torch.empty_like(P)
             res = pme.pme_autotune(plan, P, Q, F, reps=20)
             assert res["candidates"] == 4 and res["rejected"] == 0 and res["from_cache"] == 0
-            assert res["tile_edge"] in (8, 16) and res["tile_threads"] in (128, 256)
+            assert (res["tile_edge"], res["tile_threads"]) in ((8, 128), (8, 256), (16, 256), (16, 512))
             assert 0 < res["us_per_eval"] <= res["default_us"]
             assert pme.pme_plan_get_tiling(plan) == (res["tile_edge"], res["tile_threads"])
             E, V = pme.pme_compute(plan, P, Q, F)
