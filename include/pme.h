@@ -138,13 +138,17 @@ pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, in
 
 /* Paper: Sec. III (many timesteps without host round trips) with the host application of Fig. "MDOverview":
  * the asynchronous form of pme_compute_host. pos, q, forces (n x 3) and result (8 doubles) must all be
- * page-locked host memory (cudaHostAlloc / cudaHostRegister), else PME_EINVAL. Enqueues the evaluation on
- * the plan stream and returns: the binning kernel reads positions and charges in host memory, and one copy
- * kernel writes the forces and result[0..6] = (energy, virial[6]) and result[7] = the device status bits
- * (0: no error) into host memory when the stream gets there. Each call may use its own arrays, so a caller
- * can keep several evaluations in flight (double buffering) and wait on the plan stream for the oldest. The
- * first call with an argument set records the evaluation as a CUDA graph; the four most recent sets are kept
- * and replayed. The arrays must stay allocated and unchanged until the evaluation has completed. */
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister), else PME_EINVAL. Enqueues the evaluation and
+ * returns: positions and charges are copied by the copy engine, on a stream of the plan's own, into one of
+ * two device input slots (alternating per call) as soon as the evaluation that last used that slot has
+ * finished, so the copy overlaps the evaluation still running on the plan stream; the plan stream waits
+ * for the copy, runs the evaluation, and one copy kernel writes the forces and result[0..6] = (energy,
+ * virial[6]) and result[7] = the device status bits (0: no error) into host memory. Each call may use its
+ * own arrays, so a caller can keep several evaluations in flight (double buffering) and wait on the plan
+ * stream for the oldest. All four arrays must stay allocated and unchanged until the plan stream has
+ * completed the evaluation. The evaluation and copy
+ * kernel of each argument set are recorded once as a CUDA graph (the four most recent sets are kept). Not
+ * callable while the plan stream is being captured into a graph. */
 pme_status pme_enqueue_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
                             double *result);
 

@@ -458,6 +458,7 @@ static pme_status batch_refresh(pme_batch *b) {
         pme_plan *pl = b->plans[s];
         if ((st = plan_reserve(pl, b->n[s])) != PME_OK) return st;
         b->sys[s] = plan_descriptor(pl, nullptr, nullptr, b->n[s], nullptr, nullptr);
+        if (b->plans.size() > 1) shared_tiling(b->sys[s]);
         b->plan_gen[s] = pl->gen;
     }
     build_work_list(b->sys, b->entries, b->count);
@@ -542,6 +543,7 @@ pme_status pme_batch_create(int nsys, pme_plan *const *plans, const int64_t *n, 
         b->n.push_back(n[s]);
         b->off.push_back(off);
         b->sys.push_back(plan_descriptor(pl, nullptr, nullptr, n[s], nullptr, nullptr));
+        if (nsys > 1) shared_tiling(b->sys.back());
         b->plan_gen.push_back(pl->gen);
         off += n[s];
     }

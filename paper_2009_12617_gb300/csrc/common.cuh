@@ -138,7 +138,8 @@ struct SysDev {
     int K1, K2, K3, H3;          // mesh; H3 = K3/2 + 1 (half spectrum along k3)
     int p;                       // B-spline order
     int tlog;                    // tile edge 2^tlog mesh points
-    int nt1, nt2, nt3, ntiles;   // spread / gather tiles per dimension
+    int nt1, nt2, nt3, ntiles;   // spread / gather tiles per dimension (nt1: pieces of the k1 axis)
+    float rnt1;                  // 1 / nt1
     int cap;                     // bucket capacity (atoms per tile)
     int n;                       // atoms
     int nbin;                    // binning work items = ceil(n / BIN_CHUNK)
@@ -220,6 +221,12 @@ PME_DEV int imin(int a, int b) { return a < b ? a : b; }
 // floor(a / b) for 0 <= a < 2^20 and 1 <= b <= 2^12 from a precomputed float reciprocal: (a + 0.5) / b is
 // at least 1/(2b) away from an integer, far more than the float rounding, so the truncation is exact.
 PME_DEV int fdiv(int a, float binv) { return (int)(((float)a + 0.5f) * binv); }
+
+// Pieces of the k1 axis for the spread / force tiles (set_tiling): piece j covers [floor(j K1 / nt1),
+// floor((j + 1) K1 / nt1)); the piece holding k is floor(((k + 1) nt1 - 1) / K1). Both divisions are exact
+// by fdiv (numerators below 2^16, divisors at most 256).
+PME_DEV int k1_piece(const SysDev &d, int k) { return fdiv((k + 1) * d.nt1 - 1, d.kinv[0]); }
+PME_DEV int k1_start(const SysDev &d, int j) { return fdiv(j * d.K1, d.rnt1); }
 
 #if defined(PME_HOST_EMULATION)
 inline unsigned long long warp_sum_u64(unsigned long long v) { return v; }

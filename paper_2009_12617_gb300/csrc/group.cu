@@ -189,7 +189,7 @@ cudaError_t launch_group_chain(const SysDev *sys_dev, int nsys, const SysDev &pr
             case STAGE_CONV: e = launch_ex(conv_g(d), grid, NT_CONV, smem_conv(d.K1, NT_CONV), s, a); break;
             case STAGE_INV: e = launch_ex(inv_g(d), grid, NT_SLAB, smem_inv(d.K2, d.K3), s, a); break;
             default:
-                e = launch_ex(gather_g(d), grid, (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK),
+                e = launch_ex(gather_g(d), grid, (unsigned)tile_threads(d, (int64_t)max_nbin * BIN_CHUNK, true),
                               smem_gather_all(d.p, d.tlog), s, a);
                 break;
         }

@@ -69,14 +69,47 @@ inline bool cell_reciprocal(const double box[9], double recip[9], double *vol) {
     return true;
 }
 
-// Tile edge 2^tlog: tiles per dimension (the last one ragged) and their count. Needs d.K1..K3.
-inline void set_tiling(SysDev &d, int tlog) {
+// Tile edge 2^tlog: tiles per dimension and their count. Needs d.K1..K3. Along k2 and k3 the tiles are
+// 2^tlog wide (the last one ragged); along k1 the mesh is cut into np1 >= ceil(K1 / 2^tlog) pieces, piece j
+// starting at floor(j K1 / np1) (k1_piece / k1_start), so every piece is at most 2^tlog wide (np1 = 0: the
+// fewest pieces, which for K1 a multiple of the edge are the plain 2^tlog slabs).
+inline void set_tiling(SysDev &d, int tlog, int np1 = 0) {
     const int T = 1 << tlog;
+    const int base = (d.K1 + T - 1) / T;
     d.tlog = tlog;
-    d.nt1 = (d.K1 + T - 1) / T;
+    d.nt1 = np1 > base ? np1 : base;
+    d.rnt1 = 1.0f / (float)d.nt1;
     d.nt2 = (d.K2 + T - 1) / T;
     d.nt3 = (d.K3 + T - 1) / T;
     d.ntiles = d.nt1 * d.nt2 * d.nt3;
+}
+
+// Descriptor of a system that shares the GPU with others (batches, server waves of several systems): the
+// fewest k1 pieces, since balancing one system's tiles over the SMs is moot there and thinner pieces only add
+// halo. Uses the plan's buckets as they are (fewer tiles of at most the same capacity).
+inline void shared_tiling(SysDev &d) { set_tiling(d, d.tlog, 0); }
+
+// Pieces along k1 for one system on `sms` SMs. When a single system has more tiles than SMs, all of them
+// are resident at once and the SMs holding one tile more than the others set the stage time (at 64^3:
+// 512 tiles on 152 SMs, 64 SMs with four and 88 with three). Cutting k1 into a few more, thinner pieces can
+// lower the busiest SM's work, ceil(tiles / SMs) x (atoms + halo share) per tile, at the price of a little
+// more halo: 64^3 at p = 4 takes 9 pieces (576 tiles, at most four per SM, each 7/8 as heavy).
+inline int choose_k1_pieces(const SysDev &d, int sms) {
+    const int T = 1 << d.tlog;
+    const int base = (d.K1 + T - 1) / T;
+    const int64_t cols = (int64_t)((d.K2 + T - 1) / T) * ((d.K3 + T - 1) / T);
+    if (sms <= 0 || base * cols < sms) return base;
+    int best = base;
+    double best_cost = 0.0;
+    for (int np = base; np <= 2 * base; ++np) {
+        const int64_t per_sm = (np * cols + sms - 1) / sms;
+        const double cost = (double)per_sm * ((double)d.K1 / np + 0.5 * (d.p - 1));
+        if (np == base || cost < best_cost - 1e-9) {
+            best = np;
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
 // Tile edge for n atoms on a GPU with `sms` SMs. 16^3 tiles halve the halo each tile adds to the global
@@ -282,9 +315,9 @@ inline int bucket_capacity(int64_t n, int ntiles, int tlog) {
 
 // Bytes of the padded tile-counter array and of the influence-stage partials.
 inline size_t bcount_bytes(int ntiles) { return (size_t)ntiles * BCOUNT_STRIDE * sizeof(unsigned); }
-// counters for the finest tiling (the most tiles any choice can need)
+// counters for the finest tiling (the most tiles any choice can need: 8-point tiles, twice the k1 pieces)
 inline size_t bcount_bytes_max(const int K[3]) {
-    return bcount_bytes(((K[0] + 7) / 8) * ((K[1] + 7) / 8) * ((K[2] + 7) / 8));
+    return bcount_bytes(2 * ((K[0] + 7) / 8) * ((K[1] + 7) / 8) * ((K[2] + 7) / 8));
 }
 inline size_t partials_bytes(const SysDev &d) { return ((size_t)d.nconv + d.K1) * 8 * sizeof(float2); }
 

@@ -246,7 +246,7 @@ static void launch_tiles_spread(const SysDev &d, cudaStream_t s) {
 }
 template <int P>
 static void launch_tiles_gather(const SysDev &d, cudaStream_t s) {
-    const unsigned nt = (unsigned)tile_threads(d, d.n);
+    const unsigned nt = (unsigned)tile_threads(d, d.n, true);
     if (d.tlog == 4) launch_pdl(k_gather<P, 16>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 4), s, d, STAGE_GATHER);
     else launch_pdl(k_gather<P, 8>, d.ntiles + OVF_ITEMS, nt, smem_gather_all(P, 3), s, d, STAGE_GATHER);
 }

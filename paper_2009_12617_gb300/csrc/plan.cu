@@ -155,6 +155,7 @@ pme_status plan_reserve(pme_plan *pl, int64_t n) {
     // tile edge from the atom density, or the one the autotuner / caller set (every tile counter is zero
     // between evaluations, so the tiling may change here; results do not depend on it)
     set_tiling(d, pl->tile_log_set ? pl->tile_log_set : choose_tile_log(ncap, pl->K, pl->sms));
+    set_tiling(d, d.tlog, choose_k1_pieces(d, pl->sms));
     const int cap = bucket_capacity(ncap, d.ntiles, d.tlog);
     const size_t nb = (size_t)d.ntiles * cap;
     size_t off = 0;
@@ -453,6 +454,44 @@ pme_status pme_compute_debug(pme_plan *pl, const float *pos, const float *q, int
     return PME_OK;
 }
 
+// pme_enqueue_host's two input slots (device positions and charges) for at least n atoms, the copy stream
+// and the slot events.
+static pme_status ensure_async_inputs(pme_plan *pl, int64_t n) {
+    cudaError_t e;
+    if (!pl->copy_stream && (e = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        pl->copy_stream = nullptr;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    for (int s = 0; s < 2; ++s)
+        for (cudaEvent_t *ev : {&pl->in_ready[s], &pl->in_free[s]})
+            if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) {
+                *ev = nullptr;
+                return cuda_fail(e, "cudaEventCreate");
+            }
+    if (n <= pl->async_cap && pl->async_mem) return PME_OK;
+    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaStreamSynchronize(pl->copy_stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (pl->async_mem) cudaFree(pl->async_mem);
+    pl->async_mem = nullptr;
+    pl->async_cap = 0;
+    const int64_t m = n > 0 ? n : 1;
+    const size_t bytes = 2 * (align256((size_t)m * 12) + align256((size_t)m * 4));
+    if ((e = lib_malloc(&pl->async_mem, bytes)) != cudaSuccess) {
+        pl->async_mem = nullptr;
+        return fail(PME_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    pl->async_cap = m;
+    for (pme_plan::EvalGraph &gr : pl->g_async)  // recorded for the old slots
+        if (gr.exec) {
+            cudaGraphExecDestroy(gr.exec);
+            gr = pme_plan::EvalGraph();
+        }
+    return PME_OK;
+}
+
+static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *forces,
+                                     float *mfor, double *result, double *mres);
+
 pme_status pme_enqueue_host(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *result) {
     pme_status st = check_atoms(pl, pos, q, n, forces);
     if (st) return st;
@@ -460,17 +499,43 @@ pme_status pme_enqueue_host(pme_plan *pl, const float *pos, const float *q, int6
     DeviceGuard g(pl->dev);
     if ((st = plan_reserve(pl, n)) != PME_OK) return st;
     if ((st = ensure_host_staging(pl, n)) != PME_OK) return st;
-    const float *mpos = n > 0 ? (const float *)device_view(pos) : nullptr;
-    const float *mq = n > 0 ? (const float *)device_view(q) : nullptr;
+    if ((st = ensure_async_inputs(pl, n)) != PME_OK) return st;
     float *mfor = n > 0 ? (float *)device_view(forces) : nullptr;
     double *mres = (double *)device_view(result);
-    if (!mres || (n > 0 && (!mpos || !mq || !mfor)))
+    if (!mres || (n > 0 && (!device_view(pos) || !device_view(q) || !mfor)))
         return fail(PME_EINVAL, "pme_enqueue_host needs page-locked pos, q, forces and result (cudaHostAlloc / cudaHostRegister)");
+    // the inputs go to the next slot by the copy engine on the copy stream, once the evaluation that last
+    // read that slot has finished; the plan stream waits for them, so the copies overlap the evaluation
+    // still running there
+    const int slot = pl->async_slot;
+    pl->async_slot ^= 1;
+    char *sb = (char *)pl->async_mem + (size_t)slot * (align256((size_t)pl->async_cap * 12) + align256((size_t)pl->async_cap * 4));
+    float *dpos = (float *)sb, *dq = (float *)(sb + align256((size_t)pl->async_cap * 12));
+    cudaError_t e;
+    if ((e = cudaStreamWaitEvent(pl->copy_stream, pl->in_free[slot], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    if (n > 0) {
+        if ((e = cudaMemcpyAsync(dpos, pos, (size_t)n * 12, cudaMemcpyHostToDevice, pl->copy_stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(pos)");
+        if ((e = cudaMemcpyAsync(dq, q, (size_t)n * 4, cudaMemcpyHostToDevice, pl->copy_stream)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(q)");
+    }
+    if ((e = cudaEventRecord(pl->in_ready[slot], pl->copy_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(pl->stream, pl->in_ready[slot], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((st = launch_async_graph(pl, dpos, dq, n, forces, mfor, result, mres)) != PME_OK) return st;
+    if ((e = cudaEventRecord(pl->in_free[slot], pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return PME_OK;
+}
+
+// The evaluation of pme_enqueue_host on device inputs dpos / dq and the copy of its forces, energy, virial
+// and status to page-locked host memory (device-side addresses mfor / mres), as a graph recorded once per
+// argument set (the four most recent kept).
+static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *forces,
+                                     float *mfor, double *result, double *mres) {
     float *dfor = (float *)((char *)pl->host_mem + align256((size_t)pl->host_cap * 12));
-    const SysDev d = plan_descriptor(pl, mpos, mq, n, dfor, nullptr);
+    const SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, nullptr);
     pme_plan::EvalGraph key;
-    key.pos = pos;
-    key.q = q;
+    key.pos = dpos;
+    key.q = dq;
     key.forces = forces;
     key.atoms = pl->atom_mem;
     key.staging = pl->host_mem;
@@ -640,10 +705,11 @@ pme_status pme_set_slab_split(int fwd_ctas, int inv_ctas) {
 }
 
 size_t pme_plan_device_bytes(const pme_plan *pl) {
-    return pl ? pl->mesh_bytes + pl->atom_bytes + (pl->host_mem ? align256((size_t)pl->host_cap * 12) * 2 +
-                                                                          align256((size_t)pl->host_cap * 4)
-                                                                    : 0)
-              : 0;
+    if (!pl) return 0;
+    size_t b = pl->mesh_bytes + pl->atom_bytes;
+    if (pl->host_mem) b += align256((size_t)pl->host_cap * 12) * 2 + align256((size_t)pl->host_cap * 4);
+    if (pl->async_mem) b += 2 * (align256((size_t)pl->async_cap * 12) + align256((size_t)pl->async_cap * 4));
+    return b;
 }
 
 void pme_destroy(pme_plan *pl) {
@@ -658,6 +724,14 @@ void pme_destroy(pme_plan *pl) {
     if (pl->md_mem) cudaFree(pl->md_mem);
     if (pl->tc_w) cudaFree(pl->tc_w);
     if (pl->rec_stream) cudaStreamDestroy(pl->rec_stream);
+    if (pl->copy_stream) {
+        cudaStreamSynchronize(pl->copy_stream);
+        cudaStreamDestroy(pl->copy_stream);
+    }
+    for (int s = 0; s < 2; ++s)
+        for (cudaEvent_t ev : {pl->in_ready[s], pl->in_free[s]})
+            if (ev) cudaEventDestroy(ev);
+    if (pl->async_mem) cudaFree(pl->async_mem);
     if (pl->mesh_mem) cudaFree(pl->mesh_mem);
     if (pl->atom_mem) cudaFree(pl->atom_mem);
     if (pl->host_mem) cudaFree(pl->host_mem);

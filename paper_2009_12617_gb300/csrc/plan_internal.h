@@ -51,6 +51,14 @@ struct pme_plan {
     EvalGraph g_dev, g_host, seen_dev, seen_host;  // recorded graphs, and the previous call's arguments
     EvalGraph g_async[4];           // recorded graphs of pme_enqueue_host, most recent argument sets
     int g_async_next = 0;
+    // pme_enqueue_host's input slots: two device copies of (positions, charges), filled by the copy engine on
+    // copy_stream while the plan stream still runs the previous evaluation; in_ready[s] marks slot s filled,
+    // in_free[s] the evaluation that read it finished
+    void *async_mem = nullptr;
+    int64_t async_cap = 0;
+    int async_slot = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
     cudaStream_t rec_stream = nullptr;
     // multi-step loop (pme_run_steps): step counter and real-space energies, and the recorded graph of one
     // chunk of steps for the last argument set

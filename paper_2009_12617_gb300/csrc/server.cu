@@ -139,6 +139,7 @@ static bool launch_wave(pme_server *sv, Wave &w) {
     for (int s = 0; s < nsys; ++s) {
         Request *r = w.reqs[s];
         w.sys.push_back(plan_descriptor(r->plan, r->pos, r->q, r->n, r->forces, nullptr));
+        if (nsys > 1) shared_tiling(w.sys.back());
     }
     if (!w.st.dmem) {
         if (w.st.init(sv->dev, MAX_WAVE_SYSTEMS, 1) != PME_OK) {

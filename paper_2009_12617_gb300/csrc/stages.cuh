@@ -161,7 +161,7 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
                 continue;
             }
             qacc += (unsigned long long)f2ll_rn(fabsf(q) * QABS_SCALE);
-            tile[k] = ((b0 >> d.tlog) * d.nt2 + (b1 >> d.tlog)) * d.nt3 + (b2 >> d.tlog);
+            tile[k] = (k1_piece(d, b0) * d.nt2 + (b1 >> d.tlog)) * d.nt3 + (b2 >> d.tlog);
             ra[k] = make_float4(w0, w1, w2, q);
             rb[k] = make_int2(b0 | (b1 << 10) | (b2 << 20), i);
             kind[k] = fabsf(q) <= Q_TILE_MAX ? 1 : 2;
@@ -216,10 +216,12 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
 
 PME_DEV void tile_origin(const SysDev &d, int tile, int &o1, int &o2, int &o3) {
     const int t3 = tile % d.nt3, t2 = (tile / d.nt3) % d.nt2, t1 = tile / (d.nt3 * d.nt2);
-    o1 = t1 << d.tlog;
+    o1 = k1_start(d, t1);
     o2 = t2 << d.tlog;
     o3 = t3 << d.tlog;
 }
+// Width along k1 of the tile with origin o1 (the piece's end minus its start).
+PME_DEV int tile_width1(const SysDev &d, int o1) { return k1_start(d, k1_piece(d, o1) + 1) - o1; }
 
 PME_DEV int wrapk(int k, int K) { return k < 0 ? k + K : (k >= K ? k - K : k); }
 
@@ -313,6 +315,11 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     }
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
+    // this thread's first record in flight with the count (the slot is always inside the bucket; it is used
+    // only if it holds an atom)
+    const int a0 = imin(tid, d.cap - 1);
+    const float4 ra0 = ldcg(A + a0);
+    const int2 rb0 = ldcg(B + a0);
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
     if (!cleared) spread_clear<P, T>(smem);
     PME_SYNC();
@@ -321,8 +328,8 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     // distinct residues and their shared-memory atomics do not share banks. Results do not depend on the
     // order (integer sums).
     for (int a = tid; a < cnt; a += nth) {
-        const float4 ra = ldcg(A + a);
-        const int2 rb = ldcg(B + a);
+        const float4 ra = a == tid ? ra0 : ldcg(A + a);
+        const int2 rb = a == tid ? rb0 : ldcg(B + a);
         ra_s[a] = ra;
         rb_s[a] = rb;
         const int l1 = (rb.x & 1023) - o1 + H, l2 = ((rb.x >> 10) & 1023) - o2 + H, l3 = ((rb.x >> 20) & 1023) - o3 + H;
@@ -381,12 +388,13 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     }
     PME_SYNC();
     // flush: thread t < ng R adds point i3 = t mod R of rows t / R, t / R + ng, ... (as the force stage's
-    // region load)
+    // region load); rows of the planes i1 < R1 (the tile's k1 width plus the halo) only
+    const int R1 = tile_width1(d, o1) + H;
     const int ng = nth >= R ? nth / R : 1, rg = nth >= R ? tid / R : 0;
     for (int i3 = nth >= R ? tid - rg * R : 0; i3 < R; i3 += (nth >= R ? R : 1)) {
         if (rg >= ng) break;
         const int k3 = wrapk(o3 - H + i3, d.K3);
-        for (int r = rg; r < R * R; r += ng) {
+        for (int r = rg; r < R1 * R; r += ng) {
             const int i1 = r / R, i2 = r - i1 * R;
             const int i = i1 * PL + i2 * R + i3;
             const int h = hi[i], l = lo[i];
@@ -1260,7 +1268,6 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
         for (int jj = 0; jj < (half ? P - H0 : H0); ++jj) {
             const int j1 = half * H0 + jj;
             const int k1 = wrapk(b1 - j1, d.K1);
-            float a = 0.f, b = 0.f, c = 0.f;  // plane sums, as in the tile path
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) {
                 const int k2 = wrapk(b2 - j2, d.K2);
@@ -1272,13 +1279,10 @@ PME_DEV void gather_atom_global(const SysDev &d, float4 ra, int2 rb) {
                     s = fmaf(th3[j3], ph, s);
                     ds = fmaf(dth3[j3], ph, ds);
                 }
-                a = fmaf(th2[j2], s, a);
-                b = fmaf(dth2[j2], s, b);
-                c = fmaf(th2[j2], ds, c);
+                g1 = fmaf(dth1[j1] * th2[j2], s, g1);
+                g2 = fmaf(th1[j1] * dth2[j2], s, g2);
+                g3 = fmaf(th1[j1] * th2[j2], ds, g3);
             }
-            g1 = fmaf(dth1[j1], a, g1);
-            g2 = fmaf(th1[j1], b, g2);
-            g3 = fmaf(th1[j1], c, g3);
         }
         gh[half][0] = g1;
         gh[half][1] = g2;
@@ -1315,18 +1319,19 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
         const int a0 = imin(tid >> 1, d.cap - 1);
         const float4 ra0 = ldcg(A + a0);
         const int2 rb0 = ldcg(B + a0);
+        const int R1 = tile_width1(d, o1) + H;  // planes of the region the tile's atoms reach
         if (nth >= R) {
             // thread t < ng R loads point i3 = t mod R of rows t / R, t / R + ng, ... (ng = nth / R row
             // groups): the k3 index is computed once, each row costs two wraps
             const int ng = nth / R, rg = tid / R, i3 = tid - rg * R;
             if (rg < ng) {
                 const int k3 = wrapk(o3 - H + i3, d.K3);
-                for (int r0 = rg; r0 < R * R; r0 += LOAD_BATCH * ng) {
+                for (int r0 = rg; r0 < R1 * R; r0 += LOAD_BATCH * ng) {
                     float v[LOAD_BATCH];
 #pragma unroll
                     for (int u = 0; u < LOAD_BATCH; ++u) {
                         const int r = r0 + u * ng;
-                        if (r < R * R) {
+                        if (r < R1 * R) {
                             const int i1 = r / R, i2 = r - i1 * R;
                             const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2);
                             v[u] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
@@ -1334,11 +1339,11 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
                     }
 #pragma unroll
                     for (int u = 0; u < LOAD_BATCH; ++u)
-                        if (r0 + u * ng < R * R) reg[(r0 + u * ng) * R + i3] = v[u];
+                        if (r0 + u * ng < R1 * R) reg[(r0 + u * ng) * R + i3] = v[u];
                 }
             }
         } else {
-            for (int i = tid; i < VOL; i += nth) {
+            for (int i = tid; i < R1 * R * R; i += nth) {
                 const int i3 = i % R, i2 = (i / R) % R, i1 = i / (R * R);
                 const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2), k3 = wrapk(o3 - H + i3, d.K3);
                 reg[i] = ldcg(d.phi + ((size_t)k1 * d.K2 + k2) * d.K3 + k3);
@@ -1372,9 +1377,6 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
                 const int jh = H0 + jj < P ? H0 + jj : P - 1;
                 const float t1 = half ? th1[jh] : th1[jj];
                 const float dt1 = half ? dth1[jh] : dth1[jj];
-                // per plane: a = sum_j2 th2 S, b = sum_j2 dth2 S, c = sum_j2 th2 dS over the rows' sums
-                // S = sum_j3 th3 phi, dS = sum_j3 dth3 phi; then the plane's weight (one multiply-add each)
-                float a = 0.f, b = 0.f, c = 0.f;
 #pragma unroll
                 for (int j2 = 0; j2 < P; ++j2) {
                     const float *row = reg + ((l1 - j1) * R + (l2 - j2)) * R + l3;
@@ -1385,13 +1387,10 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
                         s = fmaf(th3[j3], ph, s);
                         ds = fmaf(dth3[j3], ph, ds);
                     }
-                    a = fmaf(th2[j2], s, a);
-                    b = fmaf(dth2[j2], s, b);
-                    c = fmaf(th2[j2], ds, c);
+                    g1 = fmaf(dt1 * th2[j2], s, g1);
+                    g2 = fmaf(t1 * dth2[j2], s, g2);
+                    g3 = fmaf(t1 * th2[j2], ds, g3);
                 }
-                g1 = fmaf(dt1, a, g1);
-                g2 = fmaf(t1, b, g2);
-                g3 = fmaf(t1, c, g3);
             }
 #if defined(PME_HOST_EMULATION)
             if (!half) {

@@ -111,7 +111,8 @@ static void load_cache_locked() {
             t.tile_threads = (int)tt;
             t.us = us;
             if ((t.tile_edge == 8 || t.tile_edge == 16) &&
-                (t.tile_threads == 128 || t.tile_threads == 256 || (t.tile_threads == 512 && t.tile_edge == 16)))
+                (t.tile_threads == 0 || t.tile_threads == 128 || t.tile_threads == 256 ||
+                 (t.tile_threads == 512 && t.tile_edge == 16)))
                 g_entries.push_back(t);
         }
         s = e + 1;
@@ -292,7 +293,9 @@ pme_status pme_autotune(pme_plan *pl, const float *pos, const float *q, int64_t 
     // candidates: the default first (its results are the reference bits), then every other combination
     const int tdef = pl->tile_log_set ? pl->tile_log_set : choose_tile_log(n > 0 ? n : 1, pl->K, pl->sms);
     if ((st = plan_retile(pl, tdef, 0, n)) != PME_OK) return st;
-    const int ntdef = tile_threads(pl->d, n);
+    // the default sizes: one CTA size for 8^3 tiles; for 16^3 tiles spreading and force interpolation
+    // differ (nt = 0 keeps that per-stage default)
+    const int ntdef = tdef == 4 ? 0 : tile_threads(pl->d, n);
     struct Cand { int tlog, nt; double us; bool same; };
     std::vector<Cand> cands = {{tdef, ntdef, 0.0, true}};
     for (int tlog : {3, 4})
@@ -316,7 +319,7 @@ pme_status pme_autotune(pme_plan *pl, const float *pos, const float *q, int64_t 
     pl->tuned_apt = apt_class(pl->K, n);
     tune_record(pl, n, cands[best].tlog, cands[best].nt, cands[best].us);
     res.tile_edge = 1 << cands[best].tlog;
-    res.tile_threads = cands[best].nt;
+    res.tile_threads = tile_threads(pl->d, n);
     res.us_per_eval = cands[best].us;
     res.default_us = cands[0].us;
     if (out) *out = res;

@@ -22,6 +22,7 @@ def main(lib_path):
                              dp, ctypes.c_int, ctypes.c_int, fp, dp, ctypes.POINTER(ctypes.c_longlong), fp,
                              ctypes.c_int]
     lib.emu_spme.restype = ctypes.c_int
+    lib.emu_set_k1_pieces.argtypes = [ctypes.c_int]
 
     def run(pos, q, K, p, box, cap, tile_log):
         pos = np.ascontiguousarray(pos, np.float32)
@@ -54,6 +55,11 @@ def main(lib_path):
             for cap, tile_log in ((0, 0), (32, 3), (0, 4)):
                 run(pos, q, K, p, box, cap, tile_log)
                 cases += 1
+            # the k1 axis cut into the most pieces the library may choose (widths floor / ceil of K1 / pieces)
+            lib.emu_set_k1_pieces(2 * ((K[0] + 7) // 8))
+            run(pos, q, K, p, box, 0, 3)
+            lib.emu_set_k1_pieces(0)
+            cases += 1
     # empty system and every atom in one tile (all of them on the overflow path)
     run(np.zeros((0, 3)), np.zeros(0), (32, 32, 32), 4, np.diag([20.0] * 3), 0, 0)
     pos = np.full((300, 3), 5.0) + rng.random((300, 3)) * 0.1

@@ -56,6 +56,9 @@ static void gather_item(const SysDev &d, int it, void *sp) {
     }
 }
 
+// Pieces of the k1 axis for the tiles of later emu_setup calls (0: the fewest, as set_tiling's default).
+static int g_k1_pieces = 0;
+
 // The emulated resident state of one system (as pme_create + pme_reserve build it on the device).
 // Returns 0, or -1 / -2 for invalid / unsupported input.
 static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta, const double box[9], int cap_override,
@@ -80,7 +83,7 @@ static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta,
     make_twiddles(K[1], K[1], s.tw.data() + K1);
     make_twiddles((int)Nh, (int)Nh, s.tw.data() + K1 + K2);
     make_twiddles(K[2], (int)Nh + 1, s.tw.data() + K1 + K2 + Nh);
-    set_tiling(d, tile_log > 0 ? tile_log : choose_tile_log(n > 0 ? n : 1, K, 0));
+    set_tiling(d, tile_log > 0 ? tile_log : choose_tile_log(n > 0 ? n : 1, K, 0), g_k1_pieces);
     s.bcount.assign(bcount_bytes(d.ntiles) / sizeof(unsigned), 0u);
     s.partials.assign(partials_bytes(d) / sizeof(double), 0.0);
     const int cap = cap_override > 0 ? cap_override : bucket_capacity(n > 0 ? n : 1, d.ntiles, d.tlog);
@@ -110,6 +113,8 @@ static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta,
 }
 
 extern "C" {
+
+void emu_set_k1_pieces(int n) { g_k1_pieces = n; }
 
 // One or more evaluations (repeat >= 1, same inputs) of the emulated pipeline. Outputs: forces (n*3),
 // ev[7], and optionally the fixed-point mesh as spread (grid_out, K1*K2*K3 int64) and phi (K1*K2*K3).

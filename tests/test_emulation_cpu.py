@@ -1,6 +1,8 @@
 """The library's stage bodies, compiled for the CPU with one thread per CTA (tests/emu), against the FP64
 oracle: checks the index arithmetic, FFT plumbing, influence table and reductions without a GPU. The
 tolerances are the ones the GPU parity tests use."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -78,6 +80,29 @@ def test_emulated_results_do_not_depend_on_tiling(emu):
     _, F16, ev16, m16, _ = emu_spme(emu, s.pos, s.q, (32, 40, 48), 6, 0.34, s.box, tile_log=4)
     assert np.array_equal(m8, m16)
     assert np.array_equal(F8, F16) and np.array_equal(ev8, ev16)
+
+
+@pytest.mark.parametrize("K,p,tile_log,pieces", [((32, 40, 48), 4, 3, (5, 7, 8)), ((30, 32, 36), 5, 3, (5, 6, 8)),
+                                                 ((32, 40, 48), 6, 4, (3, 4))])
+def test_emulated_k1_pieces_do_not_change_results(emu, oracle_mod, K, p, tile_log, pieces):
+    """Cutting the k1 axis into more, thinner tile pieces (widths floor / ceil of K1 / pieces, as the
+    library does to balance tiles over the SMs) gives the default tiling's mesh, forces and energies bit
+    for bit; the default matches the oracle."""
+    s = wl.parity_system()
+    emu.emu_set_k1_pieces.argtypes = [ctypes.c_int]
+    emu.emu_set_k1_pieces(0)
+    _, F0, ev0, m0, _ = emu_spme(emu, s.pos, s.q, K, p, 0.34, s.box, tile_log=tile_log)
+    r = oracle_mod.spme(s.pos.astype(float), s.q.astype(float), K, p, 0.34, s.box)
+    assert rel_energy(ev0[0], r["energy"]) < E_REL_TOL and rms_force(F0, r["forces"]) < F_RMS_TOL
+    try:
+        for n in pieces:
+            emu.emu_set_k1_pieces(n)
+            st, F, ev, m, _ = emu_spme(emu, s.pos, s.q, K, p, 0.34, s.box, tile_log=tile_log)
+            assert st == 0
+            assert np.array_equal(m, m0), n
+            assert np.array_equal(F, F0) and np.array_equal(ev, ev0), n
+    finally:
+        emu.emu_set_k1_pieces(0)
 
 
 def test_emulated_mesh_permutation_invariant(emu):
