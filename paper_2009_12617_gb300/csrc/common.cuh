@@ -43,6 +43,11 @@ constexpr float FIX_INV = 9.094947017729282379150390625e-13f;  // 2^-40
 // bounds every mesh value and every partial sum, so larger totals are refused.
 constexpr float QABS_SCALE = 16777216.0f;                // 2^24
 constexpr unsigned long long QABS_LIMIT = 1ull << 46;    // 2^22 e in 2^24 units
+// The binning CTAs add their sums of |q| into QABS_SLOTS counters, one per 128-byte line (CTA b into
+// b mod QABS_SLOTS), so no single address collects one atomic per CTA; the force stage's final reduction
+// adds them up and resets them.
+constexpr int QABS_SLOTS = 64;
+constexpr size_t QABS_BYTES = (size_t)QABS_SLOTS * 128;
 constexpr int BIN_PER_THREAD = 1;           // atoms per thread per pass of the binning stage
 constexpr int BIN_CHUNK = 128 * BIN_PER_THREAD;  // atoms per binning work item
 constexpr int OVF_ITEMS = 8;     // extra spread / gather work items that handle bucket-overflow atoms
@@ -127,7 +132,7 @@ enum StatusBits : unsigned {
 struct Ctl {
     unsigned status;            // StatusBits, latched until the host reads and clears it
     unsigned novf;              // atoms that did not fit in their tile's bucket
-    unsigned long long qabs;    // sum |q| in 2^-24 e units
+    unsigned long long unused;  // (kept for the layout the host copy expects)
     unsigned novf_gather;       // copy of novf taken by the spreading stage for the force stage
     unsigned pad[3];
     double ev[8];               // energy, virial xx yy zz xy xz yz (internal copy for synchronous calls)
@@ -179,6 +184,7 @@ struct SysDev {
     float4 *bka;                 // bucket records (w1, w2, w3, q), [tile][cap]
     int2 *bkb;                   // bucket records (packed base, atom index)
     unsigned *bcount;            // atoms binned per tile, at tile * BCOUNT_STRIDE
+    unsigned long long *qslot;   // QABS_SLOTS sums of |q| (2^-24 e units), at slot * 16
     float4 *ova;                 // overflow records, capacity n
     int2 *ovb;
     double *partials;            // 8 double-float (hi, lo) slots per influence-stage item, then K1 level-1 slots

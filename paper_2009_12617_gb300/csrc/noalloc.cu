@@ -280,6 +280,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     size_t off = 0;
     const size_t o_ctl = off;  off = al256(off + sizeof(Ctl));
     const size_t o_cnt = off;  off = al256(off + bcount_bytes(d.ntiles));
+    const size_t o_qs = off;   off = al256(off + QABS_BYTES);
     const size_t o_par = off;  off = al256(off + partials_bytes(d));
     const size_t o_grid = off; off = al256(off + K1 * K2 * K3 * 8);
     const size_t zero_bytes = off;
@@ -298,6 +299,7 @@ extern "C" pme_status pme_compute_noalloc(const int K[3], int p, double beta, co
     unsigned char *b = nd->scratch;
     d.ctl = (Ctl *)(b + o_ctl);
     d.bcount = (unsigned *)(b + o_cnt);
+    d.qslot = (unsigned long long *)(b + o_qs);
     d.partials = (double *)(b + o_par);
     d.grid = (unsigned long long *)(b + o_grid);
     A.bmod = (double *)(b + o_bmod);

@@ -121,6 +121,7 @@ static pme_status alloc_mesh(pme_plan *pl) {
     const size_t o_bc = off;   off = align256(off + K1 * K2 * H3 * sizeof(float4));
     const size_t o_tw = off;   off = align256(off + (K1 + K2 + Nh + Nh + 1) * 8);
     const size_t o_cnt = off;  off = align256(off + bcount_bytes_max(pl->K));
+    const size_t o_qs = off;   off = align256(off + QABS_BYTES);
     const size_t o_par = off;  off = align256(off + partials_bytes(d));
     const size_t o_ctl = off;  off = align256(off + sizeof(Ctl));
     cudaError_t e = lib_malloc(&pl->mesh_mem, off);
@@ -140,6 +141,7 @@ static pme_status alloc_mesh(pme_plan *pl) {
     d.tw3h = tw + K1 + K2;
     d.tw3 = tw + K1 + K2 + Nh;
     d.bcount = (unsigned *)(b + o_cnt);
+    d.qslot = (unsigned long long *)(b + o_qs);
     d.partials = (double *)(b + o_par);
     d.ctl = (Ctl *)(b + o_ctl);
     // The int64 mesh, bucket counts and control block start at zero; afterwards the consuming stages

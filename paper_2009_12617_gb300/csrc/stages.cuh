@@ -129,7 +129,9 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
     const int i1 = imin(d.n, i0 + BIN_CHUNK);
     unsigned long long qacc = 0;
     unsigned bad = 0;
-    for (int base = i0 + tid; base < i1; base += BIN_PER_THREAD * nth) {
+    // the trip count is the same for every thread of the block (lanes past the end have no atom), so the
+    // warp-wide slot claim below always sees whole warps
+    for (int base = i0 + tid; base - tid < i1; base += BIN_PER_THREAD * nth) {
         float r[BIN_PER_THREAD][3], qv[BIN_PER_THREAD];
 #pragma unroll
         for (int k = 0; k < BIN_PER_THREAD; ++k) {  // issue every load first
@@ -168,8 +170,22 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
         }
         unsigned rank[BIN_PER_THREAD];
 #pragma unroll
-        for (int k = 0; k < BIN_PER_THREAD; ++k)  // independent atomics, all in flight together
+        for (int k = 0; k < BIN_PER_THREAD; ++k) {  // independent atomics, all in flight together
+#if defined(PME_HOST_EMULATION)
             if (kind[k] == 1) rank[k] = atomic_add_u32(&d.bcount[(size_t)tile[k] * BCOUNT_STRIDE], 1u);
+#else
+            // lanes of a warp binning into the same tile (the atoms of a molecule, mostly) claim consecutive
+            // slots with one atomic by their lowest lane: fewer same-address atomics queue at each counter
+            const int key = kind[k] == 1 ? tile[k] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const int lane = tid & 31, leader = __ffs(peers) - 1;
+            unsigned first = 0;
+            if (key >= 0 && lane == leader)
+                first = atomic_add_u32(&d.bcount[(size_t)key * BCOUNT_STRIDE], (unsigned)__popc(peers));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            rank[k] = first + (unsigned)__popc(peers & ((1u << lane) - 1u));
+#endif
+        }
 #pragma unroll
         for (int k = 0; k < BIN_PER_THREAD; ++k) {
             const int i = base + k * nth;
@@ -203,7 +219,7 @@ PME_DEV void stage_bin(const SysDev &d, int item, void *smem) {
         unsigned long long tot = 0;
         for (int w = 0; w < (nth + 31) / 32; ++w) tot += red[w];
         if (tot >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
-        else if (tot) atomic_add_u64(&d.ctl->qabs, tot);
+        else if (tot) atomic_add_u64(d.qslot + (size_t)(item & (QABS_SLOTS - 1)) * 16, tot);
     }
 }
 
@@ -712,11 +728,28 @@ PME_DEV void reduce_level2(const SysDev &d, void *smem) {
         }
         PME_SYNC();
     }
-    if (tid == 0) {
+    if (tid == 0)
         for (int c = 0; c < 7; ++c) d.ev[c] = (double)t[c].hi + (double)t[c].lo;
-        if (ldcg(&d.ctl->qabs) >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
-        d.ctl->qabs = 0ull;
+    // the sum of |q| over the binning slots (exact integers): past the fixed-point headroom -> overflow;
+    // the slots go back to zero for the next binning
+#if defined(PME_HOST_EMULATION)
+    if (tid == 0) {
+        unsigned long long qa = 0;
+        for (int sl = 0; sl < QABS_SLOTS; ++sl) {
+            qa += d.qslot[(size_t)sl * 16];
+            d.qslot[(size_t)sl * 16] = 0ull;
+        }
+        if (qa >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
     }
+#else
+    if (tid < 32) {
+        unsigned long long qa = ldcg(d.qslot + (size_t)tid * 16) + ldcg(d.qslot + (size_t)(tid + 32) * 16);
+        qa = warp_sum_u64(qa);
+        d.qslot[(size_t)tid * 16] = 0ull;
+        d.qslot[(size_t)(tid + 32) * 16] = 0ull;
+        if (tid == 0 && qa >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+    }
+#endif
     PME_SYNC();
 }
 
@@ -1301,7 +1334,7 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
         for (unsigned a = (unsigned)((item - d.ntiles) * nth + tid); a < novf; a += (unsigned)(OVF_ITEMS * nth))
             gather_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
     } else {
-        constexpr int R = Region<P, T>::R, VOL = Region<P, T>::VOL, H = P - 1;
+        constexpr int R = Region<P, T>::R, H = P - 1;
         float *reg = (float *)smem;
         int o1, o2, o3;
         if (org) {

@@ -24,6 +24,7 @@ struct EmuState {
     std::vector<float4> bc;
     std::vector<float> phi;
     std::vector<unsigned> bcount;
+    std::vector<unsigned long long> qslot;
     std::vector<double> partials;
     std::vector<float4> bka, ova;
     std::vector<int2> bkb, ovb;
@@ -85,6 +86,7 @@ static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta,
     make_twiddles(K[2], (int)Nh + 1, s.tw.data() + K1 + K2 + Nh);
     set_tiling(d, tile_log > 0 ? tile_log : choose_tile_log(n > 0 ? n : 1, K, 0), g_k1_pieces);
     s.bcount.assign(bcount_bytes(d.ntiles) / sizeof(unsigned), 0u);
+    s.qslot.assign(QABS_BYTES / sizeof(unsigned long long), 0ull);
     s.partials.assign(partials_bytes(d) / sizeof(double), 0.0);
     const int cap = cap_override > 0 ? cap_override : bucket_capacity(n > 0 ? n : 1, d.ntiles, d.tlog);
     s.bka.resize((size_t)d.ntiles * cap);
@@ -102,6 +104,7 @@ static int emu_setup(EmuState &s, int64_t n, const int K[3], int p, double beta,
     d.tw3h = s.tw.data() + K1 + K2;
     d.tw3 = s.tw.data() + K1 + K2 + Nh;
     d.bcount = s.bcount.data();
+    d.qslot = s.qslot.data();
     d.partials = s.partials.data();
     d.ctl = &s.ctl;
     d.bka = s.bka.data();
@@ -172,7 +175,8 @@ int emu_spme(int64_t n, const float *pos, const float *q, const int K[3], int p,
     for (int c = 0; c < 7; ++c) ev[c] = s.ctl.ev[c];
     if (phi_out) memcpy(phi_out, s.phi.data(), s.phi.size() * 4);
     // every self-resetting counter must be back at zero after an evaluation
-    bool clean = s.ctl.novf == 0 && s.ctl.qabs == 0;
+    bool clean = s.ctl.novf == 0;
+    for (unsigned long long v : s.qslot) clean = clean && v == 0;
     for (unsigned c : s.bcount) clean = clean && c == 0;
     for (unsigned long long g : s.grid) clean = clean && g == 0;
     if (!clean) status |= 0x100u;
