@@ -46,7 +46,56 @@ def parse():
     ap.add_argument("--legs", default="", help="comma list of extra legs to run alone (batched, serving, large, "
                                                "profile); skips the headline (profile: a short fixed sequence "
                                                "for ncu captures)")
+    ap.add_argument("--write-traffic", default="", metavar="NCU_CSV",
+                    help="no GPU work: read an ncu --csv log of dram__bytes_read.sum / dram__bytes_write.sum for "
+                         "the six stage kernels of one 64^3 evaluation and write profiles/dram_bytes.json for "
+                         "the roofline's traffic field (tied to the current kernel sources)")
     return ap.parse_args()
+
+
+TRAFFIC_SOURCES = ["paper_2009_12617_gb300/csrc/common.cuh", "paper_2009_12617_gb300/csrc/fft.cuh",
+                   "paper_2009_12617_gb300/csrc/stages.cuh", "paper_2009_12617_gb300/csrc/kernels.h",
+                   "paper_2009_12617_gb300/csrc/kernels.cu", "paper_2009_12617_gb300/csrc/pdl.cuh"]
+STAGE_OF_KERNEL = (("k_bin", "bin"), ("k_spread", "spread"), ("k_fwd", "fft_fwd"), ("k_conv", "influence"),
+                   ("k_inv", "fft_inv"), ("k_gather", "gather"))
+
+
+def write_traffic(csv_path: str) -> None:
+    """Mean DRAM read + write bytes per launch of each stage kernel from an ncu --csv metrics log, written to
+    profiles/dram_bytes.json with the hash of the kernel sources they were taken from."""
+    import csv
+    import hashlib
+
+    per_launch = {}
+    with open(csv_path, newline="") as f:
+        rows = [r for r in csv.reader(f) if r]
+    hdr_i = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    hdr = rows[hdr_i]
+    col = {k: hdr.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    for r in rows[hdr_i + 1:]:
+        if len(r) < len(hdr) or not r[col["Metric Name"]].startswith("dram__bytes_"):
+            continue
+        stage = next((st for k, st in STAGE_OF_KERNEL if k in r[col["Kernel Name"]]), None)
+        if stage is None:
+            continue
+        key = (stage, r[col["ID"]])
+        v = float(r[col["Metric Value"]].replace(",", "")) * scale.get(r[col["Metric Unit"]], 1.0)
+        per_launch[key] = per_launch.get(key, 0.0) + v
+    by_stage = {}
+    for (stage, _), v in per_launch.items():
+        by_stage.setdefault(stage, []).append(v)
+    sha = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in TRAFFIC_SOURCES)).hexdigest()
+    rec = {"what": "dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage kernel (mean over the "
+                   "captured launches), from " + os.path.basename(csv_path) + "; valid only while the kernel "
+                   "sources hash to source_sha256",
+           "source_files": TRAFFIC_SOURCES, "source_sha256": sha,
+           "launches": {st: len(v) for st, v in by_stage.items()},
+           "bytes_per_launch": {st: int(round(sum(v) / len(v))) for st, v in by_stage.items()}}
+    with open(os.path.join(ROOT, "profiles", "dram_bytes.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec["bytes_per_launch"]))
 
 
 # ---------------------------------------------------------------------------------------------------------
@@ -285,7 +334,7 @@ def traffic_record(stage: str):
     try:
         with open(path) as f:
             rec = json.load(f)
-        sha = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in rec["source_files"])).hexdigest()
+        sha = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in TRAFFIC_SOURCES)).hexdigest()
         if sha != rec["source_sha256"]:
             return None
         return rec["bytes_per_launch"].get(stage)
@@ -761,6 +810,9 @@ def spawn_ranks(args) -> int:
 
 def main():
     args = parse()
+    if args.write_traffic:
+        write_traffic(args.write_traffic)
+        return
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(spawn_ranks(args))
     dist = Dist()

@@ -331,11 +331,15 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     }
     const float4 *A = d.bka + (size_t)item * d.cap;
     const int2 *B = d.bkb + (size_t)item * d.cap;
-    // this thread's first record in flight with the count (the slot is always inside the bucket; it is used
-    // only if it holds an atom)
-    const int a0 = imin(tid, d.cap - 1);
-    const float4 ra0 = ldcg(A + a0);
-    const int2 rb0 = ldcg(B + a0);
+    // this thread's first record in flight with the count, for the threads below the mean occupancy (the
+    // bucket capacity is twice it plus a margin), so that few loads land on empty slots
+    const bool pf = tid < (d.cap >> 1);
+    float4 ra0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int2 rb0 = make_int2(0, 0);
+    if (pf) {
+        ra0 = ldcg(A + tid);
+        rb0 = ldcg(B + tid);
+    }
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
     if (!cleared) spread_clear<P, T>(smem);
     PME_SYNC();
@@ -344,8 +348,9 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     // distinct residues and their shared-memory atomics do not share banks. Results do not depend on the
     // order (integer sums).
     for (int a = tid; a < cnt; a += nth) {
-        const float4 ra = a == tid ? ra0 : ldcg(A + a);
-        const int2 rb = a == tid ? rb0 : ldcg(B + a);
+        const bool first = pf && a == tid;
+        const float4 ra = first ? ra0 : ldcg(A + a);
+        const int2 rb = first ? rb0 : ldcg(B + a);
         ra_s[a] = ra;
         rb_s[a] = rb;
         const int l1 = (rb.x & 1023) - o1 + H, l2 = ((rb.x >> 10) & 1023) - o2 + H, l3 = ((rb.x >> 20) & 1023) - o3 + H;
