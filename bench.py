@@ -610,12 +610,15 @@ def run_ours(args, dist: Dist):
     return result, sampler, plan, locals()
 
 
+INFLIGHT = 3  # host-array steps the end-to-end loop keeps in flight
+
+
 def run_e2e(pme, plan, s, steps: int):
     """End to end through the library's host-array calls on page-locked buffers, every step: positions and
     charges move host -> device (read by the binning kernel over the CPU-GPU link), the evaluation runs, and
     forces, energy and virial move device -> host (written by the library's copy kernel).
-    value: pme_enqueue_host with two steps in flight (the host waits for step i - 2, reads its result and
-    enqueues step i), host clock over all steps; host_writes_positions_us: the same with the host copying the
+    value: pme_enqueue_host with three steps in flight (the host waits for step i - 3's ticket, reads its
+    result and enqueues step i), host clock over all steps; host_writes_positions_us: the same with the host copying the
     positions of each step into page-locked memory first; synchronous: pme_compute_host, one call and one wait
     per step."""
     import torch
@@ -629,28 +632,28 @@ def run_e2e(pme, plan, s, steps: int):
     def pinned(shape, dtype):
         return torch.empty(shape, dtype=dtype).pin_memory().numpy()
 
-    # four page-locked position frames (prepared before the timed region), one charge array, two force/result
-    # sets: step i reads frame i % 4 and writes set i % 2, so four argument sets cycle (one cached graph each)
+    # four page-locked position frames (prepared before the timed region), one charge array, three
+    # force/result sets: step i reads frame i % 4 and writes set i % 3
     P_frames = [pinned((s.n, 3), torch.float32) for _ in frames]
     for P, fr in zip(P_frames, frames):
         P[:] = fr
     Q = pinned(s.n, torch.float32)
     Q[:] = s.q
-    outs = [(pinned((s.n, 3), torch.float32), pinned(8, torch.float64)) for _ in range(2)]
+    outs = [(pinned((s.n, 3), torch.float32), pinned(8, torch.float64)) for _ in range(INFLIGHT)]
     e2e_plan = pme.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
     try:
         def run(nsteps, host_writes):
             """host_writes: the host copies step i's frame into a working position array of its slot before
             enqueueing (as an integrator writing its new positions would), instead of cycling prepared frames."""
-            events = [torch.cuda.Event(), torch.cuda.Event()]
+            tickets = [0] * INFLIGHT
             energy = 0.0
-            for i in range(nsteps + 2):
-                slot = i % 2
-                if i >= 2:
-                    events[slot].synchronize()
+            for i in range(nsteps + INFLIGHT):
+                slot = i % INFLIGHT
+                if i >= INFLIGHT:
+                    pme.pme_host_wait(e2e_plan, tickets[slot])
                     R = outs[slot][1]
                     if R[7] != 0.0:
-                        raise RuntimeError(f"device status {R[7]} in step {i - 2}")
+                        raise RuntimeError(f"device status {R[7]} in step {i - INFLIGHT}")
                     energy += R[0]  # the step's result, read on the host
                 if i >= nsteps:
                     continue
@@ -660,8 +663,7 @@ def run_e2e(pme, plan, s, steps: int):
                     P[:] = frames[i % len(frames)]
                 else:
                     P = P_frames[i % len(P_frames)]
-                pme.pme_enqueue_host(e2e_plan, P, Q, F, R)
-                events[slot].record(stream)
+                tickets[slot] = pme.pme_enqueue_host(e2e_plan, P, Q, F, R)
             return energy
 
         run(10, False)  # records the argument sets' graphs
@@ -675,15 +677,14 @@ def run_e2e(pme, plan, s, steps: int):
         dt_w = time.perf_counter() - t0
         # device time of the same steps enqueued back to back (CUDA events on the plan stream, no host
         # waits): what the two-in-flight loop converges to when the host keeps ahead
-        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         nd = min(steps, 2000)
-        st.record(stream)
+        pme.pme_sync(e2e_plan)
+        t0 = time.perf_counter()
         for i in range(nd):
-            F, R = outs[i % 2]
-            pme.pme_enqueue_host(e2e_plan, P_frames[i % len(P_frames)], Q, F, R)
-        en.record(stream)
-        en.synchronize()
-        dev_us = 1000.0 * st.elapsed_time(en) / nd
+            F, R = outs[i % INFLIGHT]
+            t = pme.pme_enqueue_host(e2e_plan, P_frames[i % len(P_frames)], Q, F, R)
+        pme.pme_host_wait(e2e_plan, t)
+        dev_us = 1e6 * (time.perf_counter() - t0) / nd
     finally:
         pme.pme_destroy(e2e_plan)
     # synchronous, for comparison
@@ -701,10 +702,12 @@ def run_e2e(pme, plan, s, steps: int):
     dts = time.perf_counter() - t1
     return {"value": round(1e6 * dt / steps, 3), "unit": UNIT, "h2d_bytes_per_step": s.n * 16,
             "d2h_bytes_per_step": s.n * 12 + 8 * 8, "steps": steps,
-            "how": "pme_enqueue_host with two steps in flight on page-locked arrays (wait for step i-2, read its "
-                   "energy and status, enqueue step i on prepared position frame i % 4), host clock",
-            "device_us_per_step": round(dev_us, 3),
-            "device_how": "the same steps enqueued back to back, CUDA events on the plan stream",
+            "how": "pme_enqueue_host with three steps in flight on page-locked arrays (pme_host_wait for step "
+                   "i-3's ticket, read its energy and status, enqueue step i on prepared position frame i % 4), "
+                   "host clock",
+            "back_to_back_us_per_step": round(dev_us, 3),
+            "back_to_back_how": "the same steps enqueued without waiting (results overwritten), host clock from "
+                                "the first enqueue to the last ticket's completion: the device-side rate",
             "host_writes_positions_us": round(1e6 * dt_w / steps, 3),
             "host_writes_how": "the same, the host copying each step's 786 KB of positions into the slot's "
                                "page-locked array before enqueueing it",

@@ -139,18 +139,23 @@ pme_status pme_compute_host(pme_plan *plan, const float *pos, const float *q, in
 /* Paper: Sec. III (many timesteps without host round trips) with the host application of Fig. "MDOverview":
  * the asynchronous form of pme_compute_host. pos, q, forces (n x 3) and result (8 doubles) must all be
  * page-locked host memory (cudaHostAlloc / cudaHostRegister), else PME_EINVAL. Enqueues the evaluation and
- * returns: positions and charges are copied by the copy engine, on a stream of the plan's own, into one of
- * two device input slots (alternating per call) as soon as the evaluation that last used that slot has
- * finished, so the copy overlaps the evaluation still running on the plan stream; the plan stream waits
- * for the copy, runs the evaluation, and one copy kernel writes the forces and result[0..6] = (energy,
- * virial[6]) and result[7] = the device status bits (0: no error) into host memory. Each call may use its
- * own arrays, so a caller can keep several evaluations in flight (double buffering) and wait on the plan
- * stream for the oldest. All four arrays must stay allocated and unchanged until the plan stream has
- * completed the evaluation. The evaluation and copy
- * kernel of each argument set are recorded once as a CUDA graph (the four most recent sets are kept). Not
- * callable while the plan stream is being captured into a graph. */
+ * returns its ticket in *ticket (may be NULL; tickets count the plan's calls from 0). The plan keeps two
+ * device slots (positions, charges, forces), used alternately: on a stream of the plan's own the copy
+ * engine brings the inputs into the slot once the evaluation that last used it has finished; the plan
+ * stream waits for them and evaluates; then the copy engine takes the forces and result[0..6] = (energy,
+ * virial[6]), result[7] = the device status bits (0: no error) out on a second stream of the plan's own. So
+ * the copies of one evaluation overlap the evaluation before or after it. The results of ticket t are in host
+ * memory once pme_host_wait(plan, t) returns (or pme_sync). A caller keeps evaluations in flight on several
+ * sets of arrays and waits for the older ticket before reusing its set. Each slot's evaluation is recorded
+ * once as a CUDA graph, whatever host arrays the calls name. All four arrays
+ * must stay allocated and unchanged until the ticket has completed. Not callable while the plan stream is
+ * being captured into a graph. */
 pme_status pme_enqueue_host(pme_plan *plan, const float *pos, const float *q, int64_t n, float *forces,
-                            double *result);
+                            double *result, int64_t *ticket);
+
+/* Blocks until the forces and result of pme_enqueue_host's ticket are in host memory. PME_EINVAL for a
+ * ticket the plan has not issued. Device errors are reported through result[7] (and by pme_sync). */
+pme_status pme_host_wait(pme_plan *plan, int64_t ticket);
 
 /* Paper: Sec. V-B and V-C, which time the stages of the pipeline separately (Table IV brackets the forward
  * and inverse FFTs with timestamps). */

@@ -17,13 +17,14 @@ constexpr int NT_TILE16 = 512; // with 8^3 / 16^3 tiles
 PME_HD int tile_nt_bound(int T) { return T >= 16 ? NT_TILE16 : NT_TILE; }
 // Spread / gather CTA size for a system whose binned atoms number about n_bins * BIN_CHUNK: two threads per
 // atom, sized to the mean tile occupancy, so sparse 8^3 tiles (large meshes) do not leave half the CTA idle
-// and twice as many CTAs fit on an SM. 16^3 tiles (hundreds of atoms each): 512 threads for spreading, 256
-// for force interpolation, whose 106 registers per thread (p = 6) would otherwise leave one CTA per SM
-// (128^3, p = 6: spread 50.8 vs 52.2 us, gather 45.4 vs 49.2 us). Results do not depend on it.
+// and twice as many CTAs fit on an SM. 16^3 tiles (hundreds of atoms each): 512 threads for spreading, 128
+// for force interpolation, whose 106 registers per thread (p = 6) leave room for four 128-thread CTAs per
+// SM but only one 512-thread CTA, so all tiles of a 128^3 mesh fit in one wave (128^3, p = 6: 131.6 vs
+// 133.6 us per evaluation with 256 threads, 145.4 with 512). Results do not depend on it.
 inline int tile_threads(const SysDev &d, int64_t n, bool gather = false) {
     if (d.nt_tile == 128 || d.nt_tile == NT_TILE || (d.nt_tile == NT_TILE16 && d.tlog >= 4))
         return d.nt_tile;  // chosen by the autotuner or the caller
-    if (d.tlog >= 4) return gather ? NT_TILE : NT_TILE16;
+    if (d.tlog >= 4) return gather ? 128 : NT_TILE16;
     return (d.ntiles > 0 && n <= (int64_t)64 * d.ntiles) ? 128 : NT_TILE;
 }
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage

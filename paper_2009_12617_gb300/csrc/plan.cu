@@ -408,6 +408,11 @@ pme_status pme_enqueue(pme_plan *pl, const float *pos, const float *q, int64_t n
 pme_status pme_sync(pme_plan *pl) {
     if (!pl) return fail(PME_EINVAL, "plan is NULL");
     DeviceGuard g(pl->dev);
+    for (cudaStream_t cs : {pl->copy_stream, pl->out_stream})  // pme_enqueue_host's copies
+        if (cs) {
+            cudaError_t e = cudaStreamSynchronize(cs);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        }
     return collect_status(pl, false);
 }
 
@@ -456,28 +461,38 @@ pme_status pme_compute_debug(pme_plan *pl, const float *pos, const float *q, int
     return PME_OK;
 }
 
-// pme_enqueue_host's two input slots (device positions and charges) for at least n atoms, the copy stream
-// and the slot events.
+// One slot of pme_enqueue_host's device buffers: positions, forces, charges for m atoms, then the result
+// (energy, virial, status: 8 doubles).
+static size_t async_slot_bytes(int64_t m) { return 2 * align256((size_t)m * 12) + align256((size_t)m * 4) + 256; }
+
+// pme_enqueue_host's two slots (device positions, charges and forces) for at least n atoms, the copy stream
+// and the events.
 static pme_status ensure_async_inputs(pme_plan *pl, int64_t n) {
     cudaError_t e;
-    if (!pl->copy_stream && (e = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
-        pl->copy_stream = nullptr;
-        return cuda_fail(e, "cudaStreamCreate");
-    }
+    for (cudaStream_t *cs : {&pl->copy_stream, &pl->out_stream})
+        if (!*cs && (e = cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking)) != cudaSuccess) {
+            *cs = nullptr;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
     for (int s = 0; s < 2; ++s)
-        for (cudaEvent_t *ev : {&pl->in_ready[s], &pl->in_free[s]})
+        for (cudaEvent_t *ev : {&pl->in_ready[s], &pl->in_free[s], &pl->out_done[s]})
             if (!*ev && (e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) {
                 *ev = nullptr;
                 return cuda_fail(e, "cudaEventCreate");
             }
+    for (cudaEvent_t &ev : pl->host_done)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            ev = nullptr;
+            return cuda_fail(e, "cudaEventCreate");
+        }
     if (n <= pl->async_cap && pl->async_mem) return PME_OK;
-    if ((e = cudaStreamSynchronize(pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    if ((e = cudaStreamSynchronize(pl->copy_stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    for (cudaStream_t cs : {pl->stream, pl->copy_stream, pl->out_stream})
+        if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     if (pl->async_mem) cudaFree(pl->async_mem);
     pl->async_mem = nullptr;
     pl->async_cap = 0;
     const int64_t m = n > 0 ? n : 1;
-    const size_t bytes = 2 * (align256((size_t)m * 12) + align256((size_t)m * 4));
+    const size_t bytes = 2 * async_slot_bytes(m);
     if ((e = lib_malloc(&pl->async_mem, bytes)) != cudaSuccess) {
         pl->async_mem = nullptr;
         return fail(PME_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
@@ -491,28 +506,32 @@ static pme_status ensure_async_inputs(pme_plan *pl, int64_t n) {
     return PME_OK;
 }
 
-static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *forces,
-                                     float *mfor, double *result, double *mres);
+static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *dfor,
+                                     double *dres);
 
-pme_status pme_enqueue_host(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *result) {
+pme_status pme_enqueue_host(pme_plan *pl, const float *pos, const float *q, int64_t n, float *forces, double *result,
+                            int64_t *ticket) {
     pme_status st = check_atoms(pl, pos, q, n, forces);
     if (st) return st;
     if (!result) return fail(PME_EINVAL, "result must be non-NULL");
     DeviceGuard g(pl->dev);
     if ((st = plan_reserve(pl, n)) != PME_OK) return st;
-    if ((st = ensure_host_staging(pl, n)) != PME_OK) return st;
     if ((st = ensure_async_inputs(pl, n)) != PME_OK) return st;
-    float *mfor = n > 0 ? (float *)device_view(forces) : nullptr;
-    double *mres = (double *)device_view(result);
-    if (!mres || (n > 0 && (!device_view(pos) || !device_view(q) || !mfor)))
+    if (!device_view(result) || (n > 0 && (!device_view(pos) || !device_view(q) || !device_view(forces))))
         return fail(PME_EINVAL, "pme_enqueue_host needs page-locked pos, q, forces and result (cudaHostAlloc / cudaHostRegister)");
-    // the inputs go to the next slot by the copy engine on the copy stream, once the evaluation that last
-    // read that slot has finished; the plan stream waits for them, so the copies overlap the evaluation
-    // still running there
+    // Slot s (alternating): the copy engine brings the inputs in on the copy stream once the evaluation that
+    // last used the slot has finished; the plan stream waits for them (and for the slot's previous results to
+    // have left) and evaluates into the slot's device forces and result (the graph of the slot, the same
+    // whatever host arrays the call names); then the copy engine takes forces and result out on the output
+    // stream. Each copy overlaps the evaluation running on the plan stream at the time.
     const int slot = pl->async_slot;
     pl->async_slot ^= 1;
-    char *sb = (char *)pl->async_mem + (size_t)slot * (align256((size_t)pl->async_cap * 12) + align256((size_t)pl->async_cap * 4));
-    float *dpos = (float *)sb, *dq = (float *)(sb + align256((size_t)pl->async_cap * 12));
+    char *sb = (char *)pl->async_mem + (size_t)slot * async_slot_bytes(pl->async_cap);
+    float *dpos = (float *)sb, *dfor = (float *)(sb + align256((size_t)pl->async_cap * 12));
+    float *dq = (float *)(sb + 2 * align256((size_t)pl->async_cap * 12));
+    double *dres = (double *)(sb + 2 * align256((size_t)pl->async_cap * 12) + align256((size_t)pl->async_cap * 4));
+    const int64_t t = pl->host_seq;
+    cudaEvent_t done = pl->host_done[t % pme_plan::HOST_TICKETS];
     cudaError_t e;
     if ((e = cudaStreamWaitEvent(pl->copy_stream, pl->in_free[slot], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
     if (n > 0) {
@@ -523,25 +542,44 @@ pme_status pme_enqueue_host(pme_plan *pl, const float *pos, const float *q, int6
     }
     if ((e = cudaEventRecord(pl->in_ready[slot], pl->copy_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaStreamWaitEvent(pl->stream, pl->in_ready[slot], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-    if ((st = launch_async_graph(pl, dpos, dq, n, forces, mfor, result, mres)) != PME_OK) return st;
+    if ((e = cudaStreamWaitEvent(pl->stream, pl->out_done[slot], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    if ((st = launch_async_graph(pl, dpos, dq, n, dfor, dres)) != PME_OK) return st;
     if ((e = cudaEventRecord(pl->in_free[slot], pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaStreamWaitEvent(pl->out_stream, pl->in_free[slot], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    if (n > 0 && (e = cudaMemcpyAsync(forces, dfor, (size_t)n * 12, cudaMemcpyDeviceToHost, pl->out_stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(forces)");
+    if ((e = cudaMemcpyAsync(result, dres, 8 * sizeof(double), cudaMemcpyDeviceToHost, pl->out_stream)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(result)");
+    if ((e = cudaEventRecord(pl->out_done[slot], pl->out_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaEventRecord(done, pl->out_stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    pl->host_seq = t + 1;
+    if (ticket) *ticket = t;
     return PME_OK;
 }
 
-// The evaluation of pme_enqueue_host on device inputs dpos / dq and the copy of its forces, energy, virial
-// and status to page-locked host memory (device-side addresses mfor / mres), as a graph recorded once per
-// argument set (the four most recent kept).
-static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *forces,
-                                     float *mfor, double *result, double *mres) {
-    float *dfor = (float *)((char *)pl->host_mem + align256((size_t)pl->host_cap * 12));
+pme_status pme_host_wait(pme_plan *pl, int64_t ticket) {
+    if (!pl) return fail(PME_EINVAL, "plan is NULL");
+    if (ticket < 0 || ticket >= pl->host_seq) return fail(PME_EINVAL, "no pme_enqueue_host call has ticket %lld", (long long)ticket);
+    DeviceGuard g(pl->dev);
+    // the event of an older ticket may have been recorded again for a newer one; the copy stream runs in
+    // order, so waiting for the newer one covers it
+    cudaError_t e = cudaEventSynchronize(pl->host_done[ticket % pme_plan::HOST_TICKETS]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    return PME_OK;
+}
+
+// The evaluation of pme_enqueue_host on slot buffers dpos / dq / dfor and the copy of its energy, virial and
+// status to the slot's dres, as a graph recorded once per slot (and atom count; the four most recent kept).
+static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *dfor,
+                                     double *dres) {
     const SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, nullptr);
     pme_plan::EvalGraph key;
     key.pos = dpos;
     key.q = dq;
-    key.forces = forces;
+    key.forces = dfor;
     key.atoms = pl->atom_mem;
-    key.staging = pl->host_mem;
-    key.result = result;
+    key.staging = pl->async_mem;
+    key.result = dres;
     key.n = n;
     key.mode = launch_mode();
     key.gen = pl->gen;
@@ -558,7 +596,7 @@ static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const floa
     if ((e = cudaStreamBeginCapture(pl->rec_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
     cudaError_t r = launch_pipeline(d, pl->rec_stream);
-    if (r == cudaSuccess) r = launch_copy_out(dfor, mfor, (long long)n * 3, pl->d.ctl, nullptr, pl->rec_stream, mres);
+    if (r == cudaSuccess) r = launch_copy_out(nullptr, nullptr, 0, pl->d.ctl, nullptr, pl->rec_stream, dres);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(pl->rec_stream, &graph);
     if (r != cudaSuccess || e != cudaSuccess) {
@@ -710,7 +748,7 @@ size_t pme_plan_device_bytes(const pme_plan *pl) {
     if (!pl) return 0;
     size_t b = pl->mesh_bytes + pl->atom_bytes;
     if (pl->host_mem) b += align256((size_t)pl->host_cap * 12) * 2 + align256((size_t)pl->host_cap * 4);
-    if (pl->async_mem) b += 2 * (align256((size_t)pl->async_cap * 12) + align256((size_t)pl->async_cap * 4));
+    if (pl->async_mem) b += 2 * async_slot_bytes(pl->async_cap);
     return b;
 }
 
@@ -726,13 +764,16 @@ void pme_destroy(pme_plan *pl) {
     if (pl->md_mem) cudaFree(pl->md_mem);
     if (pl->tc_w) cudaFree(pl->tc_w);
     if (pl->rec_stream) cudaStreamDestroy(pl->rec_stream);
-    if (pl->copy_stream) {
-        cudaStreamSynchronize(pl->copy_stream);
-        cudaStreamDestroy(pl->copy_stream);
-    }
+    for (cudaStream_t cs : {pl->copy_stream, pl->out_stream})
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
     for (int s = 0; s < 2; ++s)
-        for (cudaEvent_t ev : {pl->in_ready[s], pl->in_free[s]})
+        for (cudaEvent_t ev : {pl->in_ready[s], pl->in_free[s], pl->out_done[s]})
             if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : pl->host_done)
+        if (ev) cudaEventDestroy(ev);
     if (pl->async_mem) cudaFree(pl->async_mem);
     if (pl->mesh_mem) cudaFree(pl->mesh_mem);
     if (pl->atom_mem) cudaFree(pl->atom_mem);

@@ -57,8 +57,12 @@ struct pme_plan {
     void *async_mem = nullptr;
     int64_t async_cap = 0;
     int async_slot = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr, out_stream = nullptr;  // copies in / out
+    cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr}, out_done[2] = {nullptr, nullptr};
+    // completion of each ticket's force copy to host memory (ticket t: host_done[t % HOST_TICKETS])
+    static constexpr int HOST_TICKETS = 8;
+    cudaEvent_t host_done[HOST_TICKETS] = {};
+    int64_t host_seq = 0;
     cudaStream_t rec_stream = nullptr;
     // multi-step loop (pme_run_steps): step counter and real-space energies, and the recorded graph of one
     // chunk of steps for the last argument set

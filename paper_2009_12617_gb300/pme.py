@@ -44,7 +44,7 @@ EXPORTS = ("pme_create", "pme_set_box", "pme_compute", "pme_compute_debug", "pme
            "pme_plan_get_tiling", "pme_batch_autotune", "pme_run_steps", "pme_debug_fail_alloc",
            "pme_set_influence_path", "pme_get_influence_path", "pme_slab_create", "pme_slab_layout",
            "pme_slab_stage1", "pme_slab_stage2", "pme_slab_stage3", "pme_slab_sync", "pme_slab_destroy",
-           "pme_enqueue_host")
+           "pme_enqueue_host", "pme_host_wait")
 
 
 PME_TUNE_FORCE = 1
@@ -133,7 +133,8 @@ def load_library(path: str | None = None):
         "pme_reserve": (_st, [_vp, _i64]),
         "pme_sync": (_st, [_vp]),
         "pme_compute_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, _vp]),
-        "pme_enqueue_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp]),
+        "pme_enqueue_host": (_st, [_vp, _vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_i64)]),
+        "pme_host_wait": (_st, [_vp, _i64]),
         "pme_profile_stages": (_st, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "pme_set_launch_mode": (_st, [ctypes.c_int]),
         "pme_set_slab_split": (_st, [ctypes.c_int, ctypes.c_int]),
@@ -278,16 +279,23 @@ def pme_sync(plan: int) -> None:
     check(load_library().pme_sync(_vp(plan)))
 
 
-def pme_enqueue_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray, result: np.ndarray) -> None:
+def pme_enqueue_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray, result: np.ndarray) -> int:
     """Asynchronous evaluation on page-locked numpy arrays (pos (n,3), q (n,), forces (n,3) float32; result (8,)
-    float64 receives energy, virial[6] and the status bits when the plan stream completes the evaluation)."""
+    float64 receives energy, virial[6] and the status bits); returns the ticket to pass to pme_host_wait."""
     for name, a, dt in (("pos", pos, np.float32), ("q", q, np.float32), ("forces", forces, np.float32),
                         ("result", result, np.float64)):
         if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
             raise ValueError(f"{name} must be a contiguous {np.dtype(dt).name} array")
     n = int(q.shape[0])
+    t = ctypes.c_int64()
     check(load_library().pme_enqueue_host(_vp(plan), _vp(_addr(pos)), _vp(_addr(q)), n, _vp(_addr(forces)),
-                                          _vp(_addr(result))))
+                                          _vp(_addr(result)), ctypes.byref(t)))
+    return t.value
+
+
+def pme_host_wait(plan: int, ticket: int) -> None:
+    """Block until pme_enqueue_host's ticket has its forces and result in host memory."""
+    check(load_library().pme_host_wait(_vp(plan), int(ticket)))
 
 
 def pme_compute_host(plan: int, pos: np.ndarray, q: np.ndarray, forces: np.ndarray | None = None):

@@ -416,24 +416,26 @@ def test_enqueue_host_double_buffered(pmelib):
     plan = pmelib.pme_create(s.K, s.p, s.beta, s.box, stream=stream)
     ref = pmelib.pme_create(s.K, s.p, s.beta, s.box)
     try:
-        events = [None, None]
+        tickets = [None, None]
         got = [None] * len(frames)
         for i, fr in enumerate(frames + [None, None]):
             slot = i % 2
-            if events[slot] is not None:  # the evaluation of frame i - 2 is done: read it
-                events[slot].synchronize()
+            if tickets[slot] is not None:  # the evaluation of frame i - 2: wait for its ticket, read it
+                pmelib.pme_host_wait(plan, tickets[slot])
                 P, Q, F, R = bufs[slot]
                 got[i - 2] = (F.copy(), R.copy())
+                tickets[slot] = None
             if fr is None:
                 continue
             P, Q, F, R = bufs[slot]
             P[:] = fr
             R[:] = np.nan
-            pmelib.pme_enqueue_host(plan, P, Q, F, R)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-            events[slot] = ev
+            F[:] = np.nan
+            tickets[slot] = pmelib.pme_enqueue_host(plan, P, Q, F, R)
+            assert tickets[slot] == i
         pmelib.pme_sync(plan)
+        with pytest.raises(pmelib.PMEError):
+            pmelib.pme_host_wait(plan, len(frames))  # not issued
         for i, fr in enumerate(frames):
             F2, E2, V2 = pmelib.pme_compute_host(ref, fr.copy(), s.q.copy())
             F, R = got[i]
