@@ -185,6 +185,7 @@ struct SysDev {
     int2 *bkb;                   // bucket records (packed base, atom index)
     unsigned *bcount;            // atoms binned per tile, at tile * BCOUNT_STRIDE
     unsigned long long *qslot;   // QABS_SLOTS sums of |q| (2^-24 e units), at slot * 16
+    int ev_status;               // 1: the final reduction also stores the status bits, as a double, in ev[7]
     float4 *ova;                 // overflow records, capacity n
     int2 *ovb;
     double *partials;            // 8 double-float (hi, lo) slots per influence-stage item, then K1 level-1 slots

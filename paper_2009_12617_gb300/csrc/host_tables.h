@@ -158,6 +158,7 @@ inline void fill_geometry(SysDev &d, const int K[3], int p, double beta, const d
     d.item0 = 0;
     d.k1_lo = 0;
     d.k1_hi = K[0];
+    d.ev_status = 0;
     set_tiling(d, TILE_MIN_LOG);
     choose_fft_paths(d, LANE_FFT_DEFAULT);
     for (int a = 0; a < 3; ++a) d.kinv[a] = 1.0f / (float)K[a];

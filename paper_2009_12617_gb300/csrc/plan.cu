@@ -568,11 +568,13 @@ pme_status pme_host_wait(pme_plan *pl, int64_t ticket) {
     return PME_OK;
 }
 
-// The evaluation of pme_enqueue_host on slot buffers dpos / dq / dfor and the copy of its energy, virial and
-// status to the slot's dres, as a graph recorded once per slot (and atom count; the four most recent kept).
+// The evaluation of pme_enqueue_host on slot buffers dpos / dq / dfor, its energy, virial and status bits
+// into the slot's dres, as a graph recorded once per slot (and atom count; the four most recent kept).
 static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const float *dq, int64_t n, float *dfor,
                                      double *dres) {
-    const SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, nullptr);
+    // the force stage's final reduction writes energy, virial and the status bits straight into dres
+    SysDev d = plan_descriptor(pl, dpos, dq, n, dfor, dres);
+    d.ev_status = 1;
     pme_plan::EvalGraph key;
     key.pos = dpos;
     key.q = dq;
@@ -589,14 +591,13 @@ static pme_status launch_async_graph(pme_plan *pl, const float *dpos, const floa
             if ((e = cudaGraphLaunch(gr.exec, pl->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
             return PME_OK;
         }
-    // first use of these arguments: record the evaluation and the copy kernel as a graph (on the private
-    // stream, so the plan stream may itself be capturing or busy), then launch it
+    // first use of this slot: record the evaluation as a graph (on the private stream, so the plan stream may
+    // itself be busy), then launch it
     if (!pl->rec_stream && (e = cudaStreamCreateWithFlags(&pl->rec_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamCreate");
     if ((e = cudaStreamBeginCapture(pl->rec_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
     cudaError_t r = launch_pipeline(d, pl->rec_stream);
-    if (r == cudaSuccess) r = launch_copy_out(nullptr, nullptr, 0, pl->d.ctl, nullptr, pl->rec_stream, dres);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(pl->rec_stream, &graph);
     if (r != cudaSuccess || e != cudaSuccess) {

@@ -737,6 +737,8 @@ PME_DEV void reduce_level2(const SysDev &d, void *smem) {
         for (int c = 0; c < 7; ++c) d.ev[c] = (double)t[c].hi + (double)t[c].lo;
     // the sum of |q| over the binning slots (exact integers): past the fixed-point headroom -> overflow;
     // the slots go back to zero for the next binning
+    // (every stage that may set status bits but this one has completed, so with ev_status the word stored
+    // in ev[7] is final)
 #if defined(PME_HOST_EMULATION)
     if (tid == 0) {
         unsigned long long qa = 0;
@@ -745,6 +747,7 @@ PME_DEV void reduce_level2(const SysDev &d, void *smem) {
             d.qslot[(size_t)sl * 16] = 0ull;
         }
         if (qa >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+        if (d.ev_status) d.ev[7] = (double)d.ctl->status;
     }
 #else
     if (tid < 32) {
@@ -752,7 +755,10 @@ PME_DEV void reduce_level2(const SysDev &d, void *smem) {
         qa = warp_sum_u64(qa);
         d.qslot[(size_t)tid * 16] = 0ull;
         d.qslot[(size_t)(tid + 32) * 16] = 0ull;
-        if (tid == 0 && qa >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+        if (tid == 0) {
+            if (qa >= QABS_LIMIT) atomic_or_u32(&d.ctl->status, ST_OVERFLOW);
+            if (d.ev_status) d.ev[7] = (double)(ldcg(&d.ctl->status) | (qa >= QABS_LIMIT ? (unsigned)ST_OVERFLOW : 0u));
+        }
     }
 #endif
     PME_SYNC();
