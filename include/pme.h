@@ -239,7 +239,8 @@ pme_status pme_compute_noalloc(const int K[3], int p, double beta, const double 
  * fixed order), so tuning changes only speed. */
 typedef struct {
     int tile_edge;       /* chosen tile edge (8 or 16 mesh points) */
-    int tile_threads;    /* chosen spread / force CTA size (128, 256, or 512 with 16^3 tiles) */
+    int tile_threads;    /* chosen spread / force CTA size (0: the default sizes, which differ per stage;
+                          * else 128, 256, or 512 with 16^3 tiles, for both stages) */
     double us_per_eval;  /* its time per evaluation (0 when taken from the cache) */
     double default_us;   /* the default configuration's time (0 when taken from the cache) */
     int candidates;      /* configurations tried */
@@ -262,8 +263,9 @@ pme_status pme_autotune(pme_plan *plan, const float *pos, const float *q, int64_
 pme_status pme_tune_cache(const char *path);
 
 /* Set the plan's tile edge (0 = default: 16 where the 16^3 tiling has at least two tiles per SM and about
- * 256 atoms per tile or more, else 8) and spread / force CTA size (0 = by atom density, 128 or 256, or 512
- * with tile edge 16) by hand; the current configuration is reported by pme_plan_get_tiling. Batches built on
+ * 256 atoms per tile or more, else 8) and spread / force CTA size (0 = the defaults, chosen per stage by
+ * tile edge and atom density; else 128 or 256, or 512 with tile edge 16, for both stages) by hand; the
+ * current configuration is reported by pme_plan_get_tiling (tile_threads 0: the defaults). Batches built on
  * the plan pick the change up at their next pme_batch_enqueue. */
 pme_status pme_plan_set_tiling(pme_plan *plan, int tile_edge, int tile_threads);
 pme_status pme_plan_get_tiling(const pme_plan *plan, int *tile_edge, int *tile_threads);

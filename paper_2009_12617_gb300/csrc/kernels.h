@@ -17,7 +17,10 @@ constexpr int NT_TILE16 = 512; // with 8^3 / 16^3 tiles
 PME_HD int tile_nt_bound(int T) { return T >= 16 ? NT_TILE16 : NT_TILE; }
 // Spread / gather CTA size for a system whose binned atoms number about n_bins * BIN_CHUNK: two threads per
 // atom, sized to the mean tile occupancy, so sparse 8^3 tiles (large meshes) do not leave half the CTA idle
-// and twice as many CTAs fit on an SM. 16^3 tiles (hundreds of atoms each): 512 threads for spreading, 128
+// and twice as many CTAs fit on an SM. Dense 8^3 tiles interpolate forces on 192 threads: at 64 registers,
+// five such CTAs fit on an SM, three beside an inverse-stage CTA that has not retired yet, so all tiles of
+// a 64^3 mesh are dispatched at once (with 256 threads, 13-15 SMs ran a fifth tile in a second wave; 28.65
+// vs 28.75 us per evaluation). 16^3 tiles (hundreds of atoms each): 512 threads for spreading, 128
 // for force interpolation, whose 106 registers per thread (p = 6) leave room for four 128-thread CTAs per
 // SM but only one 512-thread CTA, so all tiles of a 128^3 mesh fit in one wave (128^3, p = 6: 131.6 vs
 // 133.6 us per evaluation with 256 threads, 145.4 with 512). Results do not depend on it.
@@ -25,7 +28,8 @@ inline int tile_threads(const SysDev &d, int64_t n, bool gather = false) {
     if (d.nt_tile == 128 || d.nt_tile == NT_TILE || (d.nt_tile == NT_TILE16 && d.tlog >= 4))
         return d.nt_tile;  // chosen by the autotuner or the caller
     if (d.tlog >= 4) return gather ? 128 : NT_TILE16;
-    return (d.ntiles > 0 && n <= (int64_t)64 * d.ntiles) ? 128 : NT_TILE;
+    if (d.ntiles > 0 && n <= (int64_t)64 * d.ntiles) return 128;
+    return gather ? 192 : NT_TILE;
 }
 constexpr int NT_CONV = 128;   // threads per CTA for the influence stage
 constexpr size_t MAX_SMEM_BYTES = 226 * 1024;  // opt-in limit is 227 KB including static shared memory

@@ -270,7 +270,7 @@ pme_status pme_plan_set_tiling(pme_plan *pl, int tile_edge, int tile_threads) {
 pme_status pme_plan_get_tiling(const pme_plan *pl, int *tile_edge, int *tile_threads) {
     if (!pl) return fail(PME_EINVAL, "plan is NULL");
     if (tile_edge) *tile_edge = 1 << pl->d.tlog;
-    if (tile_threads) *tile_threads = pme::tile_threads(pl->d, pl->n_cap);
+    if (tile_threads) *tile_threads = pl->d.nt_tile;  // 0: the per-stage default sizes
     return PME_OK;
 }
 
@@ -285,7 +285,7 @@ pme_status pme_autotune(pme_plan *pl, const float *pos, const float *q, int64_t 
     if (!(flags & PME_TUNE_FORCE) && tune_apply_cached(pl, n, &st)) {
         if (st != PME_OK) return st;
         res.tile_edge = 1 << pl->d.tlog;
-        res.tile_threads = tile_threads(pl->d, n);
+        res.tile_threads = pl->d.nt_tile;
         res.from_cache = 1;
         if (out) *out = res;
         return PME_OK;
@@ -293,9 +293,8 @@ pme_status pme_autotune(pme_plan *pl, const float *pos, const float *q, int64_t 
     // candidates: the default first (its results are the reference bits), then every other combination
     const int tdef = pl->tile_log_set ? pl->tile_log_set : choose_tile_log(n > 0 ? n : 1, pl->K, pl->sms);
     if ((st = plan_retile(pl, tdef, 0, n)) != PME_OK) return st;
-    // the default sizes: one CTA size for 8^3 tiles; for 16^3 tiles spreading and force interpolation
-    // differ (nt = 0 keeps that per-stage default)
-    const int ntdef = tdef == 4 ? 0 : tile_threads(pl->d, n);
+    // the default sizes (nt = 0): spreading and force interpolation take different CTA sizes
+    const int ntdef = 0;
     struct Cand { int tlog, nt; double us; bool same; };
     std::vector<Cand> cands = {{tdef, ntdef, 0.0, true}};
     for (int tlog : {3, 4})
@@ -319,7 +318,7 @@ pme_status pme_autotune(pme_plan *pl, const float *pos, const float *q, int64_t 
     pl->tuned_apt = apt_class(pl->K, n);
     tune_record(pl, n, cands[best].tlog, cands[best].nt, cands[best].us);
     res.tile_edge = 1 << cands[best].tlog;
-    res.tile_threads = tile_threads(pl->d, n);
+    res.tile_threads = cands[best].nt;
     res.us_per_eval = cands[best].us;
     res.default_us = cands[0].us;
     if (out) *out = res;

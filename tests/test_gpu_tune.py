@@ -79,8 +79,9 @@ def test_autotune_picks_and_persists(pme, tmp_path):
             E0, V0 = pme.pme_compute(plan, P, Q, F0)
             F = torch.empty_like(P)
             res = pme.pme_autotune(plan, P, Q, F, reps=20)
-            assert res["candidates"] == 4 and res["rejected"] == 0 and res["from_cache"] == 0
-            assert (res["tile_edge"], res["tile_threads"]) in ((8, 128), (8, 256), (16, 256), (16, 512))
+            assert res["candidates"] == 5 and res["rejected"] == 0 and res["from_cache"] == 0
+            assert (res["tile_edge"], res["tile_threads"]) in ((8, 0), (16, 0), (8, 128), (8, 256), (16, 256),
+                                                                (16, 512))
             assert 0 < res["us_per_eval"] <= res["default_us"]
             assert pme.pme_plan_get_tiling(plan) == (res["tile_edge"], res["tile_threads"])
             E, V = pme.pme_compute(plan, P, Q, F)
