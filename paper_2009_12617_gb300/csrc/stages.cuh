@@ -35,20 +35,68 @@ struct Region {
 // H0 = ceil(P / 2) (equal halves for even orders, one plane more in half 0 for odd ones).
 PME_HD int half_planes(int P) { return (P + 1) / 2; }
 
-// Spreading region layout: planes of R x R points padded to PL so that the two half-support lanes of an
-// atom (H0 planes apart) sit 16 banks apart: H0 PL = 16 (mod 32). Then the 32 lanes of a warp (16 atoms x 2
-// halves) hit distinct banks whenever the atoms' base addresses differ mod 16, which the dealt processing
-// order (stage_spread) arranges.
-constexpr int spread_plane(int R, int P) {
+// Spreading region layout: R planes of R rows of R points, rows RS apart and planes PL apart.
+//
+// P = 4 with 8^3 tiles (spread_warp_lanes): one warp takes one atom at a time, lane (jA, j2, j3) =
+// (lane / 16, lane / 4 mod 4, lane mod 4) adding the points (jA, j2, j3) and (jA + 2, j2, j3) below the
+// atom's highest support point. RS and PL are padded until the 32 offsets jA PL + j2 RS + j3 fall in
+// distinct banks (mod 32), so every shared-memory atomic of the warp is conflict-free wherever the atom
+// sits (R = 11: RS = 12, PL = 144).
+//
+// Otherwise: two threads per atom split its planes (half_planes); rows are not padded (RS = R) and planes
+// are padded so that the two halves (H0 planes apart) sit 16 banks apart, H0 PL = 16 (mod 32). Then the 32
+// lanes of a warp (16 atoms x 2 halves) hit distinct banks whenever the atoms' base addresses differ mod
+// 16, which the dealt processing order (stage_spread) arranges.
+PME_HD bool spread_warp_lanes(int P, int tlog) { return P == 4 && tlog == 3; }
+PME_HD bool warp_lanes_distinct(int rs, int pl) {
+    unsigned seen = 0u;
+    for (int ja = 0; ja < 2; ++ja)
+        for (int j2 = 0; j2 < 4; ++j2)
+            for (int j3 = 0; j3 < 4; ++j3) {
+                const unsigned bit = 1u << ((ja * pl + j2 * rs + j3) & 31);
+                if (seen & bit) return false;
+                seen |= bit;
+            }
+    return true;
+}
+// the smallest RS >= R for which some PL in [R RS, R RS + 32) gives distinct lane banks, and the smallest
+// such PL (RS = 4 (mod 16) with PL = 16 (mod 32) always works, so the search ends within 16 steps)
+PME_HD int warp_row_stride(int R) {
+    for (int rs = R; rs < R + 16; ++rs)
+        for (int pl = R * rs; pl < R * rs + 32; ++pl)
+            if (warp_lanes_distinct(rs, pl)) return rs;
+    return -1;
+}
+PME_HD int warp_plane_stride(int R) {
+    const int rs = warp_row_stride(R);
+    for (int pl = R * rs; pl < R * rs + 32; ++pl)
+        if (warp_lanes_distinct(rs, pl)) return pl;
+    return -1;
+}
+PME_HD int spread_row(int P, int tlog) {
+    const int R = (1 << tlog) + P - 1;
+    return spread_warp_lanes(P, tlog) ? warp_row_stride(R) : R;
+}
+PME_HD int spread_plane(int P, int tlog) {
+    const int R = (1 << tlog) + P - 1;
+    if (spread_warp_lanes(P, tlog)) return warp_plane_stride(R);
     int pl = R * R;
     while ((half_planes(P) * pl) % 32 != 16) ++pl;
     return pl;
 }
+// Accumulator array length (R PL rounded up to 4 ints, so the record arrays after the two accumulators
+// stay 16-byte aligned) and record bytes per atom: the warp-lane path keeps the atom's weights (three
+// float4) and region index, the other the record (float4 + int2), the dealt order's key and inverse.
+PME_HD int spread_vol(int P, int tlog) { return (((1 << tlog) + P - 1) * spread_plane(P, tlog) + 3) / 4 * 4; }
+PME_HD int spread_rec_bytes(int P, int tlog) { return spread_warp_lanes(P, tlog) ? 3 * 16 + 4 : 16 + 8 + 4 + 4; }
 template <int P, int T>
 struct SpreadLayout {
+    static constexpr int TLOG = T >= 16 ? 4 : 3;
+    static constexpr bool WARP = spread_warp_lanes(P, TLOG);
     static constexpr int R = T + P - 1;
-    static constexpr int PL = spread_plane(R, P);
-    static constexpr int VOLP = R * PL;
+    static constexpr int RS = spread_row(P, TLOG);
+    static constexpr int PL = spread_plane(P, TLOG);
+    static constexpr int VOLP = spread_vol(P, TLOG);
     static constexpr int CAP = cap_max_for(T >= 16 ? 4 : 3);  // record slots
 };
 
@@ -60,11 +108,10 @@ inline size_t smem_tile_region(int p, int tlog) {
     const size_t r = (size_t)(1 << tlog) + p - 1;
     return r * r * r;
 }
-// split accumulators over the padded region (2 x R PL ints), the tile's records (cap x (float4 + int2)),
-// the dealt order's keys and inverse (cap ints each) and 16 residue counters; cap = cap_max_for(tlog)
+// split accumulators over the padded region (2 x spread_vol ints), cap = cap_max_for(tlog) records of
+// spread_rec_bytes and 16 residue counters
 inline size_t smem_spread(int p, int tlog) {
-    const int r = (1 << tlog) + p - 1;
-    return (size_t)2 * r * spread_plane(r, p) * sizeof(int) + (size_t)cap_max_for(tlog) * (16 + 8 + 4 + 4) +
+    return (size_t)2 * spread_vol(p, tlog) * sizeof(int) + (size_t)cap_max_for(tlog) * spread_rec_bytes(p, tlog) +
            16 * sizeof(unsigned);
 }
 inline size_t smem_gather(int p, int tlog) { return smem_tile_region(p, tlog) * sizeof(float); }
@@ -267,13 +314,20 @@ PME_DEV void spread_atom_global(const SysDev &d, float4 ra, int2 rb) {
     }
 }
 
-// Shared memory of a spreading tile (sizes as smem_spread): split accumulators over the padded region, the
-// tile's records, the dealt order's keys and inverse, and 16 residue counters.
+// Shared memory of a spreading tile (sizes as smem_spread): split accumulators over the padded region, then
+// per atom either its weights and region index (warp-lane path) or its record, the dealt order's key and
+// inverse, and 16 residue counters.
 template <int P, int T>
 struct SpreadSmem {
     static constexpr int VOLP = SpreadLayout<P, T>::VOLP;
+    static constexpr int CAP = SpreadLayout<P, T>::CAP;
     int *hi, *lo;
-    float4 *ra_s;    // the tile's records (16-byte aligned: VOLP is even)
+    // warp-lane path: rn(q th1[j]) 2^40 for j = 0, 2, 1, 3 (lane jA reads planes jA and jA + 2 as one pair),
+    // th2, th3, and the region index of the highest support point
+    float4 *u_s, *t2_s, *t3_s;
+    int *ix_s;
+    // two-thread path
+    float4 *ra_s;    // the tile's records (16-byte aligned: VOLP is a multiple of 4)
     int2 *rb_s;
     int *key_s;      // per atom: rank << 4 | residue
     int *inv_s;      // dealt position -> atom
@@ -281,12 +335,24 @@ struct SpreadSmem {
     PME_DEV explicit SpreadSmem(void *smem) {
         hi = (int *)smem;
         lo = hi + VOLP;
-        ra_s = (float4 *)(lo + VOLP);
-        constexpr int CAP = SpreadLayout<P, T>::CAP;
-        rb_s = (int2 *)(ra_s + CAP);
-        key_s = (int *)(rb_s + CAP);
-        inv_s = key_s + CAP;
-        bins = (unsigned *)(inv_s + CAP);
+        if (SpreadLayout<P, T>::WARP) {
+            u_s = (float4 *)(lo + VOLP);
+            t2_s = u_s + CAP;
+            t3_s = t2_s + CAP;
+            ix_s = (int *)(t3_s + CAP);
+            bins = (unsigned *)(ix_s + CAP);
+            ra_s = nullptr;
+            rb_s = nullptr;
+            key_s = inv_s = nullptr;
+        } else {
+            ra_s = (float4 *)(lo + VOLP);
+            rb_s = (int2 *)(ra_s + CAP);
+            key_s = (int *)(rb_s + CAP);
+            inv_s = key_s + CAP;
+            bins = (unsigned *)(inv_s + CAP);
+            u_s = t2_s = t3_s = nullptr;
+            ix_s = nullptr;
+        }
     }
 };
 
@@ -296,10 +362,40 @@ template <int P, int T>
 PME_DEV void spread_clear(void *smem) {
     const SpreadSmem<P, T> s(smem);
     for (int i = PME_TID; i < 16; i += PME_NTH) s.bins[i] = 0u;
-    for (int i = PME_TID; i < SpreadSmem<P, T>::VOLP; i += PME_NTH) {
-        s.hi[i] = 0;
-        s.lo[i] = 0;
-    }
+    int4 *z = (int4 *)s.hi;  // hi and lo are contiguous, 2 VOLP ints, VOLP a multiple of 4
+    for (int i = PME_TID; i < SpreadSmem<P, T>::VOLP / 2; i += PME_NTH) z[i] = make_int4(0, 0, 0, 0);
+}
+
+// One lane's share of an atom on the warp-lane path: points (jA, j2, j3) and (jA + 2, j2, j3) below the
+// atom's highest support point, jA = lane / 16, j2 = lane / 4 mod 4, j3 = lane mod 4. The value added is
+// rn(rn(rn(q th1) 2^40 th2) th3), equal to the two-thread and global paths' rn(rn(rn(q th1) th2) 2^40 th3)
+// (scaling by a power of two commutes with rounding; products too small for that to hold round to 0 in
+// both). Loading and adding are separate steps so that a warp can hold two atoms' weights in flight.
+struct Lane4 {
+    float2 u;  // rn(q th1) 2^40 of the planes jA, jA + 2
+    float t2, t3;
+    int i;     // region index of the point (jA, j2, j3)
+};
+template <int RS, int PL>
+PME_DEV Lane4 lane4_load(const float4 *u_s, const float4 *t2_s, const float4 *t3_s, const int *ix_s, int a,
+                         int lane) {
+    const int ja = lane >> 4, j2 = (lane >> 2) & 3, j3 = lane & 3;
+    Lane4 w;
+    w.u = ((const float2 *)(u_s + a))[ja];
+    w.t2 = ((const float *)(t2_s + a))[j2];
+    w.t3 = ((const float *)(t3_s + a))[j3];
+    w.i = ix_s[a] - (ja * PL + j2 * RS + j3);
+    return w;
+}
+template <int PL>
+PME_DEV void lane4_add(int *hi, int *lo, const Lane4 &w) {
+    int h, l;
+    fix_split((w.u.x * w.t2) * w.t3, h, l);
+    atomic_add_i32(hi + w.i, h);
+    atomic_add_i32(lo + w.i, l);
+    fix_split((w.u.y * w.t2) * w.t3, h, l);
+    atomic_add_i32(hi + w.i - 2 * PL, h);
+    atomic_add_i32(lo + w.i - 2 * PL, l);
 }
 
 // cleared: spread_clear already ran on this shared memory (and nothing has used it since). org: the tile's
@@ -315,7 +411,7 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
             spread_atom_global<P>(d, ldcg(d.ova + a), ldcg(d.ovb + a));
         return;
     }
-    constexpr int R = SpreadLayout<P, T>::R, PL = SpreadLayout<P, T>::PL, H = P - 1;
+    constexpr int R = SpreadLayout<P, T>::R, RS = SpreadLayout<P, T>::RS, PL = SpreadLayout<P, T>::PL, H = P - 1;
     const SpreadSmem<P, T> sm(smem);
     int *hi = sm.hi, *lo = sm.lo, *key_s = sm.key_s, *inv_s = sm.inv_s;
     float4 *ra_s = sm.ra_s;
@@ -343,86 +439,130 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
     const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
     if (!cleared) spread_clear<P, T>(smem);
     PME_SYNC();
-    // Dealt order: residue r = (base mod 16) of the atom's highest support point in the padded region;
-    // round k takes the k-th atom of every residue in turn, so 16 consecutive atoms (one warp) mostly have
-    // distinct residues and their shared-memory atomics do not share banks. Results do not depend on the
-    // order (integer sums).
-    for (int a = tid; a < cnt; a += nth) {
-        const bool first = pf && a == tid;
-        const float4 ra = first ? ra0 : ldcg(A + a);
-        const int2 rb = first ? rb0 : ldcg(B + a);
-        ra_s[a] = ra;
-        rb_s[a] = rb;
-        const int l1 = (rb.x & 1023) - o1 + H, l2 = ((rb.x >> 10) & 1023) - o2 + H, l3 = ((rb.x >> 20) & 1023) - o3 + H;
-        const int res = (l1 * PL + l2 * R + l3) & 15;
-        key_s[a] = ((int)atomic_add_u32(bins + res, 1u) << 4) | res;
-    }
-    PME_SYNC();
-    {
-        unsigned nb[16];
-#pragma unroll
-        for (int b = 0; b < 16; ++b) nb[b] = bins[b];
+    if constexpr (SpreadLayout<P, T>::WARP) {
+        // one thread per atom: its weights and the region index of its highest support point
         for (int a = tid; a < cnt; a += nth) {
-            const int key = key_s[a], res = key & 15;
-            const unsigned rk = (unsigned)(key >> 4);
-            unsigned pos = 0;
-#pragma unroll
-            for (int b = 0; b < 16; ++b) pos += (nb[b] < rk ? nb[b] : rk) + ((b < res && nb[b] > rk) ? 1u : 0u);
-            inv_s[pos] = a;
+            const bool first = pf && a == tid;
+            const float4 ra = first ? ra0 : ldcg(A + a);
+            const int2 rb = first ? rb0 : ldcg(B + a);
+            float th1[P], th2[P], th3[P];
+            bspline_w<P>(ra.x, th1);
+            bspline_w<P>(ra.y, th2);
+            bspline_w<P>(ra.z, th3);
+            const float qs = ra.w * FIX_SCALE;  // exact: a power of two
+            sm.u_s[a] = make_float4(qs * th1[0], qs * th1[2], qs * th1[1], qs * th1[3]);
+            sm.t2_s[a] = make_float4(th2[0], th2[1], th2[2], th2[3]);
+            sm.t3_s[a] = make_float4(th3[0], th3[1], th3[2], th3[3]);
+            sm.ix_s[a] = ((rb.x & 1023) - o1 + H) * PL + (((rb.x >> 10) & 1023) - o2 + H) * RS +
+                         (((rb.x >> 20) & 1023) - o3 + H);
         }
-    }
-    PME_SYNC();
-    // two threads per atom: half 0 takes the planes j1 in [0, H0), half 1 [H0, P)
-    constexpr int H0 = half_planes(P);
-    for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
-        const int a = inv_s[a2 >> 1], half = a2 & 1;
-        const float4 ra = ra_s[a];
-        const int2 rb = rb_s[a];
-        float th1[P], th2[P], th3[P];
-        bspline_w<P>(ra.x, th1);
-        bspline_w<P>(ra.y, th2);
-        bspline_w<P>(ra.z, th3);
-        // local index of the atom's highest support point; its points are l - j, j < P
-        const int l1 = (rb.x & 1023) - o1 + H;
-        const int l2 = ((rb.x >> 10) & 1023) - o2 + H;
-        const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
+        PME_SYNC();
+        // one warp per atom, its 64 points over the 32 lanes (two each, in distinct banks); each warp takes
+        // the atoms w, w + nw, ... two at a time, both atoms' weights loaded before either is added
+#if defined(PME_HOST_EMULATION)
+        for (int a = 0; a < cnt; ++a)
+            for (int lane = 0; lane < 32; ++lane)
+                lane4_add<PL>(hi, lo, lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a, lane));
+#else
+        const int nw = nth >> 5, lane = tid & 31;
+        int a = tid >> 5;
+        for (; a + nw < cnt; a += 2 * nw) {
+            const Lane4 w0 = lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a, lane);
+            const Lane4 w1 = lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a + nw, lane);
+            lane4_add<PL>(hi, lo, w0);
+            lane4_add<PL>(hi, lo, w1);
+        }
+        if (a < cnt) lane4_add<PL>(hi, lo, lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a, lane));
+#endif
+    } else {
+        // Dealt order: residue r = (base mod 16) of the atom's highest support point in the padded region;
+        // round k takes the k-th atom of every residue in turn, so 16 consecutive atoms (one warp) mostly have
+        // distinct residues and their shared-memory atomics do not share banks. Results do not depend on the
+        // order (integer sums).
+        for (int a = tid; a < cnt; a += nth) {
+            const bool first = pf && a == tid;
+            const float4 ra = first ? ra0 : ldcg(A + a);
+            const int2 rb = first ? rb0 : ldcg(B + a);
+            ra_s[a] = ra;
+            rb_s[a] = rb;
+            const int l1 = (rb.x & 1023) - o1 + H, l2 = ((rb.x >> 10) & 1023) - o2 + H,
+                      l3 = ((rb.x >> 20) & 1023) - o3 + H;
+            const int res = (l1 * PL + l2 * R + l3) & 15;
+            key_s[a] = ((int)atomic_add_u32(bins + res, 1u) << 4) | res;
+        }
+        PME_SYNC();
+        {
+            unsigned nb[16];
 #pragma unroll
-        for (int jj = 0; jj < H0; ++jj) {
-            if (half && jj >= P - H0) break;  // odd P: half 1 has one plane fewer
-            const int j1 = half * H0 + jj;
-            const float t1 = half ? th1[H0 + jj < P ? H0 + jj : P - 1] : th1[jj];
+            for (int b = 0; b < 16; ++b) nb[b] = bins[b];
+            for (int a = tid; a < cnt; a += nth) {
+                const int key = key_s[a], res = key & 15;
+                const unsigned rk = (unsigned)(key >> 4);
+                unsigned pos = 0;
 #pragma unroll
-            for (int j2 = 0; j2 < P; ++j2) {
-                // scaled row factor: rn(c 2^40 th3) = rn(c th3) 2^40 (a power of two; |v| < 2^62, and values
-                // small enough for the scaling to matter round to 0 either way), one multiply per point
-                const float c = ra.w * t1 * th2[j2] * FIX_SCALE;
-                const int row = (l1 - j1) * PL + (l2 - j2) * R + l3;
+                for (int b = 0; b < 16; ++b) pos += (nb[b] < rk ? nb[b] : rk) + ((b < res && nb[b] > rk) ? 1u : 0u);
+                inv_s[pos] = a;
+            }
+        }
+        PME_SYNC();
+        // two threads per atom: half 0 takes the planes j1 in [0, H0), half 1 [H0, P)
+        constexpr int H0 = half_planes(P);
+        for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
+            const int a = inv_s[a2 >> 1], half = a2 & 1;
+            const float4 ra = ra_s[a];
+            const int2 rb = rb_s[a];
+            float th1[P], th2[P], th3[P];
+            bspline_w<P>(ra.x, th1);
+            bspline_w<P>(ra.y, th2);
+            bspline_w<P>(ra.z, th3);
+            // local index of the atom's highest support point; its points are l - j, j < P
+            const int l1 = (rb.x & 1023) - o1 + H;
+            const int l2 = ((rb.x >> 10) & 1023) - o2 + H;
+            const int l3 = ((rb.x >> 20) & 1023) - o3 + H;
 #pragma unroll
-                for (int j3 = 0; j3 < P; ++j3) {
-                    int h, l;
-                    fix_split(c * th3[j3], h, l);
-                    atomic_add_i32(hi + row - j3, h);
-                    atomic_add_i32(lo + row - j3, l);
+            for (int jj = 0; jj < H0; ++jj) {
+                if (half && jj >= P - H0) break;  // odd P: half 1 has one plane fewer
+                const int j1 = half * H0 + jj;
+                const float t1 = half ? th1[H0 + jj < P ? H0 + jj : P - 1] : th1[jj];
+#pragma unroll
+                for (int j2 = 0; j2 < P; ++j2) {
+                    // scaled row factor: rn(c 2^40 th3) = rn(c th3) 2^40 (a power of two; |v| < 2^62, and values
+                    // small enough for the scaling to matter round to 0 either way), one multiply per point
+                    const float c = ra.w * t1 * th2[j2] * FIX_SCALE;
+                    const int row = (l1 - j1) * PL + (l2 - j2) * R + l3;
+#pragma unroll
+                    for (int j3 = 0; j3 < P; ++j3) {
+                        int h, l;
+                        fix_split(c * th3[j3], h, l);
+                        atomic_add_i32(hi + row - j3, h);
+                        atomic_add_i32(lo + row - j3, l);
+                    }
                 }
             }
         }
     }
     PME_SYNC();
-    // flush: thread t < ng R adds point i3 = t mod R of rows t / R, t / R + ng, ... (as the force stage's
-    // region load); rows of the planes i1 < R1 (the tile's k1 width plus the halo) only
+    // flush: thread t < ng R^2 takes the column (i2, i3) = (c / R, c mod R), c = t mod R^2, and adds its
+    // points of the planes i1 = t / R^2, t / R^2 + ng, ... below R1 (the tile's k1 width plus the halo):
+    // the column's mesh address is computed once, each plane costs one add and one wrap
+    constexpr int RR = R * R;
     const int R1 = tile_width1(d, o1) + H;
-    const int ng = nth >= R ? nth / R : 1, rg = nth >= R ? tid / R : 0;
-    for (int i3 = nth >= R ? tid - rg * R : 0; i3 < R; i3 += (nth >= R ? R : 1)) {
-        if (rg >= ng) break;
-        const int k3 = wrapk(o3 - H + i3, d.K3);
-        for (int r = rg; r < R1 * R; r += ng) {
-            const int i1 = r / R, i2 = r - i1 * R;
-            const int i = i1 * PL + i2 * R + i3;
-            const int h = hi[i], l = lo[i];
-            if ((h | l) == 0) continue;
-            const int k1 = wrapk(o1 - H + i1, d.K1), k2 = wrapk(o2 - H + i2, d.K2);
-            if (k1 < d.k1_lo || k1 >= d.k1_hi) continue;  // another rank's planes (slab decomposition)
-            red_add_u64(d.grid + ((size_t)k1 * d.K2 + k2) * d.K3 + k3, fix_join(h, l));
+    const int ng = nth >= RR ? nth / RR : 1, g = nth >= RR ? tid / RR : 0;
+    const size_t plane = (size_t)d.K2 * d.K3;
+    if (g < ng) {
+        for (int c = nth >= RR ? tid - g * RR : tid; c < RR; c += nth >= RR ? RR : nth) {
+            const int i2 = c / R, i3 = c - i2 * R;
+            unsigned long long *col = d.grid + (size_t)wrapk(o2 - H + i2, d.K2) * d.K3 + wrapk(o3 - H + i3, d.K3);
+            const int *hc = hi + i2 * RS + i3, *lc = lo + i2 * RS + i3;
+            int k1 = wrapk(o1 - H + g, d.K1);
+#pragma unroll 4
+            for (int i1 = g; i1 < R1; i1 += ng) {
+                const int h = hc[i1 * PL], l = lc[i1 * PL];
+                // k1 outside [k1_lo, k1_hi): another rank's planes (slab decomposition)
+                if ((h | l) != 0 && k1 >= d.k1_lo && k1 < d.k1_hi) red_add_u64(col + k1 * plane, fix_join(h, l));
+                k1 += ng;
+                if (k1 >= d.K1) k1 -= d.K1;
+            }
         }
     }
 }
@@ -1357,12 +1497,12 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
         }
         const float4 *A = d.bka + (size_t)item * d.cap;
         const int2 *B = d.bkb + (size_t)item * d.cap;
-        // the count and this thread's first record in flight with the region loads (the record slot is
-        // always inside the bucket; it is used only if it holds an atom)
+        // the count and this thread's first two records in flight with the region loads (the record slots
+        // are always inside the bucket; each is used only if it holds an atom)
         const int cnt = imin((int)ldcg(&d.bcount[(size_t)item * BCOUNT_STRIDE]), d.cap);
-        const int a0 = imin(tid >> 1, d.cap - 1);
-        const float4 ra0 = ldcg(A + a0);
-        const int2 rb0 = ldcg(B + a0);
+        const int a0 = imin(tid >> 1, d.cap - 1), a1 = imin((tid + nth) >> 1, d.cap - 1);
+        const float4 ra0 = ldcg(A + a0), ra1 = ldcg(A + a1);
+        const int2 rb0 = ldcg(B + a0), rb1 = ldcg(B + a1);
         const int R1 = tile_width1(d, o1) + H;  // planes of the region the tile's atoms reach
         if (nth >= R) {
             // thread t < ng R loads point i3 = t mod R of rows t / R, t / R + ng, ... (ng = nth / R row
@@ -1403,9 +1543,9 @@ PME_DEV void stage_gather(const SysDev &d, int item, void *smem, const int *org 
         constexpr int H0 = half_planes(P);
         for (int a2 = tid; a2 < 2 * cnt; a2 += nth) {
             const int a = a2 >> 1, half = a2 & 1;
-            const bool first = a2 == tid;
-            const float4 ra = first ? ra0 : ldcg(A + a);
-            const int2 rb = first ? rb0 : ldcg(B + a);
+            const bool first = a2 == tid, second = a2 == tid + nth;
+            const float4 ra = first ? ra0 : (second ? ra1 : ldcg(A + a));
+            const int2 rb = first ? rb0 : (second ? rb1 : ldcg(B + a));
             float th1[P], th2[P], th3[P], dth1[P], dth2[P], dth3[P];
             bspline_wd<P>(ra.x, th1, dth1);
             bspline_wd<P>(ra.y, th2, dth2);
