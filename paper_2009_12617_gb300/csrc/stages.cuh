@@ -374,29 +374,79 @@ PME_DEV void spread_clear(void *smem) {
 struct Lane4 {
     float2 u;  // rn(q th1) 2^40 of the planes jA, jA + 2
     float t2, t3;
-    int i;     // region index of the point (jA, j2, j3)
+    int i;     // region index of the point (jA, j2, j3); on the GPU its byte address in the shared window
 };
-template <int RS, int PL>
-PME_DEV Lane4 lane4_load(const float4 *u_s, const float4 *t2_s, const float4 *t3_s, const int *ix_s, int a,
-                         int lane) {
-    const int ja = lane >> 4, j2 = (lane >> 2) & 3, j3 = lane & 3;
-    Lane4 w;
-    w.u = ((const float2 *)(u_s + a))[ja];
-    w.t2 = ((const float *)(t2_s + a))[j2];
-    w.t3 = ((const float *)(t3_s + a))[j3];
-    w.i = ix_s[a] - (ja * PL + j2 * RS + j3);
-    return w;
-}
-template <int PL>
-PME_DEV void lane4_add(int *hi, int *lo, const Lane4 &w) {
-    int h, l;
-    fix_split((w.u.x * w.t2) * w.t3, h, l);
-    atomic_add_i32(hi + w.i, h);
-    atomic_add_i32(lo + w.i, l);
-    fix_split((w.u.y * w.t2) * w.t3, h, l);
-    atomic_add_i32(hi + w.i - 2 * PL, h);
-    atomic_add_i32(lo + w.i - 2 * PL, l);
-}
+#if defined(PME_HOST_EMULATION)
+template <int P, int T>
+struct Lanes4 {
+    const SpreadSmem<P, T> &s;
+    int off;  // region offset of the lane's point below the atom's highest support point
+    Lanes4(const SpreadSmem<P, T> &sm, int lane)
+        : s(sm),
+          off((lane >> 4) * SpreadLayout<P, T>::PL + ((lane >> 2) & 3) * SpreadLayout<P, T>::RS + (lane & 3)),
+          ja(lane >> 4), j2((lane >> 2) & 3), j3(lane & 3) {}
+    int ja, j2, j3;
+    Lane4 load(int a) const {
+        Lane4 w;
+        w.u = ((const float2 *)(s.u_s + a))[ja];
+        w.t2 = ((const float *)(s.t2_s + a))[j2];
+        w.t3 = ((const float *)(s.t3_s + a))[j3];
+        w.i = s.ix_s[a] - off;
+        return w;
+    }
+    void add(const Lane4 &w) const {
+        constexpr int PL = SpreadLayout<P, T>::PL;
+        int h, l;
+        fix_split((w.u.x * w.t2) * w.t3, h, l);
+        s.hi[w.i] += h;
+        s.lo[w.i] += l;
+        fix_split((w.u.y * w.t2) * w.t3, h, l);
+        s.hi[w.i - 2 * PL] += h;
+        s.lo[w.i - 2 * PL] += l;
+    }
+};
+#else
+// GPU: 32-bit shared-window addresses computed once per lane, so each load or reduction costs one add
+// instead of 64-bit generic pointer arithmetic
+PME_DEV unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int P, int T>
+struct Lanes4 {
+    static constexpr unsigned DLO = 4u * SpreadLayout<P, T>::VOLP;  // lo - hi, bytes
+    static constexpr unsigned D2 = 8u * SpreadLayout<P, T>::PL;     // two planes, bytes
+    unsigned su, st2, st3, six, shi;
+    PME_DEV Lanes4(const SpreadSmem<P, T> &s, int lane) {
+        const int ja = lane >> 4, j2 = (lane >> 2) & 3, j3 = lane & 3;
+        su = smem_u32(s.u_s) + 8u * ja;
+        st2 = smem_u32(s.t2_s) + 4u * j2;
+        st3 = smem_u32(s.t3_s) + 4u * j3;
+        six = smem_u32(s.ix_s);
+        shi = smem_u32(s.hi) - 4u * (ja * SpreadLayout<P, T>::PL + j2 * SpreadLayout<P, T>::RS + j3);
+    }
+    PME_DEV Lane4 load(int a) const {
+        Lane4 w;
+        int ix;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(w.u.x), "=f"(w.u.y) : "r"(su + 16u * a) : "memory");
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(w.t2) : "r"(st2 + 16u * a) : "memory");
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(w.t3) : "r"(st3 + 16u * a) : "memory");
+        asm volatile("ld.shared.s32 %0, [%1];" : "=r"(ix) : "r"(six + 4u * a) : "memory");
+        w.i = (int)(shi + 4u * (unsigned)ix);
+        return w;
+    }
+    PME_DEV static void red(unsigned addr, int v) {
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    }
+    PME_DEV void add(const Lane4 &w) const {
+        const unsigned ad = (unsigned)w.i;
+        int h, l;
+        fix_split((w.u.x * w.t2) * w.t3, h, l);
+        red(ad, h);
+        red(ad + DLO, l);
+        fix_split((w.u.y * w.t2) * w.t3, h, l);
+        red(ad - D2, h);
+        red(ad + DLO - D2, l);
+    }
+};
+#endif
 
 // cleared: spread_clear already ran on this shared memory (and nothing has used it since). org: the tile's
 // origin (tile_origin), when the caller computed it already.
@@ -461,18 +511,20 @@ PME_DEV void stage_spread(const SysDev &d, int item, void *smem, bool cleared = 
         // the atoms w, w + nw, ... two at a time, both atoms' weights loaded before either is added
 #if defined(PME_HOST_EMULATION)
         for (int a = 0; a < cnt; ++a)
-            for (int lane = 0; lane < 32; ++lane)
-                lane4_add<PL>(hi, lo, lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a, lane));
+            for (int lane = 0; lane < 32; ++lane) {
+                const Lanes4<P, T> ln(sm, lane);
+                ln.add(ln.load(a));
+            }
 #else
-        const int nw = nth >> 5, lane = tid & 31;
+        const int nw = nth >> 5;
+        const Lanes4<P, T> ln(sm, tid & 31);
         int a = tid >> 5;
         for (; a + nw < cnt; a += 2 * nw) {
-            const Lane4 w0 = lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a, lane);
-            const Lane4 w1 = lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a + nw, lane);
-            lane4_add<PL>(hi, lo, w0);
-            lane4_add<PL>(hi, lo, w1);
+            const Lane4 w0 = ln.load(a), w1 = ln.load(a + nw);
+            ln.add(w0);
+            ln.add(w1);
         }
-        if (a < cnt) lane4_add<PL>(hi, lo, lane4_load<RS, PL>(sm.u_s, sm.t2_s, sm.t3_s, sm.ix_s, a, lane));
+        if (a < cnt) ln.add(ln.load(a));
 #endif
     } else {
         // Dealt order: residue r = (base mod 16) of the atom's highest support point in the padded region;
