@@ -119,6 +119,15 @@ extern "C" {
 
 void emu_set_k1_pieces(int n) { g_k1_pieces = n; }
 
+// Spreading region layout for order p and tile edge 2^tlog: row stride, plane stride, accumulator length
+// (ints) and whether one warp spreads one atom at a time.
+void emu_spread_layout(int p, int tlog, int *out) {
+    out[0] = spread_row(p, tlog);
+    out[1] = spread_plane(p, tlog);
+    out[2] = spread_vol(p, tlog);
+    out[3] = spread_warp_lanes(p, tlog) ? 1 : 0;
+}
+
 // One or more evaluations (repeat >= 1, same inputs) of the emulated pipeline. Outputs: forces (n*3),
 // ev[7], and optionally the fixed-point mesh as spread (grid_out, K1*K2*K3 int64) and phi (K1*K2*K3).
 // Returns the device status bits of the last evaluation, or -1 / -2 for invalid / unsupported input.

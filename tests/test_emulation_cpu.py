@@ -142,3 +142,31 @@ def test_emulated_odd_order_paths_bit_identical(oracle_mod, emu):
     assert rel_energy(evt[0], r["energy"]) < E_REL_TOL
     assert rms_force(Ft, r["forces"]) < F_RMS_TOL
     assert rel_virial(evt[1:], r["virial"]) < V_TOL
+
+
+def test_spread_layout_banks(emu):
+    """Spreading region layouts, checked from the bank rule (word w sits in bank w mod 32): with p = 4 and 8^3
+    tiles one warp takes one atom, lane (jA, j2, j3) = (lane / 16, lane / 4 mod 4, lane mod 4) adding the
+    points (jA, j2, j3) and (jA + 2, j2, j3) below the atom's highest support point, and at each step the 32
+    lanes must hit 32 distinct banks wherever the atom lies; otherwise two threads split an atom's planes
+    into halves half_planes = ceil(p / 2) planes apart, which must sit 16 banks apart. Every region fits its
+    padded array, rounded to 4 ints so the record arrays after it stay 16-byte aligned."""
+    import ctypes
+    emu.emu_spread_layout.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    for p in (4, 5, 6, 8):
+        for tlog in (3, 4):
+            out = (ctypes.c_int * 4)()
+            emu.emu_spread_layout(p, tlog, out)
+            rs, pl, vol, warp = list(out)
+            R = (1 << tlog) + p - 1
+            assert rs >= R and pl >= R * rs and vol >= R * pl and vol % 4 == 0
+            assert warp == (p == 4 and tlog == 3)
+            if warp:
+                for base in range(64):  # the atom's highest support point, any bank alignment
+                    for step in (0, 2):  # planes jA and jA + 2
+                        banks = {(base - ((ja + step) * pl + j2 * rs + j3)) % 32
+                                 for ja in range(2) for j2 in range(4) for j3 in range(4)}
+                        assert len(banks) == 32, (p, tlog, base, step)
+            else:
+                assert rs == R
+                assert ((p + 1) // 2 * pl) % 32 == 16
